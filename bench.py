@@ -1,0 +1,356 @@
+"""Benchmark of the 2D-PT hot path on GB300.
+
+Workload (default): a planted Wishart instance with N = 200 logical spins,
+alpha = 0.5, copy-chain sparsified to at most 3 original edges per copy
+(13,400 physical spins), an I = 32 x J = 8 replica grid (geometric beta
+0.1..2.0, linear P 0.5..4.0 x 32767), 64 independent runs (16,384 replicas),
+swap interval 50.  One step = one swap event of Algorithm 1 for all runs:
+50 heat-bath sweeps of every replica, f and g of the final sweep, one round
+of P- or beta-swaps and the bottom-right record.  The int8 spin state
+(220 MB) is larger than L2, so no flush is needed between steps.
+
+Metric: spin updates per second (physical spins x replicas x sweeps / time).
+
+Arms: the default arm times the CUDA library; --impl reference times the CPU
+oracle (a plain restatement of the method, the only reference this project
+has) on the host cores for a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "spin updates/sec"
+UNIT = "spin-updates/s"
+WORKLOAD = "wishart-planted N=200 alpha=0.5, <=3 edges/copy (13400 spins), I=32 x J=8, 64 runs, swap every 50 sweeps"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_workload(N=200, alpha=0.5, inst_seed=2, I=32, J=8, runs=64, interval=50):
+    import synth
+
+    inst = synth.wishart_planted(N, alpha, inst_seed)
+    beta = synth.beta_ladder(I, 0.1, 2.0, inst.scale)
+    P = synth.penalty_ladder(J, 0.5, 4.0, 32767)
+    return dict(inst=inst, beta=beta, P=P, runs=runs, interval=interval, I=I, J=J)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus: int):
+    if n_gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ["RANK"])
+    world = int(os.environ["WORLD_SIZE"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", init_method="env://")
+    return rank, world, dist
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2506_14781_gb300 as pt
+
+    rank, world, dist = dist_setup(args.gpus)
+    dev = torch.cuda.current_device()
+    wl = make_workload()
+    inst, beta, P, runs, interval = wl["inst"], wl["beta"], wl["P"], wl["runs"], wl["interval"]
+    phys = pt.sparsify(inst.Jq, "max_edges", 3)
+    n = phys.n
+    R = len(beta) * len(P)
+    updates_per_step = n * R * runs * interval
+    stream = torch.cuda.Stream()
+    ctx = pt.PT2D(phys, beta, P, runs, stream=stream, workspace="torch", trace_capacity=4096,
+                  profile=True)
+    ctx.write(pt.TARGET, np.full(runs, inst.E_planted, np.int64))
+    seed = 100 + rank
+    with torch.cuda.stream(stream):
+        ctx.run(interval * args.warmup, interval, seed)
+    ctx.sync()
+    ms0, launches0 = ctx.kernel_time(0)
+    swap_ms0, _ = ctx.kernel_time(1)
+    n_launch0 = ctx.launch_count
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        start.record(stream)
+        ctx.run(interval * args.steps, interval, seed)
+        end.record(stream)
+        end.synchronize()
+    torch.cuda.synchronize()
+    elapsed_ms = start.elapsed_time(end)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    sweep_ms, sweep_launches = ctx.kernel_time(0)
+    swap_ms, _ = ctx.kernel_time(1)
+    gpu_launches = ctx.launch_count - n_launch0
+    sweep_ms -= ms0
+    sweep_launches -= launches0
+    swap_ms -= swap_ms0
+    value = updates_per_step * args.steps * world / (elapsed_ms / 1e3)
+    # roofline of the sweep kernel
+    peaks, peak_src = _peaks()
+    avg_launch_ms = sweep_ms / max(sweep_launches, 1)
+    updates_per_launch = n * R * runs * interval
+    # algorithmic bytes per update: one int8 write plus one int8 read of the state
+    # (neighbour rows shared within a colour pass), plus the ELL row (4 B index +
+    # 4 B coupling per neighbour, 5 neighbours) amortised over a 128-walker warp
+    algo_bytes = updates_per_launch * (2.0 + 40.0 / 128.0)
+    hbm_achieved = algo_bytes / (avg_launch_ms / 1e3) / 1e9
+    # issue roofline: lane-operations the heat-bath contract needs per update
+    # (Philox4x32-10 share 15, field 10, decision 8), against 152 SMs x 128 lanes x clock
+    ops_per_update = 33.0
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
+    alu_achieved = updates_per_launch * ops_per_update / (avg_launch_ms / 1e3) / 1e12
+    clocks = clk.summary()
+    # time to planted ground state (bottom-right g = 0 and f <= planted energy)
+    solved = ctx.read(pt.SOLVED_EVENT)
+    best = ctx.read(pt.BEST_F)
+    sec_per_sweep = elapsed_ms / 1e3 / (args.steps * interval)
+    solved_mask = solved >= 0
+    feasible = best < np.iinfo(np.int64).max
+    rho = (best[feasible] - inst.E_planted) / (inst.N * inst.scale)
+    tts = {
+        "target": "bottom-right g=0 and f <= planted energy",
+        "solved_runs": int(solved_mask.sum()),
+        "runs": int(runs),
+        "median_sweeps_to_solve": float(np.median(solved[solved_mask] * interval)) if solved_mask.any() else None,
+        "seconds_per_sweep_all_runs": sec_per_sweep,
+        "median_best_feasible_residual_per_spin": float(np.median(rho)) if rho.size else None,
+        "sweeps_run": int((args.warmup + args.steps) * interval),
+    }
+    e2e = run_e2e(pt, phys, wl, args) if rank == 0 else None
+    cpu = cpu_baseline(wl, args) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int8 spins, int32 fields, f32 decisions",
+        "data": "synthetic (seeded planted Wishart instance)",
+        "config": {"workload": WORKLOAD, "physical_spins": n, "replicas": R * runs,
+                   "sweeps_per_step": interval, "l2": "state 220 MB > L2; no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "tiling": "automatic"},
+        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                     "unit": "Tops/s (lane-ops)", "frac": alu_achieved / alu_peak,
+                     "traffic": None, "kernel": "k_sweep",
+                     "peak_source": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_src} max clock)",
+                     "ops_per_update": ops_per_update,
+                     "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks.get("hbm_gbs"),
+                             "frac": hbm_achieved / peaks.get("hbm_gbs", 6800.0),
+                             "bytes_per_update": 2.0 + 40.0 / 128.0},
+                     "avg_launch_ms": avg_launch_ms, "launches": sweep_launches,
+                     "share_of_step": sweep_ms / max(elapsed_ms, 1e-9)},
+        "e2e": e2e,
+        "gpu_launches": int(gpu_launches),
+        "clocks": clocks,
+        "tts": tts,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_e2e(pt, phys, wl, args):
+    """The same metric through the C ABI with host buffers: each job creates a
+    context from the host instance (host -> device copies), runs E events and
+    reads the results back (device -> host); wall time covers everything."""
+    import torch
+
+    inst, beta, P, runs, interval = wl["inst"], wl["beta"], wl["P"], wl["runs"], wl["interval"]
+    events = max(1, min(args.steps, 20))
+    jobs = 2
+    R = len(beta) * len(P)
+    h2d = (phys.cp_ptr.nbytes + phys.cp_col.nbytes + phys.cp_J.nbytes + phys.lk_ptr.nbytes
+           + phys.lk_col.nbytes + beta.nbytes + P.nbytes + runs * 8)
+    d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(jobs):
+        ctx = pt.PT2D(phys, beta, P, runs, trace_capacity=events)
+        ctx.write(pt.TARGET, np.full(runs, inst.E_planted, np.int64))
+        ctx.run(interval * events, interval, 500 + j)
+        res = [ctx.read(pt.BEST_F), ctx.read(pt.BEST_STATE), ctx.read(pt.SOLVED_EVENT),
+               ctx.read(pt.TRACE_F), ctx.read(pt.TRACE_G)]
+        d2h = sum(r.nbytes for r in res)
+        ctx.close()
+    wall = time.perf_counter() - t0
+    updates = phys.n * R * runs * interval * events * jobs
+    return {"value": updates / wall, "unit": UNIT, "h2d_bytes_per_step": int(h2d / events),
+            "d2h_bytes_per_step": int(d2h / events),
+            "job": f"create from host CSR + {events} events + read best/trace, x{jobs}"}
+
+
+def _oracle_sample(wl, threads, sweeps, state=None):
+    """Time the CPU oracle on `threads` runs of the workload (one thread per run),
+    `sweeps` sweeps each (one event of that length)."""
+    import threading
+
+    import oracle
+
+    if state is None:
+        phys = oracle.sparsify(wl["inst"].Jq, "max_edges", 3)
+        oinst = oracle.OracleInstance(phys)
+        orcs = [oracle.OracleRun(oinst, wl["beta"], wl["P"], [r], 100 + r) for r in range(threads)]
+        state = (phys, orcs)
+    phys, orcs = state
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=o.run, args=(sweeps, sweeps)) for o in orcs]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    wall = time.perf_counter() - t0
+    R = len(wl["beta"]) * len(wl["P"])
+    updates = phys.n * R * sweeps * threads
+    return updates / wall, wall, state
+
+
+def cpu_baseline(wl, args):
+    threads = os.cpu_count() or 1
+    rate, wall, _ = _oracle_sample(wl, threads, args.cpu_sweeps)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{threads} runs x 256 replicas x {args.cpu_sweeps} sweeps of the N=200 "
+                      f"instance (one thread per run), {wall:.1f} s wall"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload()
+    threads = os.cpu_count() or 1
+    sweeps = 2
+    state = None
+    for _ in range(args.warmup):
+        _, _, state = _oracle_sample(wl, threads, sweeps, state)
+    total_updates = 0.0
+    total_wall = 0.0
+    for _ in range(args.steps):
+        rate, wall, state = _oracle_sample(wl, threads, sweeps, state)
+        total_updates += rate * wall
+        total_wall += wall
+    value = total_updates / total_wall
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_wall / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int8 spins, int64 energies, f32 decisions", "data": "synthetic (seeded planted Wishart instance)",
+        "config": {"workload": WORKLOAD, "sample": f"per step: {threads} runs x 256 replicas x {sweeps} sweeps"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{threads} runs x 256 replicas x {sweeps} sweeps per step, one thread per run"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * pt2d.h — C ABI of the GB300 (sm_103a) two-dimensional parallel tempering
+ * library (arxiv 2506.14781, "Two-dimensional Parallel Tempering for
+ * Constrained Optimization").
+ *
+ * The library runs 2D-PT (Algorithm 1) on an I x J grid of replicas of a
+ * constrained Ising problem with penalised energy E_j = f + P_j g (Eq. 1):
+ * row i has inverse temperature beta_i, column j penalty P_j.  Heat-bath
+ * Gibbs sweeps are interleaved with P-swaps inside rows (Eq. 2) and
+ * beta-swaps inside columns (Eq. 3).  Many independent runs ("runs", each its
+ * own I x J grid, all on the same instance) are simulated together.
+ *
+ * Conventions for every entry point:
+ *  - returns PT2D_OK (0) or a negative PT2D_ERR_* code; pt2d_strerror() names it;
+ *  - host pointers are read during the call only (inputs are copied); the
+ *    caller keeps ownership of every buffer it passes;
+ *  - device work is queued on the context's stream; pt2d_read/pt2d_write and
+ *    pt2d_sync synchronise that stream;
+ *  - no global state: one context per thread at a time (contexts are
+ *    independent and may live on different streams).
+ *
+ * Numerical contract (identical on the CPU oracle and the GPU):
+ *  - couplings are int16, fields and penalties integers, so f, g, E and the
+ *    local field H_a = E(s_a=-1) - E(s_a=+1)
+ *        = 2 sum_b J_ab s_b + 2 h_a + P_j sum_{links l of a} s_l
+ *    are exact integers (|H_a| < 2^24 is required);
+ *  - g = number of copy links (a,b) with s_a != s_b (copy constraint of the
+ *    section "Graph sparsification with copy constraints", normalised so that a
+ *    broken link counts 1);
+ *  - random words: Philox4x32-10 keyed by the 64-bit seed; counter
+ *    (c0, c1, c2, (run << 4) | tag) with
+ *      sweep: c0 = spin id, c1 = global sweep index, c2 = walker / 4, word walker % 4
+ *      init:  c0 = spin id, c1 = 0,                 c2 = walker / 4, word walker % 4
+ *      swap:  c0 = lower slot index of the pair, c1 = event index n (1-based), c2 = 0, word 0
+ *    and u = (word >> 9) * 2^-23;
+ *  - heat bath: t = beta (x) float(H); e = pt_exp(-t); d = 1 (+) e; v = u (x) d;
+ *    new spin +1 iff v < 1 (single-precision, round-to-nearest, no fused ops);
+ *  - swaps: x = beta_i (x) float(dP dg) for P-swaps, x = (beta_{i+1} (-) beta_i)
+ *    (x) float(E_{i+1} - E_i) for beta-swaps; accept iff x >= 0 or u <= pt_exp(x);
+ *  - pt_exp: Cody-Waite reduction by ln 2 split in two floats, degree-7 Taylor
+ *    polynomial in Horner form, scaling by 2^k in two steps; +inf above 88.75,
+ *    0 below -104.
+ *  Spins of one colour of the greedy colouring (ascending ids, smallest colour
+ *  free among coupling and link neighbours) are updated together; colours in
+ *  ascending order make one sweep.
+ */
+#ifndef PT2D_H
+#define PT2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PT2D_OK 0
+#define PT2D_ERR_INVALID_ARG (-1) /* malformed instance, ladder or size      */
+#define PT2D_ERR_OOM (-2)         /* device or host allocation failed        */
+#define PT2D_ERR_CUDA (-3)        /* a CUDA call failed (see pt2d_cuda_error) */
+#define PT2D_ERR_TIMEOUT (-4)     /* a bounded device wait expired           */
+#define PT2D_ERR_STATE (-5)       /* call not valid in the context's state   */
+#define PT2D_ERR_UNSUPPORTED (-6) /* no sm_103a device or feature missing    */
+
+/* ---- readable / writable context arrays (pt2d_read, pt2d_write) --------- */
+/* R = I*J slots per run; slot index s = i*J + j; walker ids 0..R-1 per run. */
+#define PT2D_STATES 1       /* int8  [runs][R][n]  spins of each walker (+1/-1)    */
+#define PT2D_WALKER_AT 2    /* int32 [runs][R]     slot -> walker                  */
+#define PT2D_F 3            /* int64 [runs][R]     cost f of each walker, last event */
+#define PT2D_G 4            /* int64 [runs][R]     constraint g of each walker       */
+#define PT2D_COUNTERS 5     /* int64 [4] sweeps done, events done, direction, inited */
+#define PT2D_TRACE_F 6      /* int64 [runs][trace_capacity] bottom-right f after event n */
+#define PT2D_TRACE_G 7      /* int64 [runs][trace_capacity] bottom-right g            */
+#define PT2D_BEST_F 8       /* int64 [runs] lowest bottom-right f with g == 0         */
+#define PT2D_BEST_EVENT 9   /* int64 [runs] event of BEST_F, -1 if none               */
+#define PT2D_BEST_STATE 10  /* int8  [runs][n] spins of BEST_F                        */
+#define PT2D_SOLVED_EVENT 11 /* int64 [runs] first event with g == 0 and f <= target, -1 */
+#define PT2D_ACC_P 12       /* int64 [runs][R] accepted P-swaps, by lower slot        */
+#define PT2D_ACC_B 13       /* int64 [runs][R] accepted beta-swaps, by lower slot     */
+#define PT2D_SUM_F 14       /* int64 [runs][R] per slot: sum of f after each event    */
+#define PT2D_SUM_G 15       /* int64 [runs][R] per slot: sum of g                     */
+#define PT2D_N_FEASIBLE 16  /* int64 [runs][R] per slot: events with g == 0           */
+#define PT2D_COLORS 17      /* int32 [n] colour of each spin (read only)              */
+#define PT2D_TARGET 18      /* int64 [runs] solved threshold (write to set)           */
+
+/* ---- problem description ---------------------------------------------- */
+/* Physical (sparsified) instance.  Host pointers; copied at create time.
+ * Couplings: symmetric CSR without self loops, J in int16, f = -sum_{a<b}
+ * J_ab s_a s_b - sum_a h_a s_a.  Links (copy constraints): symmetric CSR,
+ * g = #{links (a,b): s_a != s_b}.  Column indices need not be sorted. */
+typedef struct {
+    int32_t n;              /* physical spins, >= 1                          */
+    const int32_t *cp_ptr;  /* [n+1] coupling row pointers                   */
+    const int32_t *cp_col;  /* [cp_ptr[n]] coupling neighbours                */
+    const int16_t *cp_J;    /* [cp_ptr[n]] coupling values                    */
+    const int32_t *lk_ptr;  /* [n+1] link row pointers                        */
+    const int32_t *lk_col;  /* [lk_ptr[n]] link neighbours                    */
+    const int32_t *h;       /* [n] integer field, or NULL for zero            */
+    const int32_t *color;   /* [n] proper colouring, or NULL: greedy (above)  */
+} pt2d_instance;
+
+typedef struct {
+    void *stream;            /* cudaStream_t for all work; NULL = default stream   */
+    void *workspace;         /* caller-owned device memory, or NULL: library allocates */
+    size_t workspace_bytes;  /* size of `workspace` (see pt2d_workspace_size)      */
+    int32_t trace_capacity;  /* events kept in the bottom-right trace (default 1024) */
+    int32_t walkers_per_cta; /* sweep tiling: 4..128, power of two; 0 = automatic   */
+    int32_t threads_per_cta; /* 32..256, multiple of 32, >= walkers_per_cta/4; 0 = auto */
+    int32_t device;          /* CUDA device ordinal; -1 = current device            */
+    int32_t profile;         /* nonzero: time every kernel launch with CUDA events  */
+} pt2d_options;
+
+typedef struct pt2d_ctx pt2d_ctx;
+
+/* Fill `opt` with defaults (stream NULL, no workspace, trace 1024, automatic tiling). */
+void pt2d_default_options(pt2d_options *opt);
+
+/* Device bytes a context needs (for a caller-provided workspace).
+ * Errors: INVALID_ARG for a malformed instance or sizes. */
+int pt2d_workspace_size(const pt2d_instance *inst, int32_t I, int32_t J, int32_t runs,
+                        const pt2d_options *opt, size_t *bytes);
+
+/* Create a context: validates and copies the instance (the inputs of
+ * Algorithm 1: couplings and fields, the constraint given by the copy links,
+ * and the two ordered ladders), colours it if no colouring is given, and lays
+ * it out on the device.
+ * beta: [I] float32, ascending, in the units of the integer couplings.
+ * P:    [J] int32, ascending, >= 0.  I * J <= 8192.  runs >= 1 independent grids.
+ * Errors: INVALID_ARG (bad CSR, asymmetric, self loop, improper colouring,
+ * non-ascending ladder, |H| bound exceeded, workspace too small), OOM, CUDA,
+ * UNSUPPORTED (device is not sm_103). */
+int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const float *beta,
+                int32_t J, const int32_t *P, int32_t runs, const pt2d_options *opt);
+
+/* Run floor(sweeps / swap_interval) swap events of Algorithm 1: each event is
+ * swap_interval sweeps of every walker, then f and g of the final sweep, then
+ * one round of P-swaps (direction +1) or beta-swaps (direction -1) on odd
+ * (odd n) or even (even n) pairs, then the bottom-right record; the direction
+ * flips after every even event.  The first call initialises the spins from the
+ * seeded init stream.  Counters persist, so run(a); run(b) equals run(a + b)
+ * when both are multiples of the interval.  Asynchronous on the context stream.
+ * Errors: INVALID_ARG (interval < 1, sweeps < 0, seed differs from the first
+ * call's seed, sweep counter would pass 2^32), CUDA. */
+int pt2d_run(pt2d_ctx *ctx, int64_t sweeps, int32_t swap_interval, uint64_t seed);
+
+/* Copy one context array (PT2D_* above) to host memory; synchronises the
+ * stream.  `bytes` must equal the array size.  Errors: INVALID_ARG, STATE
+ * (reading spins before the first run), CUDA. */
+int pt2d_read(pt2d_ctx *ctx, int32_t what, void *host_dst, size_t bytes);
+
+/* Copy the spins of one walker (run, walker id) to host_dst[n] in spin-id
+ * order; synchronises the stream.  Used to read a single replica (for example
+ * the one in the bottom-right slot, whose spins Algorithm 1 stores) without
+ * copying every walker.  Errors: INVALID_ARG, STATE (before the first run), CUDA. */
+int pt2d_read_walker(pt2d_ctx *ctx, int32_t run, int32_t walker, int8_t *host_dst);
+
+/* Overwrite one context array from host memory (checkpoint restore):
+ * STATES, WALKER_AT, COUNTERS, BEST_F, BEST_EVENT, BEST_STATE, SOLVED_EVENT,
+ * ACC_P, ACC_B, SUM_F, SUM_G, N_FEASIBLE, TARGET, TRACE_F, TRACE_G.  Writing
+ * COUNTERS with inited = 1 marks the context initialised (the seed of the next
+ * run is then adopted).  Errors: INVALID_ARG (size, permutation not valid),
+ * CUDA. */
+int pt2d_write(pt2d_ctx *ctx, int32_t what, const void *host_src, size_t bytes);
+
+/* Size in bytes of array `what` for this context (0 if unknown). */
+size_t pt2d_array_bytes(const pt2d_ctx *ctx, int32_t what);
+
+/* Block until the context's queued work is done.  Errors: CUDA, TIMEOUT. */
+int pt2d_sync(pt2d_ctx *ctx);
+
+/* Number of colours of the context's colouring, and kernel launches queued so far. */
+int pt2d_num_colors(const pt2d_ctx *ctx);
+int64_t pt2d_launch_count(const pt2d_ctx *ctx);
+
+/* Kernel timing of a context created with opt.profile != 0: total device
+ * milliseconds and launch count of the sweep kernel (kind 0) or the swap-event
+ * kernel (kind 1) since creation, from CUDA events recorded on the context
+ * stream around each launch.  Synchronises the stream.
+ * Errors: INVALID_ARG (bad kind), STATE (profiling off), CUDA. */
+#define PT2D_KERNEL_SWEEP 0
+#define PT2D_KERNEL_SWAP 1
+int pt2d_kernel_time(pt2d_ctx *ctx, int32_t kind, double *ms, int64_t *launches);
+
+/* Release everything the context owns (not a caller-provided workspace). */
+void pt2d_destroy(pt2d_ctx *ctx);
+
+/* Static description of a status code. */
+const char *pt2d_strerror(int status);
+
+/* Last CUDA error code (cudaError_t) recorded by the context, 0 if none. */
+int pt2d_cuda_error(const pt2d_ctx *ctx);
+
+/* ---- host-side compiler helpers (section "Graph sparsification") ------- */
+/* Copy-chain sparsification of a dense symmetric int16 logical coupling
+ * matrix Jq[N*N] (zero diagonal).  Logical node i with K_i copies owns
+ * physical ids offset_i..offset_i+K_i-1 chained by links; its nonzero
+ * neighbours in ascending order are dealt round-robin over its copies,
+ * skipping full copies; logical edge (i,j) becomes one coupling between the
+ * copy of i that received j and the copy of j that received i.
+ * rule: PT2D_SPARSIFY_FIXED (K = param), PT2D_SPARSIFY_MAX_EDGES (at most
+ * param original edges per copy), PT2D_SPARSIFY_MAX_DEGREE (physical degree
+ * including links <= param).
+ * Call once with all output pointers NULL to get n, nnz_cp, nnz_lk; then again
+ * with arrays of those sizes: cp_ptr[n+1], cp_col[nnz_cp], cp_J[nnz_cp],
+ * lk_ptr[n+1], lk_col[nnz_lk], copy_of[n] (rows sorted by column).
+ * Errors: INVALID_ARG (asymmetric matrix, bad rule). */
+#define PT2D_SPARSIFY_FIXED 0
+#define PT2D_SPARSIFY_MAX_EDGES 1
+#define PT2D_SPARSIFY_MAX_DEGREE 2
+int pt2d_sparsify(int32_t N, const int16_t *Jq, int32_t rule, int32_t param, int32_t *n,
+                  int64_t *nnz_cp, int64_t *nnz_lk, int32_t *cp_ptr, int32_t *cp_col,
+                  int16_t *cp_J, int32_t *lk_ptr, int32_t *lk_col, int32_t *copy_of);
+
+/* Greedy colouring of a physical instance (the rule described above).
+ * color: [n] output; *n_colors: number of colours.  Errors: INVALID_ARG. */
+int pt2d_greedy_color(const pt2d_instance *inst, int32_t *color, int32_t *n_colors);
+
+/* ---- diagnostics: the device arithmetic, element-wise -------------------- */
+/* Each runs the same device functions the sweep and swap kernels use, on
+ * `count` elements given in host memory, and copies results back (synchronous,
+ * default device, legacy stream).  Errors: INVALID_ARG, CUDA, UNSUPPORTED. */
+int pt2d_diag_philox(const uint32_t *ctr /*[count][4]*/, const uint32_t *key /*[count][2]*/,
+                     uint32_t *out /*[count][4]*/, int64_t count);
+int pt2d_diag_pt_exp(const float *x, float *y, int64_t count);
+int pt2d_diag_heatbath(const float *beta, const int32_t *H, const uint32_t *r, int8_t *spin,
+                       int64_t count);
+int pt2d_diag_swap_accept(const float *x, const uint32_t *r, int8_t *accept, int64_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT2D_H */

@@ -50,6 +50,17 @@ def load(path: str):
     L.orc_swap_count.restype = C.c_int64
     L.orc_pt_exp_constants.argtypes = [C.POINTER(C.c_float)]
     L.orc_pt_exp_constants.restype = None
+    L.orc_swap_event.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32, C.c_int64,
+                                 C.c_int, C.c_void_p, C.c_void_p]
+    L.orc_swap_event.restype = None
+    for name in ("orc_pt_exp_array", "orc_swap_accept_array", "orc_philox_array"):
+        getattr(L, name).restype = None
+    L.orc_pt_exp_array.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    L.orc_heatbath_array.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+    L.orc_heatbath_array.restype = None
+    L.orc_swap_accept_array.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+    L.orc_philox_array.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     return L
 
 
@@ -147,6 +158,53 @@ def pt_exp_constants() -> np.ndarray:
     out = (C.c_float * 11)()
     lib().orc_pt_exp_constants(out)
     return np.array(list(out), dtype=np.float32)
+
+
+def pt_exp_array(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    lib().orc_pt_exp_array(_p(x), _p(y), x.size)
+    return y
+
+
+def heatbath_array(beta, H, r) -> np.ndarray:
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    H = np.ascontiguousarray(H, dtype=np.int32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    out = np.empty(beta.size, dtype=np.int8)
+    lib().orc_heatbath_array(_p(beta), _p(H), _p(r), _p(out), beta.size)
+    return out
+
+
+def swap_accept_array(x, r) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    out = np.empty(x.size, dtype=np.int8)
+    lib().orc_swap_accept_array(_p(x), _p(r), _p(out), x.size)
+    return out
+
+
+def philox_array(ctr, key) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.empty_like(ctr)
+    lib().orc_philox_array(_p(ctr), _p(key), _p(out), ctr.shape[0])
+    return out
+
+
+def swap_event(beta, P, f_w, g_w, walker_at, seed: int, run: int, event: int, direction: int):
+    """One swap event of Algorithm 1 on one run's slot->walker map (copied);
+    returns (walker_at, acc_P, acc_B)."""
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    P = np.ascontiguousarray(P, dtype=np.int32)
+    f_w = np.ascontiguousarray(f_w, dtype=np.int64)
+    g_w = np.ascontiguousarray(g_w, dtype=np.int64)
+    at = np.array(walker_at, dtype=np.int32, copy=True)
+    accP = np.zeros(at.size, np.int64)
+    accB = np.zeros(at.size, np.int64)
+    lib().orc_swap_event(beta.size, _p(beta), P.size, _p(P), _p(f_w), _p(g_w), _p(at), int(seed),
+                         int(run), int(event), int(direction), _p(accP), _p(accB))
+    return at, accP, accB
 
 
 class OracleInstance:

@@ -138,8 +138,8 @@ float orc_pt_exp(float x)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Heat-bath (Gibbs) update.  The paper leaves the single-spin rule open     */
-/* ("perform sweeps", Algorithm 1); this is the standard heat bath for       */
+/* Heat-bath (Gibbs) update.  Algorithm 1 asks for sweeps but leaves the     */
+/* single-spin rule open; this is the standard heat bath for                 */
 /* E = f + P g: with the local field H = E(s_a=-1) - E(s_a=+1),              */
 /* P(s_a = +1) = 1 / (1 + exp(-beta H)).  Fixed float sequence:               */
 /*   t = beta * float(H); e = pt_exp(-t); d = 1 + e; v = u * d;              */
@@ -281,6 +281,51 @@ static void orc_swap_slots(int32_t *walker_at, int32_t sa, int32_t sb)
     walker_at[sb] = t;
 }
 
+/* One swap event of Algorithm 1 for one run, given f and g of every walker
+ * (indexed by walker) after the final sweep.  Event n (1-based) uses the pairs
+ * starting at the first replica when n is odd and at the second when n is
+ * even; direction +1 swaps along P inside every row (Eq. 2), -1 along beta
+ * inside every column (Eq. 3).  `at` maps slot -> walker and is permuted in
+ * place; acc_P / acc_B count accepted swaps by the lower slot of the pair. */
+void orc_swap_event(int32_t I, const float *beta, int32_t J, const int32_t *P, const int64_t *fw,
+                    const int64_t *gw, int32_t *at, uint64_t seed, uint32_t run, int64_t nev,
+                    int direction, int64_t *acc_P, int64_t *acc_B)
+{
+    const int even = (nev % 2 == 0);
+    if (direction == 1) {
+        /* swaps along P: each row, pairs (p, p+1) for p = even, even+2, ... */
+        for (int32_t i = 0; i < I; ++i)
+            for (int32_t p = even; p + 1 < J; p += 2) {
+                const int32_t sa = i * J + p, sb = i * J + p + 1;
+                const int64_t dP = (int64_t)P[p + 1] - (int64_t)P[p];
+                const int64_t dg = gw[at[sb]] - gw[at[sa]];
+                const float x = beta[i] * (float)(dP * dg);
+                const uint32_t r = orc_word(seed, (uint32_t)sa, (uint32_t)nev, 0u, run,
+                                            ORC_TAG_SWAP, 0);
+                if (orc_swap_accept(x, r)) {
+                    orc_swap_slots(at, sa, sb);
+                    acc_P[sa] += 1;
+                }
+            }
+    } else {
+        /* swaps along beta: each column, pairs (b, b+1) for b = even, even+2, ... */
+        for (int32_t j = 0; j < J; ++j)
+            for (int32_t b = even; b + 1 < I; b += 2) {
+                const int32_t sa = b * J + j, sb = (b + 1) * J + j;
+                const float dbeta = beta[b + 1] - beta[b];
+                const int64_t Ea = fw[at[sa]] + (int64_t)P[j] * gw[at[sa]];
+                const int64_t Eb = fw[at[sb]] + (int64_t)P[j] * gw[at[sb]];
+                const float x = dbeta * (float)(Eb - Ea);
+                const uint32_t r = orc_word(seed, (uint32_t)sa, (uint32_t)nev, 0u, run,
+                                            ORC_TAG_SWAP, 0);
+                if (orc_swap_accept(x, r)) {
+                    orc_swap_slots(at, sa, sb);
+                    acc_B[sa] += 1;
+                }
+            }
+    }
+}
+
 int orc_pt2d_run(const orc_inst *in, int32_t I, const float *beta, int32_t J, const int32_t *P,
                  int32_t n_runs, const int32_t *run_ids, uint64_t seed, int64_t sweeps,
                  int32_t interval, orc_state *st)
@@ -326,38 +371,8 @@ int orc_pt2d_run(const orc_inst *in, int32_t I, const float *beta, int32_t J, co
             }
             const int64_t *fw = st->f + (int64_t)q * R;
             const int64_t *gw = st->g + (int64_t)q * R;
-            if (st->counters[2] == 1) {
-                /* swaps along P: each row, pairs (p, p+1) for p = even, even+2, ... */
-                for (int32_t i = 0; i < I; ++i)
-                    for (int32_t p = even; p + 1 < J; p += 2) {
-                        const int32_t sa = i * J + p, sb = i * J + p + 1;
-                        const int64_t dP = (int64_t)P[p + 1] - (int64_t)P[p];
-                        const int64_t dg = gw[at[sb]] - gw[at[sa]];
-                        const float x = beta[i] * (float)(dP * dg);
-                        const uint32_t r = orc_word(seed, (uint32_t)sa, (uint32_t)nev, 0u, run,
-                                                    ORC_TAG_SWAP, 0);
-                        if (orc_swap_accept(x, r)) {
-                            orc_swap_slots(at, sa, sb);
-                            st->acc_P[(int64_t)q * R + sa] += 1;
-                        }
-                    }
-            } else {
-                /* swaps along beta: each column, pairs (b, b+1) for b = even, even+2, ... */
-                for (int32_t j = 0; j < J; ++j)
-                    for (int32_t b = even; b + 1 < I; b += 2) {
-                        const int32_t sa = b * J + j, sb = (b + 1) * J + j;
-                        const float dbeta = beta[b + 1] - beta[b];
-                        const int64_t Ea = fw[at[sa]] + (int64_t)P[j] * gw[at[sa]];
-                        const int64_t Eb = fw[at[sb]] + (int64_t)P[j] * gw[at[sb]];
-                        const float x = dbeta * (float)(Eb - Ea);
-                        const uint32_t r = orc_word(seed, (uint32_t)sa, (uint32_t)nev, 0u, run,
-                                                    ORC_TAG_SWAP, 0);
-                        if (orc_swap_accept(x, r)) {
-                            orc_swap_slots(at, sa, sb);
-                            st->acc_B[(int64_t)q * R + sa] += 1;
-                        }
-                    }
-            }
+            orc_swap_event(I, beta, J, P, fw, gw, at, seed, run, nev, (int)st->counters[2],
+                           st->acc_P + (int64_t)q * R, st->acc_B + (int64_t)q * R);
             /* store spins from the last replica (bottom-right slot) */
             const int32_t wl = at[R - 1];
             const int64_t fl = fw[wl], gl = gw[wl];
@@ -424,4 +439,26 @@ void orc_pt_exp_constants(float out[11])
     out[1] = ORC_LN2_HI;
     out[2] = ORC_LN2_LO;
     for (int i = 0; i < 8; ++i) out[3 + i] = ORC_C[i];
+}
+
+/* Element-wise forms for comparing long input lists with another implementation. */
+void orc_pt_exp_array(const float *x, float *y, int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i) y[i] = orc_pt_exp(x[i]);
+}
+
+void orc_heatbath_array(const float *beta, const int32_t *H, const uint32_t *r, int8_t *s,
+                        int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i) s[i] = (int8_t)orc_heatbath(beta[i], H[i], r[i]);
+}
+
+void orc_swap_accept_array(const float *x, const uint32_t *r, int8_t *a, int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i) a[i] = (int8_t)orc_swap_accept(x[i], r[i]);
+}
+
+void orc_philox_array(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i) orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
 }

@@ -1,0 +1,259 @@
+"""GB300-native two-dimensional parallel tempering (arxiv 2506.14781).
+
+Python face of the C ABI in include/pt2d.h.  Every step of the method runs in
+the CUDA library libpt2d.so; this module only marshals arguments.  PyTorch,
+when used, only provides device memory (the context workspace) and the CUDA
+stream.  Importing works without a GPU; creating a context needs one.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ACC_B, ACC_P, BEST_EVENT, BEST_F, BEST_STATE, COLORS, COUNTERS, F, G,
+                   N_FEASIBLE, SOLVED_EVENT, STATES, SUM_F, SUM_G, TARGET, TRACE_F, TRACE_G,
+                   WALKER_AT, Pt2dError)
+
+__all__ = [
+    "PhysicalInstance", "sparsify", "greedy_color", "PT2D", "Pt2dError", "diag_philox",
+    "diag_pt_exp", "diag_heatbath", "diag_swap_accept", "STATES", "WALKER_AT", "F", "G",
+    "COUNTERS", "TRACE_F", "TRACE_G", "BEST_F", "BEST_EVENT", "BEST_STATE", "SOLVED_EVENT",
+    "ACC_P", "ACC_B", "SUM_F", "SUM_G", "N_FEASIBLE", "COLORS", "TARGET",
+]
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+@dataclasses.dataclass
+class PhysicalInstance:
+    """Sparsified (physical) constrained Ising instance: symmetric coupling CSR
+    with int16 values and symmetric copy-link CSR (see pt2d_instance)."""
+    n: int
+    cp_ptr: np.ndarray
+    cp_col: np.ndarray
+    cp_J: np.ndarray
+    lk_ptr: np.ndarray
+    lk_col: np.ndarray
+    h: np.ndarray | None = None
+    color: np.ndarray | None = None
+    copy_of: np.ndarray | None = None
+
+    def __post_init__(self):
+        self.cp_ptr = np.ascontiguousarray(self.cp_ptr, dtype=np.int32)
+        self.cp_col = np.ascontiguousarray(self.cp_col, dtype=np.int32)
+        self.cp_J = np.ascontiguousarray(self.cp_J, dtype=np.int16)
+        self.lk_ptr = np.ascontiguousarray(self.lk_ptr, dtype=np.int32)
+        self.lk_col = np.ascontiguousarray(self.lk_col, dtype=np.int32)
+        if self.h is not None:
+            self.h = np.ascontiguousarray(self.h, dtype=np.int32)
+        if self.color is not None:
+            self.color = np.ascontiguousarray(self.color, dtype=np.int32)
+
+    def c_struct(self) -> _lib.Instance:
+        return _lib.Instance(int(self.n), _p(self.cp_ptr), _p(self.cp_col), _p(self.cp_J),
+                             _p(self.lk_ptr), _p(self.lk_col), _p(self.h), _p(self.color))
+
+
+_RULES = {"fixed": _lib.SPARSIFY_FIXED, "max_edges": _lib.SPARSIFY_MAX_EDGES,
+          "max_degree": _lib.SPARSIFY_MAX_DEGREE}
+
+
+def sparsify(Jq: np.ndarray, rule: str, param: int) -> PhysicalInstance:
+    """Copy-chain sparsification (pt2d_sparsify) of a dense int16 logical matrix."""
+    Jq = np.ascontiguousarray(Jq, dtype=np.int16)
+    N = Jq.shape[0]
+    L = _lib.lib()
+    n = C.c_int32()
+    ncp = C.c_int64()
+    nlk = C.c_int64()
+    st = L.pt2d_sparsify(N, _p(Jq), _RULES[rule], int(param), C.byref(n), C.byref(ncp),
+                         C.byref(nlk), None, None, None, None, None, None)
+    _lib.check(st, "pt2d_sparsify")
+    cp_ptr = np.zeros(n.value + 1, np.int32)
+    cp_col = np.zeros(max(ncp.value, 1), np.int32)
+    cp_J = np.zeros(max(ncp.value, 1), np.int16)
+    lk_ptr = np.zeros(n.value + 1, np.int32)
+    lk_col = np.zeros(max(nlk.value, 1), np.int32)
+    copy_of = np.zeros(n.value, np.int32)
+    st = L.pt2d_sparsify(N, _p(Jq), _RULES[rule], int(param), C.byref(n), C.byref(ncp),
+                         C.byref(nlk), _p(cp_ptr), _p(cp_col), _p(cp_J), _p(lk_ptr), _p(lk_col),
+                         _p(copy_of))
+    _lib.check(st, "pt2d_sparsify")
+    return PhysicalInstance(n.value, cp_ptr, cp_col[:ncp.value], cp_J[:ncp.value], lk_ptr,
+                            lk_col[:nlk.value], copy_of=copy_of)
+
+
+def greedy_color(inst: PhysicalInstance):
+    """Greedy colouring (pt2d_greedy_color): (colour array, number of colours)."""
+    color = np.zeros(inst.n, np.int32)
+    nc = C.c_int32()
+    cs = inst.c_struct()
+    _lib.check(_lib.lib().pt2d_greedy_color(C.byref(cs), _p(color), C.byref(nc)),
+               "pt2d_greedy_color")
+    return color, nc.value
+
+
+class PT2D:
+    """One 2D-PT context: `runs` independent I x J replica grids on one instance.
+
+    workspace: "library" (the library allocates device memory with cudaMalloc),
+    or "torch" (a torch uint8 CUDA tensor owned by this object provides it).
+    stream: a torch.cuda.Stream, a raw cudaStream_t (int), or None (default stream).
+    """
+
+    def __init__(self, inst: PhysicalInstance, beta, P, runs: int, *, stream=None,
+                 workspace: str = "library", trace_capacity: int = 1024,
+                 walkers_per_cta: int = 0, threads_per_cta: int = 0, device: int = -1,
+                 profile: bool = False):
+        self.inst = inst
+        self.beta = np.ascontiguousarray(beta, dtype=np.float32)
+        self.P = np.ascontiguousarray(P, dtype=np.int32)
+        self.I, self.J = int(self.beta.size), int(self.P.size)
+        self.R = self.I * self.J
+        self.runs = int(runs)
+        self.n = int(inst.n)
+        self.trace_capacity = int(trace_capacity)
+        L = _lib.lib()
+        opt = _lib.Options()
+        L.pt2d_default_options(C.byref(opt))
+        opt.trace_capacity = int(trace_capacity)
+        opt.walkers_per_cta = int(walkers_per_cta)
+        opt.threads_per_cta = int(threads_per_cta)
+        opt.device = int(device)
+        opt.profile = 1 if profile else 0
+        self._stream_obj = stream
+        if stream is not None:
+            opt.stream = int(getattr(stream, "cuda_stream", stream))
+        self._cs = inst.c_struct()
+        self._ws = None
+        if workspace == "torch":
+            import torch
+
+            need = C.c_size_t()
+            _lib.check(L.pt2d_workspace_size(C.byref(self._cs), self.I, self.J, self.runs,
+                                             C.byref(opt), C.byref(need)), "pt2d_workspace_size")
+            dev = torch.device("cuda", device if device >= 0 else torch.cuda.current_device())
+            self._ws = torch.empty(need.value, dtype=torch.uint8, device=dev)
+            opt.workspace = self._ws.data_ptr()
+            opt.workspace_bytes = need.value
+        elif workspace != "library":
+            raise ValueError("workspace must be 'library' or 'torch'")
+        self._ctx = C.c_void_p()
+        st = L.pt2d_create(C.byref(self._ctx), C.byref(self._cs), self.I, _p(self.beta), self.J,
+                           _p(self.P), self.runs, C.byref(opt))
+        _lib.check(st, "pt2d_create")
+
+    # shapes and dtypes of the readable arrays
+    def _spec(self, what):
+        q, R, n, T = self.runs, self.R, self.n, self.trace_capacity
+        return {
+            STATES: ((q, R, n), np.int8), WALKER_AT: ((q, R), np.int32), F: ((q, R), np.int64),
+            G: ((q, R), np.int64), COUNTERS: ((4,), np.int64), TRACE_F: ((q, T), np.int64),
+            TRACE_G: ((q, T), np.int64), BEST_F: ((q,), np.int64), BEST_EVENT: ((q,), np.int64),
+            BEST_STATE: ((q, n), np.int8), SOLVED_EVENT: ((q,), np.int64),
+            ACC_P: ((q, R), np.int64), ACC_B: ((q, R), np.int64), SUM_F: ((q, R), np.int64),
+            SUM_G: ((q, R), np.int64), N_FEASIBLE: ((q, R), np.int64), COLORS: ((n,), np.int32),
+            TARGET: ((q,), np.int64),
+        }[what]
+
+    def run(self, sweeps: int, swap_interval: int, seed: int) -> None:
+        _lib.check(_lib.lib().pt2d_run(self._ctx, int(sweeps), int(swap_interval), int(seed)),
+                   "pt2d_run", self._ctx)
+
+    def read(self, what: int) -> np.ndarray:
+        shape, dt = self._spec(what)
+        out = np.empty(shape, dtype=dt)
+        _lib.check(_lib.lib().pt2d_read(self._ctx, what, _p(out), out.nbytes), "pt2d_read",
+                   self._ctx)
+        return out
+
+    def read_walker(self, run: int, walker: int) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.int8)
+        _lib.check(_lib.lib().pt2d_read_walker(self._ctx, int(run), int(walker), _p(out)),
+                   "pt2d_read_walker", self._ctx)
+        return out
+
+    def write(self, what: int, arr) -> None:
+        shape, dt = self._spec(what)
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(arr, dtype=dt), shape))
+        _lib.check(_lib.lib().pt2d_write(self._ctx, what, _p(a), a.nbytes), "pt2d_write",
+                   self._ctx)
+
+    def sync(self) -> None:
+        _lib.check(_lib.lib().pt2d_sync(self._ctx), "pt2d_sync", self._ctx)
+
+    def kernel_time(self, kind: int) -> tuple[float, int]:
+        """(total device ms, launches) of kind 0 = sweep kernel, 1 = swap kernel."""
+        ms = C.c_double()
+        cnt = C.c_int64()
+        _lib.check(_lib.lib().pt2d_kernel_time(self._ctx, int(kind), C.byref(ms), C.byref(cnt)),
+                   "pt2d_kernel_time", self._ctx)
+        return ms.value, cnt.value
+
+    @property
+    def num_colors(self) -> int:
+        return int(_lib.lib().pt2d_num_colors(self._ctx))
+
+    @property
+    def launch_count(self) -> int:
+        return int(_lib.lib().pt2d_launch_count(self._ctx))
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            _lib.lib().pt2d_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _diag(name, arrays, outs, count):
+    st = getattr(_lib.lib(), name)(*[_p(a) for a in arrays], *[_p(o) for o in outs], int(count))
+    _lib.check(st, name)
+
+
+def diag_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.empty_like(ctr)
+    _diag("pt2d_diag_philox", [ctr, key], [out], ctr.shape[0])
+    return out
+
+
+def diag_pt_exp(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    _diag("pt2d_diag_pt_exp", [x], [y], x.size)
+    return y
+
+
+def diag_heatbath(beta, H, r) -> np.ndarray:
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    H = np.ascontiguousarray(H, dtype=np.int32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    out = np.empty(beta.size, np.int8)
+    _diag("pt2d_diag_heatbath", [beta, H, r], [out], beta.size)
+    return out
+
+
+def diag_swap_accept(x, r) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    out = np.empty(x.size, np.int8)
+    _diag("pt2d_diag_swap_accept", [x, r], [out], x.size)
+    return out

@@ -1,0 +1,120 @@
+"""ctypes binding of libpt2d.so: the C ABI of include/pt2d.h, argument
+marshalling only.  Raises if the library has not been built (there is no
+fallback implementation)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpt2d.so")
+
+PT2D_OK = 0
+ERRORS = {
+    -1: "PT2D_ERR_INVALID_ARG",
+    -2: "PT2D_ERR_OOM",
+    -3: "PT2D_ERR_CUDA",
+    -4: "PT2D_ERR_TIMEOUT",
+    -5: "PT2D_ERR_STATE",
+    -6: "PT2D_ERR_UNSUPPORTED",
+}
+
+# readable / writable arrays
+STATES, WALKER_AT, F, G, COUNTERS, TRACE_F, TRACE_G, BEST_F, BEST_EVENT, BEST_STATE, \
+    SOLVED_EVENT, ACC_P, ACC_B, SUM_F, SUM_G, N_FEASIBLE, COLORS, TARGET = range(1, 19)
+
+SPARSIFY_FIXED, SPARSIFY_MAX_EDGES, SPARSIFY_MAX_DEGREE = 0, 1, 2
+
+EXPORTS = [
+    "pt2d_default_options", "pt2d_workspace_size", "pt2d_create", "pt2d_run", "pt2d_read",
+    "pt2d_read_walker",
+    "pt2d_write", "pt2d_array_bytes", "pt2d_sync", "pt2d_num_colors", "pt2d_launch_count",
+    "pt2d_destroy", "pt2d_strerror", "pt2d_cuda_error", "pt2d_sparsify", "pt2d_greedy_color",
+    "pt2d_diag_philox", "pt2d_diag_pt_exp", "pt2d_diag_heatbath", "pt2d_diag_swap_accept",
+    "pt2d_kernel_time",
+]
+
+
+class Instance(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32),
+        ("cp_ptr", C.c_void_p),
+        ("cp_col", C.c_void_p),
+        ("cp_J", C.c_void_p),
+        ("lk_ptr", C.c_void_p),
+        ("lk_col", C.c_void_p),
+        ("h", C.c_void_p),
+        ("color", C.c_void_p),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("stream", C.c_void_p),
+        ("workspace", C.c_void_p),
+        ("workspace_bytes", C.c_size_t),
+        ("trace_capacity", C.c_int32),
+        ("walkers_per_cta", C.c_int32),
+        ("threads_per_cta", C.c_int32),
+        ("device", C.c_int32),
+        ("profile", C.c_int32),
+    ]
+
+
+class Pt2dError(RuntimeError):
+    def __init__(self, status: int, what: str, cuda_error: int = 0):
+        self.status = status
+        msg = f"{what}: {ERRORS.get(status, status)} ({lib().pt2d_strerror(status).decode()})"
+        if cuda_error:
+            msg += f" [cudaError {cuda_error}]"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it first (python -c 'import "
+                              f"__graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+        L.pt2d_default_options.argtypes = [vp]
+        L.pt2d_default_options.restype = None
+        L.pt2d_workspace_size.argtypes = [vp, i32, i32, i32, vp, C.POINTER(sz)]
+        L.pt2d_create.argtypes = [C.POINTER(vp), vp, i32, vp, i32, vp, i32, vp]
+        L.pt2d_run.argtypes = [vp, i64, i32, C.c_uint64]
+        L.pt2d_read.argtypes = [vp, i32, vp, sz]
+        L.pt2d_write.argtypes = [vp, i32, vp, sz]
+        L.pt2d_read_walker.argtypes = [vp, i32, i32, vp]
+        L.pt2d_array_bytes.argtypes = [vp, i32]
+        L.pt2d_array_bytes.restype = sz
+        L.pt2d_sync.argtypes = [vp]
+        L.pt2d_num_colors.argtypes = [vp]
+        L.pt2d_launch_count.argtypes = [vp]
+        L.pt2d_launch_count.restype = i64
+        L.pt2d_destroy.argtypes = [vp]
+        L.pt2d_destroy.restype = None
+        L.pt2d_strerror.argtypes = [C.c_int]
+        L.pt2d_strerror.restype = C.c_char_p
+        L.pt2d_cuda_error.argtypes = [vp]
+        L.pt2d_sparsify.argtypes = [i32, vp, i32, i32, C.POINTER(i32), C.POINTER(i64),
+                                    C.POINTER(i64), vp, vp, vp, vp, vp, vp]
+        L.pt2d_greedy_color.argtypes = [vp, vp, C.POINTER(i32)]
+        L.pt2d_diag_philox.argtypes = [vp, vp, vp, i64]
+        L.pt2d_diag_pt_exp.argtypes = [vp, vp, i64]
+        L.pt2d_diag_heatbath.argtypes = [vp, vp, vp, vp, i64]
+        L.pt2d_diag_swap_accept.argtypes = [vp, vp, vp, i64]
+        L.pt2d_kernel_time.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]
+        for name in EXPORTS:
+            getattr(L, name)  # every declared entry point must be exported
+        _lib = L
+    return _lib
+
+
+def check(status: int, what: str, ctx=None) -> None:
+    if status != PT2D_OK:
+        cuda_err = lib().pt2d_cuda_error(ctx) if ctx else 0
+        raise Pt2dError(status, what, cuda_err)

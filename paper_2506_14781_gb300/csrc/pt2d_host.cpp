@@ -1,0 +1,882 @@
+// Host side of the 2D-PT C ABI (include/pt2d.h): validation, greedy colouring,
+// device layout, the Algorithm 1 event loop and the read/write interface.
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pt2d.h"
+#include "pt2d_internal.h"
+
+namespace {
+
+constexpr int64_t kHBound = int64_t(1) << 24;  // |H| must stay exact in float32
+constexpr int64_t kMaxSlots = 8192;             // I * J per run
+
+struct Prep {
+    int32_t n = 0, I = 0, J = 0, R = 0, Rp = 0, runs = 0, C = 0, DC = 0, DL = 0;
+    int64_t Wc = 0;
+    int32_t trace_cap = 0;
+    pt2d::SweepTiling tiling{};
+    std::vector<int32_t> color, pid, pos_of, cofs, nb, jv, lk, h2;
+};
+
+// Sum of sizes with 256-byte alignment; two passes (size, then assignment).
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(int64_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += sizeof(T) * static_cast<size_t>(count > 0 ? count : 1);
+        return p;
+    }
+};
+
+// Validates a symmetric CSR (no self loops, no duplicates, equal values both
+// ways; `val` may be NULL for unweighted links) and returns sorted adjacency.
+int check_csr(int32_t n, const int32_t *ptr, const int32_t *col, const int16_t *val,
+              std::vector<std::vector<std::pair<int32_t, int32_t>>> *adj) {
+    if (!ptr) return PT2D_ERR_INVALID_ARG;
+    if (ptr[0] != 0) return PT2D_ERR_INVALID_ARG;
+    for (int32_t a = 0; a < n; ++a)
+        if (ptr[a + 1] < ptr[a]) return PT2D_ERR_INVALID_ARG;
+    if (ptr[n] > 0 && !col) return PT2D_ERR_INVALID_ARG;
+    adj->assign(n, {});
+    for (int32_t a = 0; a < n; ++a) {
+        for (int32_t k = ptr[a]; k < ptr[a + 1]; ++k) {
+            const int32_t b = col[k];
+            if (b < 0 || b >= n || b == a) return PT2D_ERR_INVALID_ARG;
+            (*adj)[a].push_back({b, val ? static_cast<int32_t>(val[k]) : 0});
+        }
+        auto &v = (*adj)[a];
+        std::sort(v.begin(), v.end());
+        for (size_t i = 1; i < v.size(); ++i)
+            if (v[i].first == v[i - 1].first) return PT2D_ERR_INVALID_ARG;  // duplicate edge
+    }
+    // symmetry with equal values
+    for (int32_t a = 0; a < n; ++a)
+        for (const auto &e : (*adj)[a]) {
+            const auto &w = (*adj)[e.first];
+            auto it = std::lower_bound(w.begin(), w.end(), std::make_pair(a, INT32_MIN));
+            if (it == w.end() || it->first != a || it->second != e.second) return PT2D_ERR_INVALID_ARG;
+        }
+    return PT2D_OK;
+}
+
+int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, const int32_t *P,
+            int32_t runs, const pt2d_options *opt, Prep &pp) {
+    if (!inst || inst->n < 1 || I < 1 || J < 1 || runs < 1) return PT2D_ERR_INVALID_ARG;
+    // the swap kernel keeps one run's slot -> walker map in shared memory
+    if (static_cast<int64_t>(I) * J > kMaxSlots) return PT2D_ERR_INVALID_ARG;
+    if (runs >= (1 << 27)) return PT2D_ERR_INVALID_ARG;
+    const int32_t n = inst->n;
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> cadj, ladj;
+    if (!inst->cp_ptr || !inst->lk_ptr) return PT2D_ERR_INVALID_ARG;
+    if (inst->cp_ptr[n] > 0 && !inst->cp_J) return PT2D_ERR_INVALID_ARG;
+    int st = check_csr(n, inst->cp_ptr, inst->cp_col, inst->cp_J, &cadj);
+    if (st) return st;
+    st = check_csr(n, inst->lk_ptr, inst->lk_col, nullptr, &ladj);
+    if (st) return st;
+    // ladders: beta >= 0 finite and ascending, P >= 0 ascending
+    if (beta) {
+        for (int32_t i = 0; i < I; ++i) {
+            if (!(beta[i] >= 0.0f) || !(beta[i] < 3.0e38f)) return PT2D_ERR_INVALID_ARG;
+            if (i > 0 && beta[i] < beta[i - 1]) return PT2D_ERR_INVALID_ARG;
+        }
+    }
+    int64_t Pmax = 0;
+    if (P) {
+        for (int32_t j = 0; j < J; ++j) {
+            if (P[j] < 0) return PT2D_ERR_INVALID_ARG;
+            if (j > 0 && P[j] < P[j - 1]) return PT2D_ERR_INVALID_ARG;
+            Pmax = std::max<int64_t>(Pmax, P[j]);
+        }
+    }
+    // local-field bound |H_a| < 2^24
+    for (int32_t a = 0; a < n; ++a) {
+        int64_t b = 0;
+        for (const auto &e : cadj[a]) b += 2 * std::abs(static_cast<int64_t>(e.second));
+        if (inst->h) b += 2 * std::abs(static_cast<int64_t>(inst->h[a]));
+        b += Pmax * static_cast<int64_t>(ladj[a].size());
+        if (b >= kHBound) return PT2D_ERR_INVALID_ARG;
+    }
+    // colouring: given (must be proper) or greedy over couplings and links
+    pp.color.assign(n, -1);
+    if (inst->color) {
+        for (int32_t a = 0; a < n; ++a) {
+            if (inst->color[a] < 0 || inst->color[a] >= 4096) return PT2D_ERR_INVALID_ARG;
+            pp.color[a] = inst->color[a];
+        }
+        for (int32_t a = 0; a < n; ++a) {
+            for (const auto &e : cadj[a])
+                if (pp.color[e.first] == pp.color[a]) return PT2D_ERR_INVALID_ARG;
+            for (const auto &e : ladj[a])
+                if (pp.color[e.first] == pp.color[a]) return PT2D_ERR_INVALID_ARG;
+        }
+    } else {
+        std::vector<char> used;
+        for (int32_t a = 0; a < n; ++a) {
+            used.assign(cadj[a].size() + ladj[a].size() + 2, 0);
+            for (const auto &e : cadj[a])
+                if (e.first < a && pp.color[e.first] < static_cast<int32_t>(used.size()))
+                    used[pp.color[e.first]] = 1;
+            for (const auto &e : ladj[a])
+                if (e.first < a && pp.color[e.first] < static_cast<int32_t>(used.size()))
+                    used[pp.color[e.first]] = 1;
+            int32_t c = 0;
+            while (used[c]) ++c;
+            pp.color[a] = c;
+        }
+    }
+    int32_t C = 0;
+    for (int32_t a = 0; a < n; ++a) C = std::max(C, pp.color[a] + 1);
+    // positions: spins sorted by (colour, id)
+    pp.cofs.assign(C + 1, 0);
+    for (int32_t a = 0; a < n; ++a) pp.cofs[pp.color[a] + 1]++;
+    for (int32_t c = 0; c < C; ++c) pp.cofs[c + 1] += pp.cofs[c];
+    pp.pid.assign(n, 0);
+    pp.pos_of.assign(n, 0);
+    {
+        std::vector<int32_t> fill(pp.cofs.begin(), pp.cofs.end() - 1);
+        for (int32_t a = 0; a < n; ++a) {
+            const int32_t p = fill[pp.color[a]]++;
+            pp.pid[p] = a;
+            pp.pos_of[a] = p;
+        }
+    }
+    // padded degrees
+    int32_t dcmax = 0, dlmax = 0;
+    for (int32_t a = 0; a < n; ++a) {
+        dcmax = std::max<int32_t>(dcmax, static_cast<int32_t>(cadj[a].size()));
+        dlmax = std::max<int32_t>(dlmax, static_cast<int32_t>(ladj[a].size()));
+    }
+    int32_t DC, DL;
+    if (dlmax <= 2 && dcmax <= 6) {
+        DL = 2;
+        DC = dcmax <= 3 ? 3 : (dcmax <= 4 ? 4 : 6);
+    } else {
+        DC = std::max(dcmax, 1);
+        DL = std::max(dlmax, 1);
+    }
+    pp.nb.assign(static_cast<size_t>(n) * DC, n);
+    pp.jv.assign(static_cast<size_t>(n) * DC, 0);
+    pp.lk.assign(static_cast<size_t>(n) * DL, n);
+    pp.h2.assign(n, 0);
+    for (int32_t p = 0; p < n; ++p) {
+        const int32_t a = pp.pid[p];
+        for (size_t k = 0; k < cadj[a].size(); ++k) {
+            pp.nb[static_cast<size_t>(p) * DC + k] = pp.pos_of[cadj[a][k].first];
+            pp.jv[static_cast<size_t>(p) * DC + k] = 2 * cadj[a][k].second;
+        }
+        for (size_t k = 0; k < ladj[a].size(); ++k)
+            pp.lk[static_cast<size_t>(p) * DL + k] = pp.pos_of[ladj[a][k].first];
+        pp.h2[p] = inst->h ? 2 * inst->h[a] : 0;
+    }
+    pp.n = n;
+    pp.I = I;
+    pp.J = J;
+    pp.R = I * J;
+    pp.Rp = (pp.R + 3) / 4 * 4;
+    pp.runs = runs;
+    pp.C = C;
+    pp.DC = DC;
+    pp.DL = DL;
+    pp.trace_cap = opt ? std::max<int32_t>(opt->trace_capacity, 0) : 1024;
+    // sweep tiling: quads per spin-row segment of a CTA and threads per CTA
+    const int64_t quads = static_cast<int64_t>(runs) * pp.Rp / 4;
+    int ql;
+    if (opt && opt->walkers_per_cta > 0) {
+        const int w = opt->walkers_per_cta;
+        if (w < 4 || w > 128 || (w & (w - 1))) return PT2D_ERR_INVALID_ARG;
+        ql = w / 4;
+    } else {
+        int sms = 152;
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            int v = 0;
+            if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+                sms = v;
+        }
+        ql = 32;
+        while (ql > 1 && (quads + ql - 1) / ql < 2LL * sms) ql /= 2;
+    }
+    int threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta : 256;
+    if (threads < 32 || threads > 256 || threads % 32) return PT2D_ERR_INVALID_ARG;
+    if (threads < ql) return PT2D_ERR_INVALID_ARG;
+    pp.tiling.lanes_per_spin = ql;
+    pp.tiling.threads = threads;
+    const int64_t slab = 4LL * ql;
+    pp.Wc = (static_cast<int64_t>(runs) * pp.Rp + slab - 1) / slab * slab;
+    return PT2D_OK;
+}
+
+}  // namespace
+
+struct pt2d_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_ws = false;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    Prep pp;
+    pt2d::Layout L{};
+    pt2d::Walkers wk{};
+    pt2d::RunState rs{};
+    float *d_beta = nullptr;
+    int32_t *d_P = nullptr;
+    int64_t *d_target = nullptr;
+    std::vector<float> beta;
+    std::vector<int32_t> P;
+    int64_t sweeps_done = 0, events_done = 0, dir = 1, inited = 0;
+    uint64_t seed = 0;
+    int64_t launches = 0;
+    int last_cuda = 0;
+    bool adopt_seed = false;  // initialised by a checkpoint restore: take the next run's seed
+    // kernel timing (opt.profile): pending event pairs per kernel kind, and totals
+    bool profile = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[2];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
+    double total_ms[2] = {0.0, 0.0};
+    int64_t timed_launches[2] = {0, 0};
+};
+
+namespace {
+
+size_t carve(pt2d_ctx *c, void *base) {
+    Prep &pp = c->pp;
+    Carver cv(base);
+    const int64_t n = pp.n, RR = static_cast<int64_t>(pp.runs) * pp.R;
+    c->L.S = cv.take<int8_t>((n + 1) * pp.Wc);
+    int32_t *pid = cv.take<int32_t>(n);
+    int32_t *cofs = cv.take<int32_t>(pp.C + 1);
+    int32_t *nb = cv.take<int32_t>(n * pp.DC);
+    int32_t *jv = cv.take<int32_t>(n * pp.DC);
+    int32_t *lk = cv.take<int32_t>(n * pp.DL);
+    int32_t *h2 = cv.take<int32_t>(n);
+    c->L.pid = pid;
+    c->L.cofs = cofs;
+    c->L.nb = nb;
+    c->L.jv = jv;
+    c->L.lk = lk;
+    c->L.h2 = h2;
+    c->wk.wbeta = cv.take<float>(pp.Wc);
+    c->wk.wP = cv.take<int32_t>(pp.Wc);
+    c->wk.f = cv.take<int64_t>(pp.Wc);
+    c->wk.g = cv.take<int32_t>(pp.Wc);
+    c->d_beta = cv.take<float>(pp.I);
+    c->d_P = cv.take<int32_t>(pp.J);
+    c->rs.walker_at = cv.take<int32_t>(RR);
+    c->rs.acc_P = cv.take<int64_t>(RR);
+    c->rs.acc_B = cv.take<int64_t>(RR);
+    c->rs.sum_f = cv.take<int64_t>(RR);
+    c->rs.sum_g = cv.take<int64_t>(RR);
+    c->rs.n_feasible = cv.take<int64_t>(RR);
+    c->rs.trace_f = cv.take<int64_t>(static_cast<int64_t>(pp.runs) * pp.trace_cap);
+    c->rs.trace_g = cv.take<int64_t>(static_cast<int64_t>(pp.runs) * pp.trace_cap);
+    c->rs.best_f = cv.take<int64_t>(pp.runs);
+    c->rs.best_event = cv.take<int64_t>(pp.runs);
+    c->rs.solved_event = cv.take<int64_t>(pp.runs);
+    c->d_target = cv.take<int64_t>(pp.runs);
+    c->rs.best_state = cv.take<int8_t>(static_cast<int64_t>(pp.runs) * n);
+    return cv.off + 256;
+}
+
+std::pair<cudaEvent_t, cudaEvent_t> take_events(pt2d_ctx *c) {
+    if (!c->spare.empty()) {
+        auto p = c->spare.back();
+        c->spare.pop_back();
+        return p;
+    }
+    std::pair<cudaEvent_t, cudaEvent_t> p{nullptr, nullptr};
+    cudaEventCreate(&p.first);
+    cudaEventCreate(&p.second);
+    return p;
+}
+
+// Fold finished event pairs into the totals (after a stream synchronisation).
+cudaError_t drain_events(pt2d_ctx *c) {
+    for (int k = 0; k < 2; ++k) {
+        for (auto &p : c->pending[k]) {
+            float ms = 0.0f;
+            cudaError_t e = cudaEventElapsedTime(&ms, p.first, p.second);
+            if (e != cudaSuccess) return e;
+            c->total_ms[k] += ms;
+            c->timed_launches[k] += 1;
+            c->spare.push_back(p);
+        }
+        c->pending[k].clear();
+    }
+    return cudaSuccess;
+}
+
+int cuda_fail(pt2d_ctx *c, cudaError_t e) {
+    if (c) c->last_cuda = static_cast<int>(e);
+    return PT2D_ERR_CUDA;
+}
+
+#define CK(ctx, expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e); \
+    } while (0)
+
+int check_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PT2D_ERR_UNSUPPORTED;
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess)
+        return PT2D_ERR_UNSUPPORTED;
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return PT2D_ERR_UNSUPPORTED;
+    return PT2D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pt2d_default_options(pt2d_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->trace_capacity = 1024;
+    opt->device = -1;
+}
+
+const char *pt2d_strerror(int status) {
+    switch (status) {
+        case PT2D_OK: return "ok";
+        case PT2D_ERR_INVALID_ARG: return "invalid argument";
+        case PT2D_ERR_OOM: return "out of memory";
+        case PT2D_ERR_CUDA: return "CUDA error";
+        case PT2D_ERR_TIMEOUT: return "device wait timed out";
+        case PT2D_ERR_STATE: return "invalid state for this call";
+        case PT2D_ERR_UNSUPPORTED: return "unsupported device (needs sm_103)";
+        default: return "unknown status";
+    }
+}
+
+int pt2d_workspace_size(const pt2d_instance *inst, int32_t I, int32_t J, int32_t runs,
+                        const pt2d_options *opt, size_t *bytes) {
+    if (!bytes) return PT2D_ERR_INVALID_ARG;
+    pt2d_ctx tmp;
+    int st = prepare(inst, I, nullptr, J, nullptr, runs, opt, tmp.pp);
+    if (st) return st;
+    *bytes = carve(&tmp, nullptr);
+    return PT2D_OK;
+}
+
+int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const float *beta, int32_t J,
+                const int32_t *P, int32_t runs, const pt2d_options *opt) {
+    if (!out || !beta || !P) return PT2D_ERR_INVALID_ARG;
+    *out = nullptr;
+    pt2d_options dflt;
+    pt2d_default_options(&dflt);
+    if (!opt) opt = &dflt;
+    if (opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return PT2D_ERR_UNSUPPORTED;
+    int st = check_device();
+    if (st) return st;
+    pt2d_ctx *c = new (std::nothrow) pt2d_ctx;
+    if (!c) return PT2D_ERR_OOM;
+    st = prepare(inst, I, beta, J, P, runs, opt, c->pp);
+    if (st) {
+        delete c;
+        return st;
+    }
+    cudaGetDevice(&c->device);
+    c->stream = static_cast<cudaStream_t>(opt->stream);
+    c->profile = opt->profile != 0;
+    const size_t need = carve(c, nullptr);
+    if (opt->workspace) {
+        if (opt->workspace_bytes < need || (reinterpret_cast<uintptr_t>(opt->workspace) & 255)) {
+            delete c;
+            return PT2D_ERR_INVALID_ARG;
+        }
+        c->ws = opt->workspace;
+        c->ws_bytes = opt->workspace_bytes;
+    } else {
+        if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return PT2D_ERR_OOM;
+        }
+        c->own_ws = true;
+        c->ws_bytes = need;
+    }
+    carve(c, c->ws);
+    Prep &pp = c->pp;
+    c->beta.assign(beta, beta + I);
+    c->P.assign(P, P + J);
+    c->L.Wc = pp.Wc;
+    c->L.n = pp.n;
+    c->L.C = pp.C;
+    c->L.DC = pp.DC;
+    c->L.DL = pp.DL;
+    c->rs.runs = pp.runs;
+    c->rs.I = pp.I;
+    c->rs.J = pp.J;
+    c->rs.R = pp.R;
+    c->rs.Rp = pp.Rp;
+    c->rs.beta = c->d_beta;
+    c->rs.P = c->d_P;
+    c->rs.trace_cap = pp.trace_cap;
+    c->rs.target = c->d_target;
+    cudaStream_t s = c->stream;
+    auto fail = [&](cudaError_t e) {
+        c->last_cuda = static_cast<int>(e);
+        pt2d_destroy(c);
+        return PT2D_ERR_CUDA;
+    };
+    cudaError_t e = cudaMemsetAsync(c->ws, 0, need - 256, s);
+    if (e != cudaSuccess) return fail(e);
+    const int64_t n = pp.n;
+    struct Up {
+        void *d;
+        const void *h;
+        size_t b;
+    } ups[] = {
+        {const_cast<int32_t *>(c->L.pid), pp.pid.data(), sizeof(int32_t) * n},
+        {const_cast<int32_t *>(c->L.cofs), pp.cofs.data(), sizeof(int32_t) * (pp.C + 1)},
+        {const_cast<int32_t *>(c->L.nb), pp.nb.data(), sizeof(int32_t) * n * pp.DC},
+        {const_cast<int32_t *>(c->L.jv), pp.jv.data(), sizeof(int32_t) * n * pp.DC},
+        {const_cast<int32_t *>(c->L.lk), pp.lk.data(), sizeof(int32_t) * n * pp.DL},
+        {const_cast<int32_t *>(c->L.h2), pp.h2.data(), sizeof(int32_t) * n},
+        {c->d_beta, c->beta.data(), sizeof(float) * I},
+        {c->d_P, c->P.data(), sizeof(int32_t) * J},
+    };
+    for (const auto &u : ups) {
+        if (u.b == 0) continue;
+        e = cudaMemcpyAsync(u.d, u.h, u.b, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return fail(e);
+    }
+    std::vector<int64_t> tgt(pp.runs, INT64_MIN);
+    e = cudaMemcpyAsync(c->d_target, tgt.data(), sizeof(int64_t) * pp.runs, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(e);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e);
+    *out = c;
+    return PT2D_OK;
+}
+
+void pt2d_destroy(pt2d_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    for (int k = 0; k < 2; ++k)
+        for (auto &p : c->pending[k]) c->spare.push_back(p);
+    for (auto &p : c->spare) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    delete c;
+}
+
+int pt2d_kernel_time(pt2d_ctx *c, int32_t kind, double *ms, int64_t *launches) {
+    if (!c || kind < 0 || kind > 1 || !ms || !launches) return PT2D_ERR_INVALID_ARG;
+    if (!c->profile) return PT2D_ERR_STATE;
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, drain_events(c));
+    *ms = c->total_ms[kind];
+    *launches = c->timed_launches[kind];
+    return PT2D_OK;
+}
+
+int pt2d_cuda_error(const pt2d_ctx *c) { return c ? c->last_cuda : 0; }
+int pt2d_num_colors(const pt2d_ctx *c) { return c ? c->pp.C : 0; }
+int64_t pt2d_launch_count(const pt2d_ctx *c) { return c ? c->launches : 0; }
+
+int pt2d_run(pt2d_ctx *c, int64_t sweeps, int32_t interval, uint64_t seed) {
+    if (!c || sweeps < 0 || interval < 1) return PT2D_ERR_INVALID_ARG;
+    const int64_t nev = sweeps / interval;
+    if (c->adopt_seed) {
+        c->seed = seed;
+        c->adopt_seed = false;
+    }
+    if (c->inited && seed != c->seed) return PT2D_ERR_INVALID_ARG;
+    if (c->sweeps_done + nev * interval > (int64_t(1) << 32)) return PT2D_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    if (!c->inited) {
+        c->seed = seed;
+        CK(c, pt2d::launch_init(c->L, c->rs, c->wk, seed, s));
+        c->launches += 2;
+        c->inited = 1;
+        c->dir = 1;
+        c->sweeps_done = 0;
+        c->events_done = 0;
+    }
+    for (int64_t e = 0; e < nev; ++e) {
+        const int64_t event = c->events_done + 1;
+        std::pair<cudaEvent_t, cudaEvent_t> ev[2];
+        if (c->profile) {
+            ev[0] = take_events(c);
+            ev[1] = take_events(c);
+            CK(c, cudaEventRecord(ev[0].first, s));
+        }
+        CK(c, pt2d::launch_sweeps(c->L, c->wk, c->pp.tiling, c->pp.Rp / 4, seed,
+                                  static_cast<uint32_t>(c->sweeps_done), interval, s));
+        if (c->profile) {
+            CK(c, cudaEventRecord(ev[0].second, s));
+            CK(c, cudaEventRecord(ev[1].first, s));
+        }
+        CK(c, pt2d::launch_swap_event(c->L, c->rs, c->wk, seed, event, s));
+        if (c->profile) {
+            CK(c, cudaEventRecord(ev[1].second, s));
+            c->pending[0].push_back(ev[0]);
+            c->pending[1].push_back(ev[1]);
+        }
+        c->launches += 2;
+        c->sweeps_done += interval;
+        c->events_done = event;
+        if (event % 2 == 0) c->dir = -c->dir;
+    }
+    return PT2D_OK;
+}
+
+int pt2d_sync(pt2d_ctx *c) {
+    if (!c) return PT2D_ERR_INVALID_ARG;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PT2D_OK;
+}
+
+size_t pt2d_array_bytes(const pt2d_ctx *c, int32_t what) {
+    if (!c) return 0;
+    const Prep &pp = c->pp;
+    const size_t RR = static_cast<size_t>(pp.runs) * pp.R;
+    switch (what) {
+        case PT2D_STATES: return RR * pp.n;
+        case PT2D_WALKER_AT: return RR * 4;
+        case PT2D_F:
+        case PT2D_G:
+        case PT2D_ACC_P:
+        case PT2D_ACC_B:
+        case PT2D_SUM_F:
+        case PT2D_SUM_G:
+        case PT2D_N_FEASIBLE: return RR * 8;
+        case PT2D_COUNTERS: return 4 * 8;
+        case PT2D_TRACE_F:
+        case PT2D_TRACE_G: return static_cast<size_t>(pp.runs) * pp.trace_cap * 8;
+        case PT2D_BEST_F:
+        case PT2D_BEST_EVENT:
+        case PT2D_SOLVED_EVENT:
+        case PT2D_TARGET: return static_cast<size_t>(pp.runs) * 8;
+        case PT2D_BEST_STATE: return static_cast<size_t>(pp.runs) * pp.n;
+        case PT2D_COLORS: return static_cast<size_t>(pp.n) * 4;
+        default: return 0;
+    }
+}
+
+static void *direct_ptr(pt2d_ctx *c, int32_t what) {
+    switch (what) {
+        case PT2D_WALKER_AT: return c->rs.walker_at;
+        case PT2D_ACC_P: return c->rs.acc_P;
+        case PT2D_ACC_B: return c->rs.acc_B;
+        case PT2D_SUM_F: return c->rs.sum_f;
+        case PT2D_SUM_G: return c->rs.sum_g;
+        case PT2D_N_FEASIBLE: return c->rs.n_feasible;
+        case PT2D_TRACE_F: return c->rs.trace_f;
+        case PT2D_TRACE_G: return c->rs.trace_g;
+        case PT2D_BEST_F: return c->rs.best_f;
+        case PT2D_BEST_EVENT: return c->rs.best_event;
+        case PT2D_SOLVED_EVENT: return c->rs.solved_event;
+        case PT2D_TARGET: return c->d_target;
+        case PT2D_BEST_STATE: return c->rs.best_state;
+        default: return nullptr;
+    }
+}
+
+int pt2d_read(pt2d_ctx *c, int32_t what, void *dst, size_t bytes) {
+    if (!c || !dst) return PT2D_ERR_INVALID_ARG;
+    const size_t need = pt2d_array_bytes(c, what);
+    if (need == 0 || bytes != need) return PT2D_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const Prep &pp = c->pp;
+    if (what == PT2D_COUNTERS) {
+        CK(c, cudaStreamSynchronize(s));
+        int64_t v[4] = {c->sweeps_done, c->events_done, c->dir, c->inited};
+        std::memcpy(dst, v, sizeof v);
+        return PT2D_OK;
+    }
+    if (what == PT2D_COLORS) {
+        std::memcpy(dst, pp.color.data(), need);
+        return PT2D_OK;
+    }
+    if (void *src = direct_ptr(c, what)) {
+        CK(c, cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, s));
+        CK(c, cudaStreamSynchronize(s));
+        return PT2D_OK;
+    }
+    if (what == PT2D_STATES) {
+        if (!c->inited) return PT2D_ERR_STATE;
+        std::vector<int8_t> tmp(static_cast<size_t>(pp.n) * pp.Wc);
+        CK(c, cudaMemcpyAsync(tmp.data(), c->L.S, tmp.size(), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaStreamSynchronize(s));
+        int8_t *o = static_cast<int8_t *>(dst);
+        for (int32_t r = 0; r < pp.runs; ++r)
+            for (int32_t w = 0; w < pp.R; ++w) {
+                int8_t *row = o + (static_cast<size_t>(r) * pp.R + w) * pp.n;
+                const size_t colw = static_cast<size_t>(r) * pp.Rp + w;
+                for (int32_t a = 0; a < pp.n; ++a)
+                    row[a] = tmp[static_cast<size_t>(pp.pos_of[a]) * pp.Wc + colw];
+            }
+        return PT2D_OK;
+    }
+    if (what == PT2D_F || what == PT2D_G) {
+        const size_t esz = what == PT2D_F ? 8 : 4;
+        std::vector<char> tmp(esz * pp.Wc);
+        const void *src = what == PT2D_F ? static_cast<void *>(c->wk.f) : static_cast<void *>(c->wk.g);
+        CK(c, cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaStreamSynchronize(s));
+        int64_t *o = static_cast<int64_t *>(dst);
+        for (int32_t r = 0; r < pp.runs; ++r)
+            for (int32_t w = 0; w < pp.R; ++w) {
+                const size_t colw = static_cast<size_t>(r) * pp.Rp + w;
+                if (esz == 8)
+                    o[static_cast<size_t>(r) * pp.R + w] = reinterpret_cast<int64_t *>(tmp.data())[colw];
+                else
+                    o[static_cast<size_t>(r) * pp.R + w] = reinterpret_cast<int32_t *>(tmp.data())[colw];
+            }
+        return PT2D_OK;
+    }
+    return PT2D_ERR_INVALID_ARG;
+}
+
+int pt2d_read_walker(pt2d_ctx *c, int32_t run, int32_t walker, int8_t *dst) {
+    if (!c || !dst) return PT2D_ERR_INVALID_ARG;
+    const Prep &pp = c->pp;
+    if (run < 0 || run >= pp.runs || walker < 0 || walker >= pp.R) return PT2D_ERR_INVALID_ARG;
+    if (!c->inited) return PT2D_ERR_STATE;
+    cudaSetDevice(c->device);
+    std::vector<int8_t> tmp(pp.n);
+    const int8_t *col = c->L.S + static_cast<int64_t>(run) * pp.Rp + walker;
+    CK(c, cudaMemcpy2DAsync(tmp.data(), 1, col, static_cast<size_t>(pp.Wc), 1, pp.n,
+                            cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int32_t a = 0; a < pp.n; ++a) dst[a] = tmp[pp.pos_of[a]];
+    return PT2D_OK;
+}
+
+int pt2d_write(pt2d_ctx *c, int32_t what, const void *src, size_t bytes) {
+    if (!c || !src) return PT2D_ERR_INVALID_ARG;
+    const size_t need = pt2d_array_bytes(c, what);
+    if (need == 0 || bytes != need || what == PT2D_COLORS || what == PT2D_F || what == PT2D_G)
+        return PT2D_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const Prep &pp = c->pp;
+    if (what == PT2D_COUNTERS) {
+        const int64_t *v = static_cast<const int64_t *>(src);
+        if (v[0] < 0 || v[1] < 0 || (v[2] != 1 && v[2] != -1) || v[0] > (int64_t(1) << 32))
+            return PT2D_ERR_INVALID_ARG;
+        CK(c, cudaStreamSynchronize(s));
+        c->sweeps_done = v[0];
+        c->events_done = v[1];
+        c->dir = v[2];
+        if (v[3] && !c->inited) {
+            c->inited = 1;
+            c->adopt_seed = true;
+        }
+        return PT2D_OK;
+    }
+    if (what == PT2D_WALKER_AT) {
+        const int32_t *at = static_cast<const int32_t *>(src);
+        std::vector<float> wb(pp.Wc, 0.0f);
+        std::vector<int32_t> wp(pp.Wc, 0);
+        for (int32_t r = 0; r < pp.runs; ++r) {
+            std::vector<char> seen(pp.R, 0);
+            for (int32_t sl = 0; sl < pp.R; ++sl) {
+                const int32_t w = at[static_cast<size_t>(r) * pp.R + sl];
+                if (w < 0 || w >= pp.R || seen[w]) return PT2D_ERR_INVALID_ARG;
+                seen[w] = 1;
+                const size_t colw = static_cast<size_t>(r) * pp.Rp + w;
+                wb[colw] = c->beta[sl / pp.J];
+                wp[colw] = c->P[sl % pp.J];
+            }
+        }
+        CK(c, cudaMemcpyAsync(c->rs.walker_at, at, need, cudaMemcpyHostToDevice, s));
+        CK(c, cudaMemcpyAsync(c->wk.wbeta, wb.data(), sizeof(float) * pp.Wc, cudaMemcpyHostToDevice, s));
+        CK(c, cudaMemcpyAsync(c->wk.wP, wp.data(), sizeof(int32_t) * pp.Wc, cudaMemcpyHostToDevice, s));
+        CK(c, cudaStreamSynchronize(s));
+        return PT2D_OK;
+    }
+    if (void *dstp = direct_ptr(c, what)) {
+        CK(c, cudaMemcpyAsync(dstp, src, need, cudaMemcpyHostToDevice, s));
+        CK(c, cudaStreamSynchronize(s));
+        return PT2D_OK;
+    }
+    if (what == PT2D_STATES) {
+        const int8_t *in = static_cast<const int8_t *>(src);
+        std::vector<int8_t> tmp(static_cast<size_t>(pp.n) * pp.Wc, 1);
+        for (int32_t r = 0; r < pp.runs; ++r)
+            for (int32_t w = 0; w < pp.R; ++w) {
+                const int8_t *row = in + (static_cast<size_t>(r) * pp.R + w) * pp.n;
+                const size_t colw = static_cast<size_t>(r) * pp.Rp + w;
+                for (int32_t a = 0; a < pp.n; ++a) {
+                    if (row[a] != 1 && row[a] != -1) return PT2D_ERR_INVALID_ARG;
+                    tmp[static_cast<size_t>(pp.pos_of[a]) * pp.Wc + colw] = row[a];
+                }
+            }
+        CK(c, cudaMemcpyAsync(c->L.S, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, s));
+        CK(c, cudaStreamSynchronize(s));
+        return PT2D_OK;
+    }
+    return PT2D_ERR_INVALID_ARG;
+}
+
+// ---- host-side compiler helpers ------------------------------------------------
+int pt2d_greedy_color(const pt2d_instance *inst, int32_t *color, int32_t *n_colors) {
+    if (!inst || !color || !n_colors) return PT2D_ERR_INVALID_ARG;
+    Prep pp;
+    pt2d_instance tmp = *inst;
+    tmp.color = nullptr;
+    pt2d_options o;
+    pt2d_default_options(&o);
+    o.walkers_per_cta = 4;
+    o.threads_per_cta = 32;
+    int st = prepare(&tmp, 1, nullptr, 1, nullptr, 1, &o, pp);
+    if (st) return st;
+    std::memcpy(color, pp.color.data(), sizeof(int32_t) * pp.n);
+    *n_colors = pp.C;
+    return PT2D_OK;
+}
+
+int pt2d_sparsify(int32_t N, const int16_t *Jq, int32_t rule, int32_t param, int32_t *n_out,
+                  int64_t *nnz_cp, int64_t *nnz_lk, int32_t *cp_ptr, int32_t *cp_col, int16_t *cp_J,
+                  int32_t *lk_ptr, int32_t *lk_col, int32_t *copy_of) {
+    if (N < 1 || !Jq || !n_out || !nnz_cp || !nnz_lk) return PT2D_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < N; ++i) {
+        if (Jq[static_cast<size_t>(i) * N + i] != 0) return PT2D_ERR_INVALID_ARG;
+        for (int32_t j = 0; j < i; ++j)
+            if (Jq[static_cast<size_t>(i) * N + j] != Jq[static_cast<size_t>(j) * N + i])
+                return PT2D_ERR_INVALID_ARG;
+    }
+    // copies per logical node and the edge capacity of each copy (-1 = unbounded)
+    std::vector<int32_t> K(N), off(N + 1, 0);
+    std::vector<std::vector<int32_t>> nbrs(N);
+    for (int32_t i = 0; i < N; ++i)
+        for (int32_t j = 0; j < N; ++j)
+            if (j != i && Jq[static_cast<size_t>(i) * N + j] != 0) nbrs[i].push_back(j);
+    std::vector<std::vector<int32_t>> cap(N);
+    for (int32_t i = 0; i < N; ++i) {
+        const int32_t d = static_cast<int32_t>(nbrs[i].size());
+        if (rule == PT2D_SPARSIFY_FIXED) {
+            if (param < 1) return PT2D_ERR_INVALID_ARG;
+            K[i] = param;
+            cap[i].assign(K[i], -1);
+        } else if (rule == PT2D_SPARSIFY_MAX_EDGES) {
+            if (param < 1) return PT2D_ERR_INVALID_ARG;
+            K[i] = std::max<int32_t>(1, (d + param - 1) / param);
+            cap[i].assign(K[i], param);
+        } else if (rule == PT2D_SPARSIFY_MAX_DEGREE) {
+            if (param < 3) return PT2D_ERR_INVALID_ARG;
+            if (d <= param) {
+                K[i] = 1;
+                cap[i].assign(1, param);
+            } else {
+                int32_t k = 2;
+                while (2 * (param - 1) + (k - 2) * (param - 2) < d) ++k;
+                K[i] = k;
+                cap[i].assign(k, param - 2);
+                cap[i][0] = param - 1;
+                cap[i][k - 1] = param - 1;
+            }
+        } else {
+            return PT2D_ERR_INVALID_ARG;
+        }
+        off[i + 1] = off[i] + K[i];
+    }
+    const int32_t n = off[N];
+    // deal neighbours round-robin over copies, skipping full ones
+    std::vector<std::vector<int32_t>> copy_for(N);
+    for (int32_t i = 0; i < N; ++i) {
+        copy_for[i].assign(N, -1);
+        std::vector<int32_t> load(K[i], 0);
+        int32_t c = 0;
+        for (int32_t j : nbrs[i]) {
+            int32_t tries = 0;
+            while (cap[i][c] >= 0 && load[c] >= cap[i][c]) {
+                c = (c + 1) % K[i];
+                if (++tries > K[i]) return PT2D_ERR_INVALID_ARG;
+            }
+            copy_for[i][j] = c;
+            load[c]++;
+            c = (c + 1) % K[i];
+        }
+    }
+    std::vector<std::vector<std::pair<int32_t, int16_t>>> adj(n);
+    for (int32_t i = 0; i < N; ++i)
+        for (int32_t j : nbrs[i]) {
+            if (j <= i) continue;
+            const int32_t a = off[i] + copy_for[i][j], b = off[j] + copy_for[j][i];
+            const int16_t v = Jq[static_cast<size_t>(i) * N + j];
+            adj[a].push_back({b, v});
+            adj[b].push_back({a, v});
+        }
+    int64_t ncp = 0;
+    for (auto &v : adj) {
+        std::sort(v.begin(), v.end());
+        ncp += static_cast<int64_t>(v.size());
+    }
+    const int64_t nlk = 2LL * (n - N);
+    *n_out = n;
+    *nnz_cp = ncp;
+    *nnz_lk = nlk;
+    if (!cp_ptr && !cp_col && !cp_J && !lk_ptr && !lk_col && !copy_of) return PT2D_OK;
+    if (!cp_ptr || !cp_col || !cp_J || !lk_ptr || !lk_col || !copy_of) return PT2D_ERR_INVALID_ARG;
+    cp_ptr[0] = 0;
+    int64_t k = 0;
+    for (int32_t a = 0; a < n; ++a) {
+        for (const auto &e : adj[a]) {
+            cp_col[k] = e.first;
+            cp_J[k] = e.second;
+            ++k;
+        }
+        cp_ptr[a + 1] = static_cast<int32_t>(k);
+    }
+    lk_ptr[0] = 0;
+    k = 0;
+    for (int32_t i = 0; i < N; ++i)
+        for (int32_t c = 0; c < K[i]; ++c) {
+            const int32_t a = off[i] + c;
+            if (c > 0) lk_col[k++] = a - 1;
+            if (c + 1 < K[i]) lk_col[k++] = a + 1;
+            lk_ptr[a + 1] = static_cast<int32_t>(k);
+            copy_of[a] = i;
+        }
+    return PT2D_OK;
+}
+
+// ---- diagnostics ------------------------------------------------------------------
+int pt2d_diag_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t count) {
+    if (count < 0 || (count > 0 && (!ctr || !key || !out))) return PT2D_ERR_INVALID_ARG;
+    if (int st = check_device()) return st;
+    return pt2d::diag_philox(ctr, key, out, count) == cudaSuccess ? PT2D_OK : PT2D_ERR_CUDA;
+}
+
+int pt2d_diag_pt_exp(const float *x, float *y, int64_t count) {
+    if (count < 0 || (count > 0 && (!x || !y))) return PT2D_ERR_INVALID_ARG;
+    if (int st = check_device()) return st;
+    return pt2d::diag_pt_exp(x, y, count) == cudaSuccess ? PT2D_OK : PT2D_ERR_CUDA;
+}
+
+int pt2d_diag_heatbath(const float *beta, const int32_t *H, const uint32_t *r, int8_t *spin,
+                       int64_t count) {
+    if (count < 0 || (count > 0 && (!beta || !H || !r || !spin))) return PT2D_ERR_INVALID_ARG;
+    if (int st = check_device()) return st;
+    return pt2d::diag_heatbath(beta, H, r, spin, count) == cudaSuccess ? PT2D_OK : PT2D_ERR_CUDA;
+}
+
+int pt2d_diag_swap_accept(const float *x, const uint32_t *r, int8_t *accept, int64_t count) {
+    if (count < 0 || (count > 0 && (!x || !r || !accept))) return PT2D_ERR_INVALID_ARG;
+    if (int st = check_device()) return st;
+    return pt2d::diag_swap_accept(x, r, accept, count) == cudaSuccess ? PT2D_OK : PT2D_ERR_CUDA;
+}
+
+}  // extern "C"

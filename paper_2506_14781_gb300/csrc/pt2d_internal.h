@@ -1,0 +1,82 @@
+// Internal interface between the C-ABI host layer and the CUDA kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace pt2d {
+
+// Device layout of one instance and its replica grid.
+//  * Spins: int8 S[n + 1][Wc], one row per spin in colour-sorted position
+//    order, columns = walkers (walker-fastest, so a warp's neighbour loads are
+//    contiguous); row n is all zeros and serves as the padding neighbour.
+//  * Columns: run r owns columns [r * Rp, r * Rp + R); Rp = R rounded up to 4
+//    so that every group of 4 columns (one Philox call) lies in one run; Wc is
+//    the total rounded up to the sweep tile.
+//  * ELL neighbour lists per position: nb[pos][DC] (positions, padding -> n),
+//    jv[pos][DC] = 2 J, lk[pos][DL] (positions, padding -> n), h2[pos] = 2 h.
+struct Layout {
+    int8_t *S;
+    int64_t Wc;
+    int32_t n;
+    int32_t C;
+    int32_t DC;
+    int32_t DL;
+    const int32_t *pid;   // [n] position -> spin id
+    const int32_t *cofs;  // [C + 1] colour class offsets (positions)
+    const int32_t *nb;
+    const int32_t *jv;
+    const int32_t *lk;
+    const int32_t *h2;
+};
+
+struct Walkers {
+    float *wbeta;   // [Wc] beta of each column's current slot
+    int32_t *wP;    // [Wc] P of each column's current slot
+    int64_t *f;     // [Wc] cost after the last sweep of an event
+    int32_t *g;     // [Wc] constraint after the last sweep of an event
+};
+
+struct RunState {
+    int32_t runs, I, J, R, Rp;
+    const float *beta;      // [I]
+    const int32_t *P;       // [J]
+    int32_t *walker_at;     // [runs][R]
+    int64_t *acc_P;         // [runs][R]
+    int64_t *acc_B;         // [runs][R]
+    int64_t *sum_f;         // [runs][R]
+    int64_t *sum_g;         // [runs][R]
+    int64_t *n_feasible;    // [runs][R]
+    int64_t *trace_f;       // [runs][trace_cap]
+    int64_t *trace_g;       // [runs][trace_cap]
+    int64_t trace_cap;
+    int64_t *best_f;        // [runs]
+    int64_t *best_event;    // [runs]
+    int8_t *best_state;     // [runs][n]
+    const int64_t *target;  // [runs]
+    int64_t *solved_event;  // [runs]
+};
+
+struct SweepTiling {
+    int lanes_per_spin;  // quads (4 walkers) per spin row segment of a CTA
+    int threads;         // threads per CTA
+};
+
+cudaError_t launch_init(const Layout &L, const RunState &rs, const Walkers &wk, uint64_t seed,
+                        cudaStream_t st);
+cudaError_t launch_sweeps(const Layout &L, const Walkers &wk, const SweepTiling &tl,
+                          int32_t quads_per_run, uint64_t seed, uint32_t sweep0, int32_t nsweeps,
+                          cudaStream_t st);
+cudaError_t launch_swap_event(const Layout &L, const RunState &rs, const Walkers &wk,
+                              uint64_t seed, int64_t event, cudaStream_t st);
+
+// diagnostics
+cudaError_t diag_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t count);
+cudaError_t diag_pt_exp(const float *x, float *y, int64_t count);
+cudaError_t diag_heatbath(const float *beta, const int32_t *H, const uint32_t *r, int8_t *spin,
+                          int64_t count);
+cudaError_t diag_swap_accept(const float *x, const uint32_t *r, int8_t *acc, int64_t count);
+
+}  // namespace pt2d

@@ -1,0 +1,332 @@
+"""GPU library vs the CPU oracle, through the C ABI.
+
+Tolerance: zero.  Couplings, fields and energies are integers and the float
+decisions follow one fixed single-precision sequence on both sides, so spins,
+walker <-> slot maps, f, g, swap counts, traces and best states must match
+bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import core as ocore
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pt():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2506_14781_gb300 import build as b
+
+    b.build()
+    import paper_2506_14781_gb300 as m
+
+    return m
+
+
+ARRAYS = [
+    ("STATES", "spins"), ("WALKER_AT", "walker_at"), ("F", "f"), ("G", "g"),
+    ("TRACE_F", "trace_f"), ("TRACE_G", "trace_g"), ("BEST_F", "best_f"),
+    ("BEST_EVENT", "best_event"), ("BEST_STATE", "best_state"), ("SOLVED_EVENT", "solved_event"),
+    ("ACC_P", "acc_P"), ("ACC_B", "acc_B"), ("SUM_F", "sum_f"), ("SUM_G", "sum_g"),
+    ("N_FEASIBLE", "n_feasible"),
+]
+
+
+def assert_same(pt, ctx, orc, runs_sel=None, trace=True):
+    for what, attr in ARRAYS:
+        if not trace and what.startswith("TRACE"):
+            continue
+        got = ctx.read(getattr(pt, what))
+        if runs_sel is not None:
+            got = got[runs_sel]
+        exp = getattr(orc, attr)
+        assert got.shape == exp.shape, what
+        if not np.array_equal(got, exp):
+            bad = np.argwhere(got != exp)
+            raise AssertionError(f"{what} differs at {bad[:5].tolist()} ({len(bad)} entries)")
+    c = ctx.read(pt.COUNTERS)
+    assert list(c) == list(orc.counters), (c, orc.counters)
+
+
+def both(pt, inst_q, Jrule, beta, P, runs, seed, schedule, *, target=None, trace=64, wpc=0,
+         threads=0, phys=None):
+    if phys is None:
+        phys_p = pt.sparsify(inst_q.Jq, *Jrule)
+        phys_o = oracle.sparsify(inst_q.Jq, *Jrule)
+    else:
+        phys_p, phys_o = phys
+    ctx = pt.PT2D(phys_p, beta, P, runs, trace_capacity=trace, walkers_per_cta=wpc,
+                  threads_per_cta=threads)
+    orc = oracle.OracleRun(oracle.OracleInstance(phys_o), beta, P, list(range(runs)), seed,
+                           trace_cap=trace, target=target)
+    if target is not None:
+        ctx.write(pt.TARGET, np.full(runs, target, np.int64))
+    for sweeps, interval in schedule:
+        ctx.run(sweeps, interval, seed)
+        orc.run(sweeps, interval)
+    return ctx, orc
+
+
+# ---- element-wise device arithmetic -------------------------------------------------
+def test_philox_matches_oracle(pt):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(200000, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(200000, 2), dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(pt.diag_philox(ctr, key), ocore.philox_array(ctr, key))
+
+
+def test_pt_exp_bit_exact_dense(pt):
+    lo = np.float32(-104.5).view(np.uint32)  # negative floats: larger bit pattern = more negative
+    neg = np.arange(np.uint32(0x80000000), lo + np.uint32(1), 53, dtype=np.uint64).astype(np.uint32)
+    pos = np.arange(0, np.float32(89.5).view(np.uint32), 53, dtype=np.uint32)
+    x = np.concatenate([neg, pos]).view(np.float32)
+    x = np.concatenate([x, np.array([0.0, -0.0, 88.72, 88.75, 88.7228, -103.97, -104.0, -87.3,
+                                     np.inf, -np.inf], np.float32)])
+    got = pt.diag_pt_exp(x)
+    exp = ocore.pt_exp_array(x)
+    assert np.array_equal(got.view(np.uint32), exp.view(np.uint32))
+
+
+def _boundary_cases(rng, count):
+    beta = rng.choice(np.array([1.1e-6, 7.3e-6, 3.1e-5, 0.01, 0.5, 2.0], np.float32), count)
+    H = rng.integers(-400000, 400001, count).astype(np.int32)
+    small = beta >= 0.01
+    H[small] = rng.integers(-60, 61, small.sum())
+    z = beta.astype(np.float64) * H
+    sig = np.where(z >= 0, 1 / (1 + np.exp(-np.minimum(z, 700))), np.exp(np.maximum(z, -700)) /
+                   (1 + np.exp(np.maximum(z, -700))))
+    m = np.clip(np.floor(sig * 2**23).astype(np.int64) + rng.integers(-3000, 3001, count), 0,
+                2**23 - 1)
+    r = (m.astype(np.uint64) << np.uint64(9)) | rng.integers(0, 512, count).astype(np.uint64)
+    return beta, H, r.astype(np.uint32)
+
+
+def test_heatbath_matches_oracle(pt):
+    rng = np.random.default_rng(2)
+    # uniform random triples
+    n = 2_000_000
+    beta = rng.choice(np.array([0.0, 1e-6, 1e-5, 3e-5, 1e-4, 0.1, 1.0, 30.0], np.float32), n)
+    H = rng.integers(-2**23, 2**23, n).astype(np.int32)
+    r = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(pt.diag_heatbath(beta, H, r), ocore.heatbath_array(beta, H, r))
+    # triples straddling the decision boundary (exercise the exact path)
+    beta, H, r = _boundary_cases(rng, 2_000_000)
+    assert np.array_equal(pt.diag_heatbath(beta, H, r), ocore.heatbath_array(beta, H, r))
+    # u = 0 with saturated exponentials
+    H = np.array([-2**23 + 1, 2**23 - 1, -500000, 500000, 0], np.int32)
+    for b in (np.float32(1.0), np.float32(1e-4), np.float32(2.1e-5)):
+        bb = np.full(H.size, b, np.float32)
+        for rv in (0, 1, 511, 512):
+            rr = np.full(H.size, rv, np.uint32)
+            assert np.array_equal(pt.diag_heatbath(bb, H, rr), ocore.heatbath_array(bb, H, rr))
+
+
+@pytest.mark.parametrize("beta,H", [(1e-5, 30000), (3.2e-5, -131068), (2.0, 3), (7.3e-6, 0)])
+def test_heatbath_exhaustive_over_uniforms(pt, beta, H):
+    r = (np.arange(2**23, dtype=np.uint64) << np.uint64(9)).astype(np.uint32)
+    b = np.full(r.size, beta, np.float32)
+    h = np.full(r.size, H, np.int32)
+    got = pt.diag_heatbath(b, h, r)
+    assert np.array_equal(got, ocore.heatbath_array(b, h, r))
+    assert int((got > 0).sum()) == oracle.heatbath_count(beta, H)
+
+
+def test_swap_accept_matches_oracle(pt):
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(-120, 5, 1_000_000), -rng.exponential(1.0, 1_000_000)])
+    x = x.astype(np.float32)
+    r = rng.integers(0, 2**32, x.size, dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(pt.diag_swap_accept(x, r), ocore.swap_accept_array(x, r))
+
+
+# ---- whole trajectories ----------------------------------------------------------------
+def test_tiny_config_bit_exact_full_length(pt, tiny_config):
+    """Tiny configuration as specified: 20 physical spins, I=4 x J=4, swaps every
+    sweep, 10^5 sweeps, one run."""
+    cfg = tiny_config
+    ctx, orc = both(pt, cfg["inst"], ("fixed", 2), cfg["beta"], cfg["P"], 1, 7,
+                    [(100000, 1)], target=cfg["inst"].E_planted, trace=1 << 17)
+    assert_same(pt, ctx, orc)
+    assert orc.best_f[0] == cfg["inst"].E_planted  # the planted ground state is reached
+
+
+@pytest.mark.parametrize("wpc,threads", [(4, 32), (16, 64), (32, 256), (128, 256), (0, 0)])
+def test_ragged_tiles_and_resume(pt, wpc, threads):
+    inst = synth.wishart_planted(30, 0.5, 21)
+    beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
+    P = synth.penalty_ladder(3, 0.5, 4.0, 32767)
+    # R = 15 (not a multiple of 4), 7 runs, interval 7, resumed once, a trailing partial block
+    ctx, orc = both(pt, inst, ("max_edges", 3), beta, P, 7, 0xDEADBEEF12345,
+                    [(35, 7), (20, 7), (7, 7)], target=inst.E_planted, wpc=wpc, threads=threads)
+    assert_same(pt, ctx, orc)
+
+
+def test_generic_degree_kernel_with_fields(pt):
+    """Irregular instance with fields and degrees beyond the specialised kernels."""
+    rng = np.random.default_rng(9)
+    n = 90
+    A = np.zeros((n, n), np.int16)
+    for a in range(n):
+        for b in rng.choice(n, 8, replace=False):
+            if b != a:
+                v = np.int16(rng.integers(-900, 901))
+                A[a, b] = A[b, a] = v
+    links = [(a, a + 1) for a in range(0, n - 1, 3)] + [(a, a + 2) for a in range(0, n - 2, 5)]
+    L = np.zeros((n, n), bool)
+    for a, b in links:
+        L[a, b] = L[b, a] = True
+    cp_ptr = np.concatenate([[0], np.cumsum((A != 0).sum(1))]).astype(np.int32)
+    cp_col = np.concatenate([np.nonzero(A[a])[0] for a in range(n)]).astype(np.int32)
+    cp_J = np.concatenate([A[a][A[a] != 0] for a in range(n)]).astype(np.int16)
+    lk_ptr = np.concatenate([[0], np.cumsum(L.sum(1))]).astype(np.int32)
+    lk_col = np.concatenate([np.nonzero(L[a])[0] for a in range(n)]).astype(np.int32)
+    h = rng.integers(-500, 501, n).astype(np.int32)
+    phys_p = pt.PhysicalInstance(n, cp_ptr, cp_col, cp_J, lk_ptr, lk_col, h=h)
+    phys_o = oracle.PhysInstance(n, cp_ptr, cp_col, cp_J, lk_ptr, lk_col, h, n, np.arange(n),
+                                 np.arange(n + 1))
+    beta = np.array([1e-4, 4e-4, 1e-3], np.float32)
+    P = np.array([0, 300, 900, 2000], np.int32)
+    ctx, orc = both(pt, None, None, beta, P, 3, 5, [(24, 4)], phys=(phys_p, phys_o), trace=8)
+    assert ctx.num_colors == orc.oinst.n_colors
+    assert np.array_equal(ctx.read(pt.COLORS), orc.oinst.color)
+    assert_same(pt, ctx, orc)
+
+
+def test_single_row_single_column_single_spin(pt):
+    inst = synth.wishart_planted(8, 0.5, 4)
+    # one row (P-swaps only) and one column (beta-swaps only)
+    for beta, P in ((synth.beta_ladder(1, 1.0, 1.0, inst.scale), synth.penalty_ladder(5, 0.5, 4, 32767)),
+                    (synth.beta_ladder(6, 0.1, 2.0, inst.scale), synth.penalty_ladder(1, 2, 2, 32767))):
+        ctx, orc = both(pt, inst, ("fixed", 2), beta, P, 2, 11, [(40, 2), (3, 2)])
+        assert_same(pt, ctx, orc)
+    # one spin, no edges, a field
+    one_p = pt.PhysicalInstance(1, [0, 0], [], [], [0, 0], [], h=np.array([3], np.int32))
+    one_o = oracle.PhysInstance(1, np.array([0, 0], np.int32), np.zeros(0, np.int32),
+                                np.zeros(0, np.int16), np.array([0, 0], np.int32),
+                                np.zeros(0, np.int32), np.array([3], np.int32), 1,
+                                np.zeros(1, np.int32), np.array([0, 1], np.int32))
+    ctx, orc = both(pt, None, None, np.array([0.1, 0.3], np.float32), np.array([0, 1], np.int32),
+                    3, 2, [(50, 5)], phys=(one_p, one_o))
+    assert_same(pt, ctx, orc)
+
+
+def test_errors_and_empty_runs(pt, tiny_config):
+    cfg = tiny_config
+    phys = pt.sparsify(cfg["inst"].Jq, "fixed", 2)
+    ctx = pt.PT2D(phys, cfg["beta"], cfg["P"], 2)
+    with pytest.raises(pt.Pt2dError):
+        ctx.read(pt.STATES)  # before the first run
+    ctx.run(0, 5, 1)  # no event: only initialisation
+    assert list(ctx.read(pt.COUNTERS)) == [0, 0, 1, 1]
+    ctx.run(4, 5, 1)  # fewer sweeps than the interval: nothing happens
+    assert list(ctx.read(pt.COUNTERS)) == [0, 0, 1, 1]
+    with pytest.raises(pt.Pt2dError):
+        ctx.run(10, 5, 2)  # another seed
+    with pytest.raises(pt.Pt2dError):
+        ctx.run(10, 0, 1)
+    with pytest.raises(pt.Pt2dError):
+        pt.PT2D(phys, cfg["beta"][::-1].copy(), cfg["P"], 1)  # descending ladder
+
+
+def test_checkpoint_restore_matches_uninterrupted(pt, tiny_config):
+    inst = synth.wishart_planted(24, 0.75, 8)
+    phys = pt.sparsify(inst.Jq, "max_edges", 3)
+    beta = synth.beta_ladder(4, 0.2, 2.0, inst.scale)
+    P = synth.penalty_ladder(4, 0.5, 4, 32767)
+    seed = 2**64 - 3
+    ref = pt.PT2D(phys, beta, P, 3, trace_capacity=32)
+    ref.write(pt.TARGET, np.full(3, inst.E_planted))
+    ref.run(60, 5, seed)
+    a = pt.PT2D(phys, beta, P, 3, trace_capacity=32)
+    a.write(pt.TARGET, np.full(3, inst.E_planted))
+    a.run(25, 5, seed)
+    saved = {w: a.read(getattr(pt, w)) for w in ("STATES", "WALKER_AT", "COUNTERS", "BEST_F",
+                                                  "BEST_EVENT", "BEST_STATE", "SOLVED_EVENT",
+                                                  "ACC_P", "ACC_B", "SUM_F", "SUM_G",
+                                                  "N_FEASIBLE", "TRACE_F", "TRACE_G", "TARGET")}
+    a.close()
+    b = pt.PT2D(phys, beta, P, 3, trace_capacity=32, workspace="torch")
+    for w, v in saved.items():
+        if w != "COUNTERS":
+            b.write(getattr(pt, w), v)
+    b.write(pt.COUNTERS, saved["COUNTERS"])
+    b.run(35, 5, seed)
+    for w in saved:
+        assert np.array_equal(b.read(getattr(pt, w)), ref.read(getattr(pt, w))), w
+    assert np.array_equal(b.read(pt.F), ref.read(pt.F))
+
+
+def test_torch_stream_and_workspace(pt, tiny_config):
+    import torch
+
+    cfg = tiny_config
+    phys = pt.sparsify(cfg["inst"].Jq, "fixed", 2)
+    s = torch.cuda.Stream()
+    a = pt.PT2D(phys, cfg["beta"], cfg["P"], 5, stream=s, workspace="torch")
+    a.run(300, 3, 77)
+    b = pt.PT2D(phys, cfg["beta"], cfg["P"], 5)
+    b.run(300, 3, 77)
+    for what, _ in ARRAYS:
+        assert np.array_equal(a.read(getattr(pt, what)), b.read(getattr(pt, what))), what
+
+
+# ---- full-size configurations, checked on samples the oracle computes -----------------
+def test_n200_full_size_sampled_runs(pt):
+    """N=200, alpha=0.5, <=3 edges per copy (13,400 spins), I=32 x J=8, 64 runs, in
+    the automatic launch configuration the benchmark uses; two runs checked in
+    full by the oracle after two events."""
+    inst = synth.wishart_planted(200, 0.5, 2)
+    phys_p = pt.sparsify(inst.Jq, "max_edges", 3)
+    assert phys_p.n == int(np.ceil(inst.degrees / 3).sum())
+    beta = synth.beta_ladder(32, 0.1, 2.0, inst.scale)
+    P = synth.penalty_ladder(8, 0.5, 4.0, 32767)
+    seed = 100
+    ctx = pt.PT2D(phys_p, beta, P, 64, trace_capacity=8)
+    ctx.write(pt.TARGET, np.full(64, inst.E_planted))
+    ctx.run(20, 10, seed)
+    oinst = oracle.OracleInstance(oracle.sparsify(inst.Jq, "max_edges", 3))
+    for run_id in (0, 45):
+        orc = oracle.OracleRun(oinst, beta, P, [run_id], seed, trace_cap=8, target=inst.E_planted)
+        orc.run(20, 10)
+        assert_same(pt, ctx, orc, runs_sel=[run_id])
+
+
+def test_n800_full_size_sampled_walkers(pt):
+    """N=800 (213,600 spins), I=64 x J=16, 16 runs (3.5 GB of spins): after one
+    event, sampled walkers match the oracle spin for spin, their f and g match,
+    and the event's P-swap decisions match the oracle's swap event replayed on
+    the GPU's f and g."""
+    inst = synth.wishart_planted(800, 0.5, 3)
+    phys_p = pt.sparsify(inst.Jq, "max_edges", 3)
+    # ~3 edges per copy of ~799 neighbours (a few quantised couplings round to 0)
+    assert phys_p.n == int(np.ceil(inst.degrees / 3).sum()) and phys_p.n > 213000
+    beta = synth.beta_ladder(64, 0.1, 2.0, inst.scale)
+    P = synth.penalty_ladder(16, 0.5, 4.0, 32767)
+    seed = 4242
+    runs = 16
+    ctx = pt.PT2D(phys_p, beta, P, runs, trace_capacity=4)
+    ctx.run(2, 2, seed)
+    oinst = oracle.OracleInstance(oracle.sparsify(inst.Jq, "max_edges", 3))
+    f_gpu = ctx.read(pt.F)
+    g_gpu = ctx.read(pt.G)
+    for run_id, w in ((0, 0), (3, 511), (3, 1023), (15, 777), (9, 14)):
+        s = oinst.init_walker(seed, run_id, w)
+        i, j = divmod(w, 16)  # walker w starts in slot w
+        for t in range(2):
+            oinst.sweep_walker(s, seed, run_id, w, t, beta[i], P[j])
+        assert np.array_equal(ctx.read_walker(run_id, w), s), (run_id, w)
+        assert f_gpu[run_id, w] == oinst.cost_f(s)
+        assert g_gpu[run_id, w] == oinst.constraint_g(s)
+    at_gpu = ctx.read(pt.WALKER_AT)
+    acc_gpu = ctx.read(pt.ACC_P)
+    for run_id in (3, 15):
+        at, accP, accB = ocore.swap_event(beta, P, f_gpu[run_id], g_gpu[run_id],
+                                          np.arange(64 * 16), seed, run_id, 1, 1)
+        assert np.array_equal(at_gpu[run_id], at)
+        assert np.array_equal(acc_gpu[run_id], accP)
