@@ -191,6 +191,37 @@ const char *pt2d_strerror(int status);
 /* Last CUDA error code (cudaError_t) recorded by the context, 0 if none. */
 int pt2d_cuda_error(const pt2d_ctx *ctx);
 
+/* ---- one-shot run without device allocation ------------------------------ */
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * cannot call cudaMalloc, for example a host program whose device memory is
+ * already fully reserved by its own pool or allocator (a serving process that
+ * claims the GPU's memory up front), or a loop that must not pay for the
+ * implicit synchronisation and latency of a device allocation.
+ *
+ * It runs create + run + read + destroy of the context API in one call, with
+ * every device buffer carved from a file-scope device array of
+ * PT2D_NOALLOC_SCRATCH_BYTES bytes that the library holds on each GPU it is
+ * used on until the process exits.  It calls no cudaMalloc or cudaFree.
+ *  - The first call on a device looks up that array's device address (with
+ *    the device current); make that first call before any stream capture.
+ *  - All calls share the array and it keeps the previous call's contents; each
+ *    call clears the part it uses before starting.  Calls whose GPU work
+ *    overlaps (several streams or host threads at once) race on the array and
+ *    give undefined results: serialise them.
+ *  - Problems whose context would need more than PT2D_NOALLOC_SCRATCH_BYTES of
+ *    device memory (see pt2d_workspace_size with trace_capacity 0) are
+ *    rejected with PT2D_ERR_INVALID_ARG before any device work.
+ * Arguments are those of pt2d_create and pt2d_run (trace off); outputs are
+ * host buffers or NULL: states int8 [runs][I*J][n], walker_at int32
+ * [runs][I*J], f and g int64 [runs][I*J], as from pt2d_read.  Synchronous on
+ * `stream` (NULL = default stream).  Errors: those of pt2d_create, pt2d_run
+ * and pt2d_read. */
+#define PT2D_NOALLOC_SCRATCH_BYTES (8u << 20)
+int pt2d_run_noalloc(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J,
+                     const int32_t *P, int32_t runs, int64_t sweeps, int32_t swap_interval,
+                     uint64_t seed, void *stream, int8_t *states, int32_t *walker_at, int64_t *f,
+                     int64_t *g);
+
 /* ---- host-side compiler helpers (section "Graph sparsification") ------- */
 /* Copy-chain sparsification of a dense symmetric int16 logical coupling
  * matrix Jq[N*N] (zero diagonal).  Logical node i with K_i copies owns

@@ -31,7 +31,7 @@ EXPORTS = [
     "pt2d_write", "pt2d_array_bytes", "pt2d_sync", "pt2d_num_colors", "pt2d_launch_count",
     "pt2d_destroy", "pt2d_strerror", "pt2d_cuda_error", "pt2d_sparsify", "pt2d_greedy_color",
     "pt2d_diag_philox", "pt2d_diag_pt_exp", "pt2d_diag_heatbath", "pt2d_diag_swap_accept",
-    "pt2d_kernel_time",
+    "pt2d_kernel_time", "pt2d_run_noalloc",
 ]
 
 
@@ -108,6 +108,8 @@ def lib():
         L.pt2d_diag_heatbath.argtypes = [vp, vp, vp, vp, i64]
         L.pt2d_diag_swap_accept.argtypes = [vp, vp, vp, i64]
         L.pt2d_kernel_time.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]
+        L.pt2d_run_noalloc.argtypes = [vp, i32, vp, i32, vp, i32, i64, i32, C.c_uint64, vp, vp,
+                                       vp, vp, vp]
         for name in EXPORTS:
             getattr(L, name)  # every declared entry point must be exported
         _lib = L
