@@ -32,7 +32,7 @@
  *      sweep: c0 = spin id, c1 = global sweep index, c2 = walker / 4, word walker % 4
  *      init:  c0 = spin id, c1 = 0,                 c2 = walker / 4, word walker % 4
  *      swap:  c0 = lower slot index of the pair, c1 = event index n (1-based), c2 = 0, word 0
- *    and u = (word >> 9) * 2^-23;
+ *    and u = ((word >> 9) + 1) * 2^-23, a uniform on the grid of (0, 1];
  *  - heat bath: t = beta (x) float(H); e = pt_exp(-t); d = 1 (+) e; v = u (x) d;
  *    new spin +1 iff v < 1 (single-precision, round-to-nearest, no fused ops);
  *  - swaps: x = beta_i (x) float(dP dg) for P-swaps, x = (beta_{i+1} (-) beta_i)
@@ -105,10 +105,15 @@ typedef struct {
     void *workspace;         /* caller-owned device memory, or NULL: library allocates */
     size_t workspace_bytes;  /* size of `workspace` (see pt2d_workspace_size)      */
     int32_t trace_capacity;  /* events kept in the bottom-right trace (default 1024) */
-    int32_t walkers_per_cta; /* sweep tiling: 4..128, power of two; 0 = automatic   */
-    int32_t threads_per_cta; /* 32..256, multiple of 32, >= walkers_per_cta/4; 0 = auto */
+    int32_t walkers_per_cta; /* sweep tiling: 4..128 (16..128 in shared memory), power of
+                                two; 0 = automatic                                  */
+    int32_t threads_per_cta; /* multiple of 32, >= walkers_per_cta/4, <= 256 (global
+                                slab) or 1024 (shared slab); 0 = automatic          */
     int32_t device;          /* CUDA device ordinal; -1 = current device            */
     int32_t profile;         /* nonzero: time every kernel launch with CUDA events  */
+    int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 slab in shared
+                                memory (INVALID_ARG if it does not fit)               */
+    int32_t walkers_per_thread; /* shared-memory kernel: 4 or 8; 0 = automatic       */
 } pt2d_options;
 
 typedef struct pt2d_ctx pt2d_ctx;

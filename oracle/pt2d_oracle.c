@@ -79,10 +79,11 @@ static uint32_t orc_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
     return out[word];
 }
 
-/* Uniform in [0,1): the top 23 bits of the word times 2^-23 (exact). */
+/* Uniform on the 2^23-point grid of (0,1]: (top 23 bits of the word + 1)
+ * times 2^-23, exact.  Never zero, so u * d is never 0 * inf. */
 static float orc_uniform(uint32_t r)
 {
-    return (float)(r >> 9) * 0x1p-23f;
+    return (float)((r >> 9) + 1u) * 0x1p-23f;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -103,13 +103,16 @@ class PT2D:
 
     workspace: "library" (the library allocates device memory with cudaMalloc),
     or "torch" (a torch uint8 CUDA tensor owned by this object provides it).
+    sweep_kernel: "auto", "global" (replica slab in global memory) or "smem"
+    (slab held in shared memory for a whole swap interval).
     stream: a torch.cuda.Stream, a raw cudaStream_t (int), or None (default stream).
     """
 
     def __init__(self, inst: PhysicalInstance, beta, P, runs: int, *, stream=None,
                  workspace: str = "library", trace_capacity: int = 1024,
                  walkers_per_cta: int = 0, threads_per_cta: int = 0, device: int = -1,
-                 profile: bool = False):
+                 profile: bool = False, sweep_kernel: str = "auto",
+                 walkers_per_thread: int = 0):
         self.inst = inst
         self.beta = np.ascontiguousarray(beta, dtype=np.float32)
         self.P = np.ascontiguousarray(P, dtype=np.int32)
@@ -126,6 +129,8 @@ class PT2D:
         opt.threads_per_cta = int(threads_per_cta)
         opt.device = int(device)
         opt.profile = 1 if profile else 0
+        opt.sweep_kernel = {"auto": 0, "global": 1, "smem": 2}[sweep_kernel]
+        opt.walkers_per_thread = int(walkers_per_thread)
         self._stream_obj = stream
         if stream is not None:
             opt.stream = int(getattr(stream, "cuda_stream", stream))

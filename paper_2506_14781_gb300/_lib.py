@@ -58,6 +58,8 @@ class Options(C.Structure):
         ("threads_per_cta", C.c_int32),
         ("device", C.c_int32),
         ("profile", C.c_int32),
+        ("sweep_kernel", C.c_int32),
+        ("walkers_per_thread", C.c_int32),
     ]
 
 

@@ -35,9 +35,40 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
     return x;
 }
 
-// Uniform u = (r >> 9) * 2^-23, exactly.
+// The ten round keys of one seed, precomputed on the host and passed as a
+// kernel parameter so the key schedule costs no per-thread instructions.
+struct RoundKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+inline RoundKeys round_keys(uint64_t seed) {
+    RoundKeys rk;
+    uint32_t a = static_cast<uint32_t>(seed), b = static_cast<uint32_t>(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        rk.k0[i] = a;
+        rk.k1[i] = b;
+        a += kWeyl0;
+        b += kWeyl1;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, const RoundKeys &rk) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = kPhiloxM0 * x.x;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, x.x);
+        const uint32_t lo1 = kPhiloxM1 * x.z;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, x.z);
+        x = make_uint4(hi1 ^ x.y ^ rk.k0[round], lo1, hi0 ^ x.w ^ rk.k1[round], lo0);
+    }
+    return x;
+}
+
+// Uniform on the 2^23-point grid of (0, 1]: u = ((r >> 9) + 1) * 2^-23, exactly.
 __device__ __forceinline__ float uniform23(uint32_t r) {
-    return __fmul_rn(__uint2float_rn(r >> 9), 0x1p-23f);
+    return __fmul_rn(__uint2float_rn((r >> 9) + 1u), 0x1p-23f);
 }
 
 // ---------------------------------------------------------------------------
@@ -95,31 +126,38 @@ __device__ __noinline__ int heatbath_exact(float beta, int32_t H, uint32_t r) {
     return v < 1.0f ? 1 : -1;
 }
 
-// Fast path: e~ = 2^(y) with y = (-beta*log2 e) * H from the hardware
-// approximation; v~ = u + u*e~.  Near the decision boundary (v ~ 1, so
-// |y| <= 24) the contract's v and v~ differ by at most ~2^-17.5 relative
-// (argument rounding of both, pt_exp's <= 3 ulp, ex2.approx's ~2^-22), so
-// outside the band |v~ - 1| <= 2^-14 both give the same answer; inside it, or
-// for u = 0 (where an infinite d makes the contract's v NaN), the exact
-// contract decides.
+// Fast path.  e~ = 2^y with y = (-beta log2 e) * H from the hardware
+// approximation, d~ = 1 + e~ and t~ = u d~ - 1 (one fused multiply-add).  Near
+// the decision boundary (t ~ 0, so |y| <= 24) the contract's v = u (x) d and
+// 1 + t~ differ by at most ~2^-17.5 relative (argument rounding on both sides,
+// pt_exp's <= 3 ulp, ex2.approx's ~2^-22), so outside the band |t~| <= 2^-14
+// the sign of t~ is the contract's answer (t~ < 0 <=> +1); inside the band the
+// exact contract decides.  u > 0, so an infinite e~ gives t~ = +inf (-1), as
+// the contract's v = u * inf does.
 __device__ __forceinline__ float ex2_approx(float y) {
     float e;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
     return e;
 }
 
-constexpr float kBandLo = 1.0f - 0x1p-14f;
-constexpr float kBandHi = 1.0f + 0x1p-14f;
+constexpr float kBand = 0x1p-14f;
 
-// nbl2e = -beta * log2(e) (rounded once per walker); Hf = float(H), exact.
+// t~ of the fast path (see above); nbl2e = -beta * log2(e), rounded once per walker.
+__device__ __forceinline__ float heatbath_fast(float nbl2e, int32_t H, uint32_t r) {
+    const float e = ex2_approx(nbl2e * __int2float_rn(H));
+    const float u = __uint_as_float(0x3f800001u + (r >> 9)) - 1.0f;  // ((r >> 9) + 1) * 2^-23
+    return fmaf(u, 1.0f + e, -1.0f);
+}
+
+// Returns a float whose sign is the decision: negative <=> new spin +1.
+__device__ __forceinline__ float heatbath_t(float beta, float nbl2e, int32_t H, uint32_t r) {
+    const float t = heatbath_fast(nbl2e, H, r);
+    if (fabsf(t) > kBand) return t;
+    return heatbath_exact(beta, H, r) > 0 ? -1.0f : 1.0f;
+}
+
 __device__ __forceinline__ int heatbath(float beta, float nbl2e, int32_t H, uint32_t r) {
-    const float y = nbl2e * __int2float_rn(H);
-    const float e = ex2_approx(y);
-    const float u = __uint_as_float(0x3f800000u | (r >> 9)) - 1.0f;  // (r >> 9) * 2^-23
-    const float v = fmaf(u, e, u);
-    if (v < kBandLo && r >= 512u) return 1;
-    if (v > kBandHi) return -1;
-    return heatbath_exact(beta, H, r);
+    return heatbath_t(beta, nbl2e, H, r) < 0.0f ? 1 : -1;
 }
 
 // Metropolis swap test: accept iff x >= 0 or u <= pt_exp(x).

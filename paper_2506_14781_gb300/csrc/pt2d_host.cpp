@@ -22,7 +22,8 @@ struct Prep {
     int64_t Wc = 0;
     int32_t trace_cap = 0;
     pt2d::SweepTiling tiling{};
-    std::vector<int32_t> color, pid, pos_of, cofs, nb, jv, lk, h2;
+    int32_t rec_vec = 0, pad_ref = 0;
+    std::vector<int32_t> color, pid, pos_of, cofs, rec;
 };
 
 // Sum of sizes with 256-byte alignment; two passes (size, then assignment).
@@ -165,19 +166,23 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         DC = std::max(dcmax, 1);
         DL = std::max(dlmax, 1);
     }
-    pp.nb.assign(static_cast<size_t>(n) * DC, n);
-    pp.jv.assign(static_cast<size_t>(n) * DC, 0);
-    pp.lk.assign(static_cast<size_t>(n) * DL, n);
-    pp.h2.assign(n, 0);
+    // packed records: [nb x DC, lk x DL, pid, 2h, 2J x DC], padded to whole int4s
+    const int32_t rec_vec = (2 * DC + DL + 2 + 3) / 4;
+    const size_t ri = static_cast<size_t>(rec_vec) * 4;
+    pp.rec_vec = rec_vec;
+    pp.rec.assign(static_cast<size_t>(n) * ri, 0);
     for (int32_t p = 0; p < n; ++p) {
         const int32_t a = pp.pid[p];
+        int32_t *r = pp.rec.data() + static_cast<size_t>(p) * ri;
+        for (int32_t k = 0; k < DC; ++k) r[k] = n;
+        for (int32_t k = 0; k < DL; ++k) r[DC + k] = n;
         for (size_t k = 0; k < cadj[a].size(); ++k) {
-            pp.nb[static_cast<size_t>(p) * DC + k] = pp.pos_of[cadj[a][k].first];
-            pp.jv[static_cast<size_t>(p) * DC + k] = 2 * cadj[a][k].second;
+            r[k] = pp.pos_of[cadj[a][k].first];
+            r[DC + DL + 2 + k] = 2 * cadj[a][k].second;
         }
-        for (size_t k = 0; k < ladj[a].size(); ++k)
-            pp.lk[static_cast<size_t>(p) * DL + k] = pp.pos_of[ladj[a][k].first];
-        pp.h2[p] = inst->h ? 2 * inst->h[a] : 0;
+        for (size_t k = 0; k < ladj[a].size(); ++k) r[DC + k] = pp.pos_of[ladj[a][k].first];
+        r[DC + DL] = a;
+        r[DC + DL + 1] = inst->h ? 2 * inst->h[a] : 0;
     }
     pp.n = n;
     pp.I = I;
@@ -189,31 +194,86 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.DC = DC;
     pp.DL = DL;
     pp.trace_cap = opt ? std::max<int32_t>(opt->trace_capacity, 0) : 1024;
-    // sweep tiling: quads per spin-row segment of a CTA and threads per CTA
-    const int64_t quads = static_cast<int64_t>(runs) * pp.Rp / 4;
-    int ql;
-    if (opt && opt->walkers_per_cta > 0) {
-        const int w = opt->walkers_per_cta;
-        if (w < 4 || w > 128 || (w & (w - 1))) return PT2D_ERR_INVALID_ARG;
-        ql = w / 4;
-    } else {
-        int sms = 152;
+    // Sweep tiling.  The shared-memory kernel holds a CTA's whole slab,
+    // (n + 1) x SW bytes, for the swap interval; it needs one of the specialised
+    // degree layouts.  Otherwise the slab stays in global memory.
+    int sms = 152, smem_max = 232448;
+    {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) {
             int v = 0;
             if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
                 sms = v;
+            if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+                v > 0)
+                smem_max = v;
+        } else {
+            cudaGetLastError();
         }
-        ql = 32;
-        while (ql > 1 && (quads + ql - 1) / ql < 2LL * sms) ql /= 2;
     }
-    int threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta : 256;
-    if (threads < 32 || threads > 256 || threads % 32) return PT2D_ERR_INVALID_ARG;
-    if (threads < ql) return PT2D_ERR_INVALID_ARG;
+    const int mode = opt ? opt->sweep_kernel : 0;
+    if (mode < 0 || mode > 2) return PT2D_ERR_INVALID_ARG;
+    const bool specialised = DL == 2 && (DC == 3 || DC == 4 || DC == 6);
+    const int64_t walkers = static_cast<int64_t>(runs) * pp.Rp;
+    auto fits = [&](int sw) {
+        return pt2d::smem_sweep_bytes(n, sw) + pt2d::kSweepStaticSmem <= static_cast<size_t>(smem_max);
+    };
+    const int req_w = opt ? opt->walkers_per_cta : 0;
+    if (req_w != 0 && (req_w < 4 || req_w > 128 || (req_w & (req_w - 1)))) return PT2D_ERR_INVALID_ARG;
+    // shared-memory slab width: the widest that fits and still gives every SM a
+    // CTA, else the narrowest that fits; 0 = global kernel
+    int sw = 0;
+    if (mode != 1 && specialised) {
+        if (req_w) {
+            if (req_w >= 16 && fits(req_w)) sw = req_w;
+        } else {
+            for (int cand = 128; cand >= 16; cand /= 2) {
+                if (!fits(cand)) continue;
+                sw = cand;
+                if ((walkers + cand - 1) / cand >= sms) break;
+            }
+        }
+    }
+    if (mode == 2 && sw == 0) return PT2D_ERR_INVALID_ARG;
+    int ql, threads, wpt = 4;
+    if (sw) {
+        ql = sw / 4;
+        const int req_t = opt ? opt->walkers_per_thread : 0;
+        if (req_t != 0 && req_t != 4 && req_t != 8) return PT2D_ERR_INVALID_ARG;
+        wpt = req_t ? req_t : 4;
+        const int lanes = sw / wpt;  // threads per spin row segment
+        const int tmax = wpt == 4 ? 1024 : 512;
+        int32_t widest = 0;
+        for (int32_t c = 0; c < C; ++c) widest = std::max(widest, pp.cofs[c + 1] - pp.cofs[c]);
+        const int64_t want = (static_cast<int64_t>(widest) * lanes + 31) / 32 * 32;
+        threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta
+                                                    : static_cast<int>(std::min<int64_t>(tmax, want));
+        if (threads < 32 || threads > tmax || threads % 32 || threads < lanes) return PT2D_ERR_INVALID_ARG;
+    } else {
+        if (opt && opt->walkers_per_thread != 0 && opt->walkers_per_thread != 4)
+            return PT2D_ERR_INVALID_ARG;
+        if (req_w) {
+            ql = req_w / 4;
+        } else {
+            const int64_t quads = walkers / 4;
+            ql = 32;
+            while (ql > 1 && (quads + ql - 1) / ql < 2LL * sms) ql /= 2;
+        }
+        threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta : 256;
+        if (threads < 32 || threads > 256 || threads % 32 || threads < ql) return PT2D_ERR_INVALID_ARG;
+    }
     pp.tiling.lanes_per_spin = ql;
     pp.tiling.threads = threads;
+    pp.tiling.smem = sw != 0;
+    pp.tiling.walkers_per_thread = wpt;
+    if (sw) {  // neighbour references become byte offsets into the shared-memory slab
+        const size_t ri2 = static_cast<size_t>(pp.rec_vec) * 4;
+        for (int32_t p = 0; p < n; ++p)
+            for (int32_t k = 0; k < DC + DL; ++k) pp.rec[static_cast<size_t>(p) * ri2 + k] *= sw;
+    }
+    pp.pad_ref = sw ? n * sw : n;
     const int64_t slab = 4LL * ql;
-    pp.Wc = (static_cast<int64_t>(runs) * pp.Rp + slab - 1) / slab * slab;
+    pp.Wc = (walkers + slab - 1) / slab * slab;
     return PT2D_OK;
 }
 
@@ -254,18 +314,8 @@ size_t carve(pt2d_ctx *c, void *base) {
     Carver cv(base);
     const int64_t n = pp.n, RR = static_cast<int64_t>(pp.runs) * pp.R;
     c->L.S = cv.take<int8_t>((n + 1) * pp.Wc);
-    int32_t *pid = cv.take<int32_t>(n);
-    int32_t *cofs = cv.take<int32_t>(pp.C + 1);
-    int32_t *nb = cv.take<int32_t>(n * pp.DC);
-    int32_t *jv = cv.take<int32_t>(n * pp.DC);
-    int32_t *lk = cv.take<int32_t>(n * pp.DL);
-    int32_t *h2 = cv.take<int32_t>(n);
-    c->L.pid = pid;
-    c->L.cofs = cofs;
-    c->L.nb = nb;
-    c->L.jv = jv;
-    c->L.lk = lk;
-    c->L.h2 = h2;
+    c->L.rec = cv.take<int4>(n * pp.rec_vec);
+    c->L.cofs = cv.take<int32_t>(pp.C + 1);
     c->wk.wbeta = cv.take<float>(pp.Wc);
     c->wk.wP = cv.take<int32_t>(pp.Wc);
     c->wk.f = cv.take<int64_t>(pp.Wc);
@@ -418,6 +468,8 @@ int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const floa
     c->L.C = pp.C;
     c->L.DC = pp.DC;
     c->L.DL = pp.DL;
+    c->L.rec_vec = pp.rec_vec;
+    c->L.pad_ref = pp.pad_ref;
     c->rs.runs = pp.runs;
     c->rs.I = pp.I;
     c->rs.J = pp.J;
@@ -441,12 +493,8 @@ int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const floa
         const void *h;
         size_t b;
     } ups[] = {
-        {const_cast<int32_t *>(c->L.pid), pp.pid.data(), sizeof(int32_t) * n},
+        {const_cast<int4 *>(c->L.rec), pp.rec.data(), sizeof(int32_t) * pp.rec.size()},
         {const_cast<int32_t *>(c->L.cofs), pp.cofs.data(), sizeof(int32_t) * (pp.C + 1)},
-        {const_cast<int32_t *>(c->L.nb), pp.nb.data(), sizeof(int32_t) * n * pp.DC},
-        {const_cast<int32_t *>(c->L.jv), pp.jv.data(), sizeof(int32_t) * n * pp.DC},
-        {const_cast<int32_t *>(c->L.lk), pp.lk.data(), sizeof(int32_t) * n * pp.DL},
-        {const_cast<int32_t *>(c->L.h2), pp.h2.data(), sizeof(int32_t) * n},
         {c->d_beta, c->beta.data(), sizeof(float) * I},
         {c->d_P, c->P.data(), sizeof(int32_t) * J},
     };

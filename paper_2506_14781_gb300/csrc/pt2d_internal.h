@@ -15,8 +15,11 @@ namespace pt2d {
 //  * Columns: run r owns columns [r * Rp, r * Rp + R); Rp = R rounded up to 4
 //    so that every group of 4 columns (one Philox call) lies in one run; Wc is
 //    the total rounded up to the sweep tile.
-//  * ELL neighbour lists per position: nb[pos][DC] (positions, padding -> n),
-//    jv[pos][DC] = 2 J, lk[pos][DL] (positions, padding -> n), h2[pos] = 2 h.
+//  * One packed record per position, rec_vec int4s: [nb_0..nb_{DC-1} (coupling
+//    neighbours, padding -> zero row), lk_0..lk_{DL-1} (link neighbours, padding
+//    -> zero row), spin id, 2h, 2J_0..2J_{DC-1}, zero padding].  Neighbour
+//    references are row indices for the global-memory kernels and byte offsets
+//    row * SW into the slab for the shared-memory kernel.
 struct Layout {
     int8_t *S;
     int64_t Wc;
@@ -24,12 +27,10 @@ struct Layout {
     int32_t C;
     int32_t DC;
     int32_t DL;
-    const int32_t *pid;   // [n] position -> spin id
+    int32_t rec_vec;      // int4s per record
+    int32_t pad_ref;      // neighbour reference of the zero row (n, or n * SW when scaled)
+    const int4 *rec;      // [n][rec_vec]
     const int32_t *cofs;  // [C + 1] colour class offsets (positions)
-    const int32_t *nb;
-    const int32_t *jv;
-    const int32_t *lk;
-    const int32_t *h2;
 };
 
 struct Walkers {
@@ -62,7 +63,13 @@ struct RunState {
 struct SweepTiling {
     int lanes_per_spin;  // quads (4 walkers) per spin row segment of a CTA
     int threads;         // threads per CTA
+    bool smem;           // slab in shared memory (k_sweep_smem) or global (k_sweep_global)
+    int walkers_per_thread;  // 4, or 8 in the shared-memory kernel
 };
+
+// Dynamic shared memory of k_sweep_smem for n spins and a slab of W walkers.
+size_t smem_sweep_bytes(int32_t n, int walkers_per_cta);
+constexpr size_t kSweepStaticSmem = 2048;  // epilogue reduction arrays and slack
 
 cudaError_t launch_init(const Layout &L, const RunState &rs, const Walkers &wk, uint64_t seed,
                         cudaStream_t st);

@@ -1,22 +1,25 @@
 // CUDA kernels of the 2D-PT library (sm_103a).
 //
-//  k_init_spins     initial state S0 from the seeded init stream (Algorithm 1 input)
-//  k_init_walkers   walker <-> slot identity, per-walker beta/P, best-state sentinels
-//  k_sweep<DC,DL>   `nsweeps` heat-bath sweeps of every walker (the sweep block of one
-//                   event of Algorithm 1), colour class by colour class, then f and g
-//                   of the final sweep (Eq. 1) fused as an epilogue
-//  k_swap_event     one swap event per run: P-swaps (Eq. 2) or beta-swaps (Eq. 3) on
-//                   odd/even pairs, then the bottom-right record (Algorithm 1)
+//  k_init_spins      initial state S0 from the seeded init stream (Algorithm 1 input)
+//  k_init_walkers    walker <-> slot identity, per-walker beta/P, best-state sentinels
+//  k_sweep_smem      the sweep block of one event of Algorithm 1 (`nsweeps` heat-bath
+//                    sweeps of every walker, colour class by colour class) with the
+//                    CTA's replica slab held in shared memory for the whole block, then
+//                    f and g of the final sweep (Eq. 1) as an epilogue
+//  k_sweep_global    the same with the slab in global memory (instances whose slab does
+//                    not fit in shared memory)
+//  k_swap_event      one swap event per run: P-swaps (Eq. 2) or beta-swaps (Eq. 3) on
+//                    odd/even pairs, then the bottom-right record (Algorithm 1)
 //
 // Sweep tiling.  Walkers evolve independently between swap events, so a CTA owns a
-// slab of 4*QL walker columns for every spin and loops over all sweeps of the event
+// slab of SW = 4*QL walker columns for every spin and runs all sweeps of the event
 // with only __syncthreads() between colour classes; no grid-wide barrier is needed.
-// A thread owns one quad (4 consecutive columns = one Philox call per spin) and
-// keeps that quad's beta and P in registers for the whole launch.  QL lanes cover
-// one spin row segment (4*QL bytes, coalesced); the CTA's QL-lane groups take
-// different spins of the current colour class.
+// A thread owns one quad (4 consecutive columns = one Philox call per spin) and keeps
+// the quad's beta and P in registers for the whole launch.  QL lanes cover one spin
+// row segment (4*QL bytes); the CTA's QL-lane groups take different spins of the
+// current colour class.  Per spin the neighbour list is one packed record
+// (positions, spin id, 2h, 2J) read with 16-byte loads.
 #include <cstdint>
-#include <cstdio>
 
 #include "pt2d_device.cuh"
 #include "pt2d_internal.h"
@@ -24,33 +27,288 @@
 namespace pt2d {
 namespace {
 
-__device__ __forceinline__ int sbyte(uint32_t x, int b) {
+// byte b of x, sign-extended (one PRMT in sign-replicate mode)
+template <int b>
+__device__ __forceinline__ int sbyte(uint32_t x) {
+    constexpr uint32_t n = 8u | b;
+    constexpr uint32_t sel = (n << 12) | (n << 8) | (n << 4) | static_cast<uint32_t>(b);
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(x), "n"(sel));
+    return static_cast<int>(d);
+}
+
+__device__ __forceinline__ int sbyte_rt(uint32_t x, int b) {
     return static_cast<int>(static_cast<int8_t>(static_cast<uint8_t>(x >> (8 * b))));
 }
 
-__device__ __forceinline__ uint32_t ld_word(const int8_t *p) {
-    return *reinterpret_cast<const uint32_t *>(p);
+// Spin word from the sign bits of four decision values: byte k = 0x01 (+1) when
+// t_k < 0, 0xFF (-1) otherwise.
+__device__ __forceinline__ uint32_t pack_signs(float t0, float t1, float t2, float t3) {
+    uint32_t lo, hi, m;
+    asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(lo) : "r"(__float_as_uint(t0)), "r"(__float_as_uint(t1)));
+    asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(hi) : "r"(__float_as_uint(t2)), "r"(__float_as_uint(t3)));
+    asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(m) : "r"(lo), "r"(hi));
+    return ~m | 0x01010101u;
 }
 
-__device__ __forceinline__ void st_word(int8_t *p, uint32_t v) {
-    *reinterpret_cast<uint32_t *>(p) = v;
-}
+constexpr int kMaxSlab = 128;  // walkers per CTA
 
-__device__ __forceinline__ uint32_t pack4(int s0, int s1, int s2, int s3) {
-    return (static_cast<uint32_t>(s0) & 0xffu) | ((static_cast<uint32_t>(s1) & 0xffu) << 8) |
-           ((static_cast<uint32_t>(s2) & 0xffu) << 16) | ((static_cast<uint32_t>(s3) & 0xffu) << 24);
-}
-
-constexpr int kMaxSlab = 128;  // walkers per CTA (QL <= 32)
-
-// DC / DL: padded coupling / link degree (compile time), or -1 for the generic
-// kernel that reads them from the layout.
+// Packed neighbour record of one position: [nb_0..nb_{DC-1}, lk_0..lk_{DL-1},
+// pid, 2h, 2J_0..2J_{DC-1}] padded to whole int4s.
 template <int DC, int DL>
-__global__ void __launch_bounds__(256) k_sweep(Layout L, Walkers wk, int ql_shift,
-                                                int32_t quads_per_run, uint32_t k0, uint32_t k1,
-                                                uint32_t sweep0, int32_t nsweeps) {
-    const int dc = DC > 0 ? DC : L.DC;
-    const int dl = DL >= 0 ? DL : L.DL;
+struct Rec {
+    static constexpr int kInts = 2 * DC + DL + 2;
+    static constexpr int kVec = (kInts + 3) / 4;
+    int v[kVec * 4];
+    __device__ __forceinline__ void load(const int4 *base, int pos) {
+        const int4 *p = base + static_cast<int64_t>(pos) * kVec;
+#pragma unroll
+        for (int i = 0; i < kVec; ++i) reinterpret_cast<int4 *>(v)[i] = __ldg(p + i);
+    }
+    __device__ __forceinline__ int nb(int k) const { return v[k]; }
+    __device__ __forceinline__ int lk(int l) const { return v[DC + l]; }
+    __device__ __forceinline__ int pid() const { return v[DC + DL]; }
+    __device__ __forceinline__ int h2() const { return v[DC + DL + 1]; }
+    __device__ __forceinline__ int j2(int k) const { return v[DC + DL + 2 + k]; }
+};
+
+struct Quad {
+    float b0, b1, b2, b3;  // beta of each walker's slot
+    float c0, c1, c2, c3;  // -beta * log2(e)
+    int p0, p1, p2, p3;    // P of each walker's slot
+};
+
+__device__ __forceinline__ Quad load_quad(const Walkers &wk, int64_t col) {
+    const float4 bt = *reinterpret_cast<const float4 *>(wk.wbeta + col);
+    const int4 pj = *reinterpret_cast<const int4 *>(wk.wP + col);
+    const float kNegL2E = -1.4426950408889634f;
+    return Quad{bt.x, bt.y, bt.z, bt.w, bt.x * kNegL2E, bt.y * kNegL2E, bt.z * kNegL2E,
+                bt.w * kNegL2E, pj.x, pj.y, pj.z, pj.w};
+}
+
+// New spin word of one quad at one position.  `fetch(row)` returns the quad's
+// spin word of a row (shared or global memory).
+template <int DC, int DL>
+__device__ __forceinline__ uint32_t decide4(const Rec<DC, DL> &rc, const Quad &q, const uint32_t *x,
+                                            const uint32_t *y, const uint4 &r) {
+    int a0 = rc.h2(), a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        const int j = rc.j2(k);
+        a0 += j * sbyte<0>(x[k]);
+        a1 += j * sbyte<1>(x[k]);
+        a2 += j * sbyte<2>(x[k]);
+        a3 += j * sbyte<3>(x[k]);
+    }
+    int l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+#pragma unroll
+    for (int l = 0; l < DL; ++l) {
+        l0 += sbyte<0>(y[l]);
+        l1 += sbyte<1>(y[l]);
+        l2 += sbyte<2>(y[l]);
+        l3 += sbyte<3>(y[l]);
+    }
+    a0 += q.p0 * l0;
+    a1 += q.p1 * l1;
+    a2 += q.p2 * l2;
+    a3 += q.p3 * l3;
+    float t0 = heatbath_fast(q.c0, a0, r.x), t1 = heatbath_fast(q.c1, a1, r.y);
+    float t2 = heatbath_fast(q.c2, a2, r.z), t3 = heatbath_fast(q.c3, a3, r.w);
+    // one branch for the four band tests; inside it the exact contract decides
+    if (fminf(fminf(fabsf(t0), fabsf(t1)), fminf(fabsf(t2), fabsf(t3))) <= kBand) {
+        if (fabsf(t0) <= kBand) t0 = heatbath_exact(q.b0, a0, r.x) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t1) <= kBand) t1 = heatbath_exact(q.b1, a1, r.y) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t2) <= kBand) t2 = heatbath_exact(q.b2, a2, r.z) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t3) <= kBand) t3 = heatbath_exact(q.b3, a3, r.w) > 0 ? -1.0f : 1.0f;
+    }
+    return pack_signs(t0, t1, t2, t3);
+}
+
+template <int DC, int DL, typename Fetch>
+__device__ __forceinline__ uint32_t update4(const Rec<DC, DL> &rc, const Quad &q, Fetch fetch,
+                                            uint32_t sweep, uint32_t lq, uint32_t c3,
+                                            const RoundKeys &rk) {
+    uint32_t x[DC], y[DL];
+#pragma unroll
+    for (int k = 0; k < DC; ++k) x[k] = fetch(rc.nb(k));
+#pragma unroll
+    for (int l = 0; l < DL; ++l) y[l] = fetch(rc.lk(l));
+    const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3), rk);
+    return decide4<DC, DL>(rc, q, x, y, r);
+}
+
+// Eight walkers (two quads) at one position: one 8-byte fetch per neighbour,
+// two independent Philox calls (quads lq and lq + 1).
+template <int DC, int DL, typename Fetch8>
+__device__ __forceinline__ uint2 update8(const Rec<DC, DL> &rc, const Quad &qa, const Quad &qb,
+                                         Fetch8 fetch8, uint32_t sweep, uint32_t lq, uint32_t c3,
+                                         const RoundKeys &rk) {
+    uint32_t xa[DC], ya[DL], xb[DC], yb[DL];
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        const uint2 w = fetch8(rc.nb(k));
+        xa[k] = w.x;
+        xb[k] = w.y;
+    }
+#pragma unroll
+    for (int l = 0; l < DL; ++l) {
+        const uint2 w = fetch8(rc.lk(l));
+        ya[l] = w.x;
+        yb[l] = w.y;
+    }
+    const uint32_t id = static_cast<uint32_t>(rc.pid());
+    const uint4 ra = philox4x32_10(make_uint4(id, sweep, lq, c3), rk);
+    const uint4 rb = philox4x32_10(make_uint4(id, sweep, lq + 1, c3), rk);
+    return make_uint2(decide4<DC, DL>(rc, qa, xa, ya, ra), decide4<DC, DL>(rc, qb, xb, yb, rb));
+}
+
+// Per-walker f and g of the CTA's slab (epilogue of the sweep kernels); the
+// thread owns NQ quads, its walkers are wbase .. wbase + 4 NQ - 1 of the slab.
+// F = sum_a s_a (sum_b 2J_ab s_b + 2 * 2h_a) = 4 (sum_{a<b} J s s + sum h s), f = -F/4;
+// g counts each broken link from both ends (padding links point at the zero row).
+template <int DC, int DL, int NQ, typename Fetch, typename Own>
+__device__ __forceinline__ void energies(const Layout &L, const Walkers &wk, Fetch fetch, Own own,
+                                         int wbase, int grp, int G, int slab, int64_t col0) {
+    __shared__ long long s_F[kMaxSlab];
+    __shared__ int s_g[kMaxSlab];
+    for (int i = threadIdx.x; i < slab; i += blockDim.x) {
+        s_F[i] = 0;
+        s_g[i] = 0;
+    }
+    __syncthreads();
+    long long F[4 * NQ];
+    int g[4 * NQ];
+#pragma unroll
+    for (int i = 0; i < 4 * NQ; ++i) {
+        F[i] = 0;
+        g[i] = 0;
+    }
+    for (int pos = grp; pos < L.n; pos += G) {
+        Rec<DC, DL> rc;
+        rc.load(L.rec, pos);
+        const int h4 = 2 * rc.h2();
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) {
+            const uint32_t xs = own(pos, h);
+            int c0 = h4, c1 = h4, c2 = h4, c3 = h4;
+#pragma unroll
+            for (int k = 0; k < DC; ++k) {
+                const uint32_t x = fetch(rc.nb(k), h);
+                const int j = rc.j2(k);
+                c0 += j * sbyte<0>(x);
+                c1 += j * sbyte<1>(x);
+                c2 += j * sbyte<2>(x);
+                c3 += j * sbyte<3>(x);
+            }
+            F[4 * h + 0] += static_cast<long long>(sbyte<0>(xs)) * c0;
+            F[4 * h + 1] += static_cast<long long>(sbyte<1>(xs)) * c1;
+            F[4 * h + 2] += static_cast<long long>(sbyte<2>(xs)) * c2;
+            F[4 * h + 3] += static_cast<long long>(sbyte<3>(xs)) * c3;
+#pragma unroll
+            for (int l = 0; l < DL; ++l) {
+                if (rc.lk(l) == L.pad_ref) continue;
+                const uint32_t y = fetch(rc.lk(l), h);
+                g[4 * h + 0] += sbyte<0>(xs) != sbyte<0>(y);
+                g[4 * h + 1] += sbyte<1>(xs) != sbyte<1>(y);
+                g[4 * h + 2] += sbyte<2>(xs) != sbyte<2>(y);
+                g[4 * h + 3] += sbyte<3>(xs) != sbyte<3>(y);
+            }
+        }
+    }
+    unsigned long long *sF = reinterpret_cast<unsigned long long *>(s_F);
+#pragma unroll
+    for (int i = 0; i < 4 * NQ; ++i) {
+        atomicAdd(sF + wbase + i, static_cast<unsigned long long>(F[i]));
+        atomicAdd(&s_g[wbase + i], g[i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < slab; i += blockDim.x) {
+        wk.f[col0 + i] = -(s_F[i] / 4);
+        wk.g[col0 + i] = s_g[i] / 2;
+    }
+}
+
+// Sweep block with the slab in shared memory: (n + 1) rows x SW bytes, loaded
+// once, swept `nsweeps` times, written back once.  SW >= 16; each thread owns
+// WPT = 4 or 8 consecutive walkers of the slab.
+template <int DC, int DL, int WPT>
+__global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
+    k_sweep_smem(Layout L, Walkers wk, int sw_shift, int32_t quads_per_run, RoundKeys rk,
+                 uint32_t sweep0, int32_t nsweeps) {
+    extern __shared__ __align__(16) int8_t sm[];
+    constexpr int NQ = WPT / 4;
+    const int SW = 1 << sw_shift;
+    const int lanes = SW / WPT;  // threads per spin row segment
+    const int lane = threadIdx.x & (lanes - 1);
+    const int grp = threadIdx.x / lanes;
+    const int G = blockDim.x / lanes;
+    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * SW;
+    const int64_t quad = col0 / 4 + static_cast<int64_t>(lane) * NQ;
+    const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
+    const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
+    const uint32_t c3 = (run << 4) | kTagSweep;
+    const int lane_off = WPT * lane;
+    const Quad qa = load_quad(wk, col0 + lane_off);
+    const Quad qb = NQ == 2 ? load_quad(wk, col0 + lane_off + 4) : qa;
+
+    // load the slab, 16 bytes per access
+    const int vec_per_row = SW >> 4;
+    const int64_t nvec = static_cast<int64_t>(L.n + 1) * vec_per_row;
+    for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
+        const int64_t row = i / vec_per_row;
+        const int part = static_cast<int>(i - row * vec_per_row);
+        reinterpret_cast<uint4 *>(sm)[i] =
+            *reinterpret_cast<const uint4 *>(L.S + row * L.Wc + col0 + 16 * part);
+    }
+    __syncthreads();
+
+    // neighbour references in the records are byte offsets row * SW into the slab
+    auto fetch4 = [&](int off) -> uint32_t {
+        return *reinterpret_cast<const uint32_t *>(sm + off + lane_off);
+    };
+    auto fetch8 = [&](int off) -> uint2 {
+        return *reinterpret_cast<const uint2 *>(sm + off + lane_off);
+    };
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
+        for (int c = 0; c < L.C; ++c) {
+            const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                Rec<DC, DL> rc;
+                rc.load(L.rec, pos);
+                int8_t *dst = sm + (pos << sw_shift) + lane_off;
+                if (NQ == 1) {
+                    *reinterpret_cast<uint32_t *>(dst) = update4<DC, DL>(rc, qa, fetch4, sweep, lq, c3, rk);
+                } else {
+                    *reinterpret_cast<uint2 *>(dst) = update8<DC, DL>(rc, qa, qb, fetch8, sweep, lq, c3, rk);
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // write the slab back (rows 0..n-1)
+    const int64_t nvec_out = static_cast<int64_t>(L.n) * vec_per_row;
+    for (int64_t i = threadIdx.x; i < nvec_out; i += blockDim.x) {
+        const int64_t row = i / vec_per_row;
+        const int part = static_cast<int>(i - row * vec_per_row);
+        *reinterpret_cast<uint4 *>(L.S + row * L.Wc + col0 + 16 * part) =
+            reinterpret_cast<const uint4 *>(sm)[i];
+    }
+    auto fetch_q = [&](int off, int h) -> uint32_t {
+        return *reinterpret_cast<const uint32_t *>(sm + off + lane_off + 4 * h);
+    };
+    auto own_q = [&](int pos, int h) -> uint32_t {
+        return *reinterpret_cast<const uint32_t *>(sm + (pos << sw_shift) + lane_off + 4 * h);
+    };
+    energies<DC, DL, NQ>(L, wk, fetch_q, own_q, lane_off, grp, G, SW, col0);
+}
+
+// Sweep block with the slab in global memory.
+template <int DC, int DL>
+__global__ void __launch_bounds__(256) k_sweep_global(Layout L, Walkers wk, int ql_shift,
+                                                      int32_t quads_per_run, RoundKeys rk,
+                                                      uint32_t sweep0, int32_t nsweeps) {
     const int QL = 1 << ql_shift;
     const int lane_q = threadIdx.x & (QL - 1);
     const int grp = threadIdx.x >> ql_shift;
@@ -60,85 +318,88 @@ __global__ void __launch_bounds__(256) k_sweep(Layout L, Walkers wk, int ql_shif
     const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
     const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
     const uint32_t c3 = (run << 4) | kTagSweep;
-
-    const float4 bt = *reinterpret_cast<const float4 *>(wk.wbeta + col);
-    const int4 pj = *reinterpret_cast<const int4 *>(wk.wP + col);
-    const float kNegL2E = -1.4426950408889634f;
-    const float n0 = bt.x * kNegL2E, n1 = bt.y * kNegL2E, n2 = bt.z * kNegL2E, n3 = bt.w * kNegL2E;
+    const Quad q = load_quad(wk, col);
     int8_t *__restrict__ S = L.S;
     const int64_t Wc = L.Wc;
-
+    auto fetch = [&](int row) -> uint32_t {
+        return *reinterpret_cast<const uint32_t *>(S + static_cast<int64_t>(row) * Wc + col);
+    };
     for (int t = 0; t < nsweeps; ++t) {
         const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
         for (int c = 0; c < L.C; ++c) {
             const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
             for (int pos = beg + grp; pos < end; pos += G) {
-                const int h2 = __ldg(L.h2 + pos);
-                int a0 = h2, a1 = h2, a2 = h2, a3 = h2;
-                const int32_t *nbp = L.nb + static_cast<int64_t>(pos) * dc;
-                const int32_t *jvp = L.jv + static_cast<int64_t>(pos) * dc;
-#pragma unroll
-                for (int k = 0; k < (DC > 0 ? DC : 1); ++k) {
-                    // compile-time trip count when DC > 0; generic loop below otherwise
-                    if (DC <= 0) break;
-                    const int j2 = __ldg(jvp + k);
-                    const uint32_t x = ld_word(S + static_cast<int64_t>(__ldg(nbp + k)) * Wc + col);
-                    a0 += j2 * sbyte(x, 0);
-                    a1 += j2 * sbyte(x, 1);
-                    a2 += j2 * sbyte(x, 2);
-                    a3 += j2 * sbyte(x, 3);
-                }
-                if (DC <= 0) {
-                    for (int k = 0; k < dc; ++k) {
-                        const int j2 = __ldg(jvp + k);
-                        const uint32_t x =
-                            ld_word(S + static_cast<int64_t>(__ldg(nbp + k)) * Wc + col);
-                        a0 += j2 * sbyte(x, 0);
-                        a1 += j2 * sbyte(x, 1);
-                        a2 += j2 * sbyte(x, 2);
-                        a3 += j2 * sbyte(x, 3);
-                    }
-                }
-                int l0 = 0, l1 = 0, l2 = 0, l3 = 0;
-                const int32_t *lkp = L.lk + static_cast<int64_t>(pos) * dl;
-#pragma unroll
-                for (int k = 0; k < (DL > 0 ? DL : 1); ++k) {
-                    if (DL <= 0) break;
-                    const uint32_t y = ld_word(S + static_cast<int64_t>(__ldg(lkp + k)) * Wc + col);
-                    l0 += sbyte(y, 0);
-                    l1 += sbyte(y, 1);
-                    l2 += sbyte(y, 2);
-                    l3 += sbyte(y, 3);
-                }
-                if (DL < 0) {
-                    for (int k = 0; k < dl; ++k) {
-                        const uint32_t y =
-                            ld_word(S + static_cast<int64_t>(__ldg(lkp + k)) * Wc + col);
-                        l0 += sbyte(y, 0);
-                        l1 += sbyte(y, 1);
-                        l2 += sbyte(y, 2);
-                        l3 += sbyte(y, 3);
-                    }
-                }
-                a0 += pj.x * l0;
-                a1 += pj.y * l1;
-                a2 += pj.z * l2;
-                a3 += pj.w * l3;
-                const uint4 r = philox4x32_10(
-                    make_uint4(static_cast<uint32_t>(__ldg(L.pid + pos)), sweep, lq, c3), k0, k1);
-                const int s0 = heatbath(bt.x, n0, a0, r.x);
-                const int s1 = heatbath(bt.y, n1, a1, r.y);
-                const int s2 = heatbath(bt.z, n2, a2, r.z);
-                const int s3 = heatbath(bt.w, n3, a3, r.w);
-                st_word(S + static_cast<int64_t>(pos) * Wc + col, pack4(s0, s1, s2, s3));
+                Rec<DC, DL> rc;
+                rc.load(L.rec, pos);
+                const uint32_t w = update4<DC, DL>(rc, q, fetch, sweep, lq, c3, rk);
+                *reinterpret_cast<uint32_t *>(S + static_cast<int64_t>(pos) * Wc + col) = w;
             }
             __syncthreads();
         }
     }
+    auto fetch_q = [&](int row, int) -> uint32_t { return fetch(row); };
+    energies<DC, DL, 1>(L, wk, fetch_q, fetch_q, 4 * lane_q, grp, G, 4 * QL,
+                        static_cast<int64_t>(blockIdx.x) * QL * 4);
+}
 
-    // Epilogue: f and g of the final sweep for the CTA's walkers (Eq. 1).
-    // F = sum_a s_a (sum_b 2J_ab s_b + 2 * 2h_a) = 4 (sum_{a<b} J s s + sum h s), f = -F/4;
-    // g counts each broken link from both ends.
+// Generic degrees (any DC, DL read from the layout), global memory.
+__global__ void __launch_bounds__(256) k_sweep_generic(Layout L, Walkers wk, int ql_shift,
+                                                       int32_t quads_per_run, RoundKeys rk,
+                                                       uint32_t sweep0, int32_t nsweeps) {
+    const int QL = 1 << ql_shift;
+    const int lane_q = threadIdx.x & (QL - 1);
+    const int grp = threadIdx.x >> ql_shift;
+    const int G = blockDim.x >> ql_shift;
+    const int64_t quad = static_cast<int64_t>(blockIdx.x) * QL + lane_q;
+    const int64_t col = quad * 4;
+    const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
+    const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
+    const uint32_t c3 = (run << 4) | kTagSweep;
+    const Quad q = load_quad(wk, col);
+    const int DC = L.DC, DL = L.DL;
+    const int rec_ints = L.rec_vec * 4;
+    const int *recs = reinterpret_cast<const int *>(L.rec);
+    int8_t *__restrict__ S = L.S;
+    const int64_t Wc = L.Wc;
+    auto word = [&](int row) -> uint32_t {
+        return *reinterpret_cast<const uint32_t *>(S + static_cast<int64_t>(row) * Wc + col);
+    };
+    const float bq[4] = {q.b0, q.b1, q.b2, q.b3};
+    const float cq[4] = {q.c0, q.c1, q.c2, q.c3};
+    const int pq[4] = {q.p0, q.p1, q.p2, q.p3};
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
+        for (int c = 0; c < L.C; ++c) {
+            const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                const int *rc = recs + static_cast<int64_t>(pos) * rec_ints;
+                const int h2 = __ldg(rc + DC + DL + 1);
+                int a[4] = {h2, h2, h2, h2};
+                int l[4] = {0, 0, 0, 0};
+                for (int k = 0; k < DC; ++k) {
+                    const uint32_t x = word(__ldg(rc + k));
+                    const int j = __ldg(rc + DC + DL + 2 + k);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) a[b] += j * sbyte_rt(x, b);
+                }
+                for (int k = 0; k < DL; ++k) {
+                    const uint32_t y = word(__ldg(rc + DC + k));
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) l[b] += sbyte_rt(y, b);
+                }
+                const uint4 r = philox4x32_10(
+                    make_uint4(static_cast<uint32_t>(__ldg(rc + DC + DL)), sweep, lq, c3), rk);
+                const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+                float tv[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) tv[b] = heatbath_t(bq[b], cq[b], a[b] + pq[b] * l[b], rr[b]);
+                *reinterpret_cast<uint32_t *>(S + static_cast<int64_t>(pos) * Wc + col) =
+                    pack_signs(tv[0], tv[1], tv[2], tv[3]);
+            }
+            __syncthreads();
+        }
+    }
+    // epilogue
     __shared__ long long s_F[kMaxSlab];
     __shared__ int s_g[kMaxSlab];
     for (int i = threadIdx.x; i < 4 * QL; i += blockDim.x) {
@@ -146,43 +407,35 @@ __global__ void __launch_bounds__(256) k_sweep(Layout L, Walkers wk, int ql_shif
         s_g[i] = 0;
     }
     __syncthreads();
-    long long F0 = 0, F1 = 0, F2 = 0, F3 = 0;
-    int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+    long long F[4] = {0, 0, 0, 0};
+    int g[4] = {0, 0, 0, 0};
     for (int pos = grp; pos < L.n; pos += G) {
-        const uint32_t xs = ld_word(S + static_cast<int64_t>(pos) * Wc + col);
-        const int h4 = 2 * __ldg(L.h2 + pos);
-        int c0 = h4, c1 = h4, c2 = h4, cc3 = h4;
-        for (int k = 0; k < dc; ++k) {
-            const int j2 = __ldg(L.jv + static_cast<int64_t>(pos) * dc + k);
-            const uint32_t x =
-                ld_word(S + static_cast<int64_t>(__ldg(L.nb + static_cast<int64_t>(pos) * dc + k)) * Wc + col);
-            c0 += j2 * sbyte(x, 0);
-            c1 += j2 * sbyte(x, 1);
-            c2 += j2 * sbyte(x, 2);
-            cc3 += j2 * sbyte(x, 3);
+        const int *rc = recs + static_cast<int64_t>(pos) * rec_ints;
+        const uint32_t xs = word(pos);
+        const int h4 = 2 * __ldg(rc + DC + DL + 1);
+        int cc[4] = {h4, h4, h4, h4};
+        for (int k = 0; k < DC; ++k) {
+            const uint32_t x = word(__ldg(rc + k));
+            const int j = __ldg(rc + DC + DL + 2 + k);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cc[b] += j * sbyte_rt(x, b);
         }
-        F0 += static_cast<long long>(sbyte(xs, 0)) * c0;
-        F1 += static_cast<long long>(sbyte(xs, 1)) * c1;
-        F2 += static_cast<long long>(sbyte(xs, 2)) * c2;
-        F3 += static_cast<long long>(sbyte(xs, 3)) * cc3;
-        for (int k = 0; k < dl; ++k) {
-            const int lp = __ldg(L.lk + static_cast<int64_t>(pos) * dl + k);
-            if (lp == L.n) continue;
-            const uint32_t y = ld_word(S + static_cast<int64_t>(lp) * Wc + col);
-            g0 += sbyte(xs, 0) != sbyte(y, 0);
-            g1 += sbyte(xs, 1) != sbyte(y, 1);
-            g2 += sbyte(xs, 2) != sbyte(y, 2);
-            g3 += sbyte(xs, 3) != sbyte(y, 3);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) F[b] += static_cast<long long>(sbyte_rt(xs, b)) * cc[b];
+        for (int k = 0; k < DL; ++k) {
+            const int lp = __ldg(rc + DC + k);
+            if (lp == L.pad_ref) continue;
+            const uint32_t y = word(lp);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) g[b] += sbyte_rt(xs, b) != sbyte_rt(y, b);
         }
     }
-    atomicAdd(reinterpret_cast<unsigned long long *>(&s_F[lane_q * 4 + 0]), static_cast<unsigned long long>(F0));
-    atomicAdd(reinterpret_cast<unsigned long long *>(&s_F[lane_q * 4 + 1]), static_cast<unsigned long long>(F1));
-    atomicAdd(reinterpret_cast<unsigned long long *>(&s_F[lane_q * 4 + 2]), static_cast<unsigned long long>(F2));
-    atomicAdd(reinterpret_cast<unsigned long long *>(&s_F[lane_q * 4 + 3]), static_cast<unsigned long long>(F3));
-    atomicAdd(&s_g[lane_q * 4 + 0], g0);
-    atomicAdd(&s_g[lane_q * 4 + 1], g1);
-    atomicAdd(&s_g[lane_q * 4 + 2], g2);
-    atomicAdd(&s_g[lane_q * 4 + 3], g3);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&s_F[lane_q * 4 + b]),
+                  static_cast<unsigned long long>(F[b]));
+        atomicAdd(&s_g[lane_q * 4 + b], g[b]);
+    }
     __syncthreads();
     const int64_t col0 = static_cast<int64_t>(blockIdx.x) * QL * 4;
     for (int i = threadIdx.x; i < 4 * QL; i += blockDim.x) {
@@ -194,17 +447,19 @@ __global__ void __launch_bounds__(256) k_sweep(Layout L, Walkers wk, int ql_shif
 __global__ void k_init_spins(Layout L, int32_t quads_per_run, uint32_t k0, uint32_t k1) {
     const int64_t quads = L.Wc / 4;
     const int64_t total = static_cast<int64_t>(L.n) * quads;
+    const int *recs = reinterpret_cast<const int *>(L.rec);
+    const int pid_at = L.DC + L.DL;
     for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t pos = e / quads;
         const int64_t quad = e - pos * quads;
         const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
         const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
-        const uint4 r = philox4x32_10(
-            make_uint4(static_cast<uint32_t>(L.pid[pos]), 0u, lq, (run << 4) | kTagInit), k0, k1);
-        const uint32_t w = pack4(r.x < 0x80000000u ? 1 : -1, r.y < 0x80000000u ? 1 : -1,
-                                 r.z < 0x80000000u ? 1 : -1, r.w < 0x80000000u ? 1 : -1);
-        st_word(L.S + pos * L.Wc + quad * 4, w);
+        const uint32_t pid = static_cast<uint32_t>(recs[pos * L.rec_vec * 4 + pid_at]);
+        const uint4 r = philox4x32_10(make_uint4(pid, 0u, lq, (run << 4) | kTagInit), k0, k1);
+        const uint32_t w = pack_signs(r.x < 0x80000000u ? -1.0f : 1.0f, r.y < 0x80000000u ? -1.0f : 1.0f,
+                                      r.z < 0x80000000u ? -1.0f : 1.0f, r.w < 0x80000000u ? -1.0f : 1.0f);
+        *reinterpret_cast<uint32_t *>(L.S + pos * L.Wc + quad * 4) = w;
     }
 }
 
@@ -305,8 +560,10 @@ __global__ void k_swap_event(Layout L, RunState rs, Walkers wk, uint32_t k0, uin
     __syncthreads();
     const int wcopy = s_copy;
     if (wcopy >= 0) {
+        const int *recs = reinterpret_cast<const int *>(L.rec);
+        const int pid_at = L.DC + L.DL;
         for (int pos = threadIdx.x; pos < L.n; pos += blockDim.x)
-            rs.best_state[static_cast<int64_t>(run) * L.n + L.pid[pos]] =
+            rs.best_state[static_cast<int64_t>(run) * L.n + recs[static_cast<int64_t>(pos) * L.rec_vec * 4 + pid_at]] =
                 L.S[static_cast<int64_t>(pos) * L.Wc + cb + wcopy];
     }
 }
@@ -343,7 +600,46 @@ cudaError_t to_device(T **d, const T *h, int64_t count) {
     return cudaMemcpy(*d, h, sizeof(T) * count, cudaMemcpyHostToDevice);
 }
 
+template <int DC, int DL, int WPT>
+cudaError_t launch_smem_variant(const Layout &L, const Walkers &wk, const SweepTiling &tl,
+                                int32_t qpr, const RoundKeys &rk, uint32_t sweep0,
+                                int32_t nsweeps, cudaStream_t st) {
+    int shift = 0;
+    while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
+    const size_t smem = static_cast<size_t>(L.n + 1) << shift;
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_smem<DC, DL, WPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
+    k_sweep_smem<DC, DL, WPT><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
+    return cudaGetLastError();
+}
+
+template <int DC, int DL>
+cudaError_t launch_smem(const Layout &L, const Walkers &wk, const SweepTiling &tl, int32_t qpr,
+                        const RoundKeys &rk, uint32_t sweep0, int32_t nsweeps, cudaStream_t st) {
+    if (tl.walkers_per_thread == 8)
+        return launch_smem_variant<DC, DL, 8>(L, wk, tl, qpr, rk, sweep0, nsweeps, st);
+    return launch_smem_variant<DC, DL, 4>(L, wk, tl, qpr, rk, sweep0, nsweeps, st);
+}
+
+template <int DC, int DL>
+cudaError_t launch_global_variant(const Layout &L, const Walkers &wk, const SweepTiling &tl,
+                                  int32_t qpr, const RoundKeys &rk, uint32_t sweep0,
+                                  int32_t nsweeps, cudaStream_t st) {
+    int shift = 0;
+    while ((1 << shift) < tl.lanes_per_spin) ++shift;
+    const unsigned blocks = static_cast<unsigned>(L.Wc / (4LL * tl.lanes_per_spin));
+    k_sweep_global<DC, DL><<<blocks, tl.threads, 0, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t smem_sweep_bytes(int32_t n, int walkers_per_cta) {
+    return static_cast<size_t>(n + 1) * static_cast<size_t>(walkers_per_cta);
+}
 
 // ---- launchers --------------------------------------------------------------
 cudaError_t launch_init(const Layout &L, const RunState &rs, const Walkers &wk, uint64_t seed,
@@ -361,20 +657,23 @@ cudaError_t launch_init(const Layout &L, const RunState &rs, const Walkers &wk, 
 cudaError_t launch_sweeps(const Layout &L, const Walkers &wk, const SweepTiling &tl,
                           int32_t quads_per_run, uint64_t seed, uint32_t sweep0, int32_t nsweeps,
                           cudaStream_t st) {
-    const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    const RoundKeys rk = round_keys(seed);
+    if (tl.smem) {
+        if (L.DC == 3 && L.DL == 2) return launch_smem<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        if (L.DC == 4 && L.DL == 2) return launch_smem<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        if (L.DC == 6 && L.DL == 2) return launch_smem<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        return cudaErrorInvalidValue;
+    }
+    if (L.DC == 3 && L.DL == 2)
+        return launch_global_variant<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+    if (L.DC == 4 && L.DL == 2)
+        return launch_global_variant<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+    if (L.DC == 6 && L.DL == 2)
+        return launch_global_variant<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
     int shift = 0;
     while ((1 << shift) < tl.lanes_per_spin) ++shift;
-    const int64_t slab = 4LL * tl.lanes_per_spin;
-    const unsigned blocks = static_cast<unsigned>(L.Wc / slab);
-    const int threads = tl.threads;
-    if (L.DC == 3 && L.DL == 2)
-        k_sweep<3, 2><<<blocks, threads, 0, st>>>(L, wk, shift, quads_per_run, k0, k1, sweep0, nsweeps);
-    else if (L.DC == 4 && L.DL == 2)
-        k_sweep<4, 2><<<blocks, threads, 0, st>>>(L, wk, shift, quads_per_run, k0, k1, sweep0, nsweeps);
-    else if (L.DC == 6 && L.DL == 2)
-        k_sweep<6, 2><<<blocks, threads, 0, st>>>(L, wk, shift, quads_per_run, k0, k1, sweep0, nsweeps);
-    else
-        k_sweep<-1, -1><<<blocks, threads, 0, st>>>(L, wk, shift, quads_per_run, k0, k1, sweep0, nsweeps);
+    const unsigned blocks = static_cast<unsigned>(L.Wc / (4LL * tl.lanes_per_spin));
+    k_sweep_generic<<<blocks, tl.threads, 0, st>>>(L, wk, shift, quads_per_run, rk, sweep0, nsweeps);
     return cudaGetLastError();
 }
 
@@ -386,8 +685,7 @@ cudaError_t launch_swap_event(const Layout &L, const RunState &rs, const Walkers
     const int parity = (event % 2 == 0) ? 1 : 0;
     const int dir_p = (((event - 1) / 2) % 2 == 0) ? 1 : 0;
     const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
-    int threads = 256;
-    k_swap_event<<<rs.runs, threads, sizeof(int) * rs.R, st>>>(L, rs, wk, k0, k1, event, dir_p, parity);
+    k_swap_event<<<rs.runs, 256, sizeof(int) * rs.R, st>>>(L, rs, wk, k0, k1, event, dir_p, parity);
     return cudaGetLastError();
 }
 

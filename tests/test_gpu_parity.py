@@ -55,14 +55,14 @@ def assert_same(pt, ctx, orc, runs_sel=None, trace=True):
 
 
 def both(pt, inst_q, Jrule, beta, P, runs, seed, schedule, *, target=None, trace=64, wpc=0,
-         threads=0, phys=None):
+         threads=0, phys=None, kernel="auto", wpt=0):
     if phys is None:
         phys_p = pt.sparsify(inst_q.Jq, *Jrule)
         phys_o = oracle.sparsify(inst_q.Jq, *Jrule)
     else:
         phys_p, phys_o = phys
     ctx = pt.PT2D(phys_p, beta, P, runs, trace_capacity=trace, walkers_per_cta=wpc,
-                  threads_per_cta=threads)
+                  threads_per_cta=threads, sweep_kernel=kernel, walkers_per_thread=wpt)
     orc = oracle.OracleRun(oracle.OracleInstance(phys_o), beta, P, list(range(runs)), seed,
                            trace_cap=trace, target=target)
     if target is not None:
@@ -156,15 +156,32 @@ def test_tiny_config_bit_exact_full_length(pt, tiny_config):
     assert orc.best_f[0] == cfg["inst"].E_planted  # the planted ground state is reached
 
 
-@pytest.mark.parametrize("wpc,threads", [(4, 32), (16, 64), (32, 256), (128, 256), (0, 0)])
-def test_ragged_tiles_and_resume(pt, wpc, threads):
+@pytest.mark.parametrize("kernel,wpc,threads,wpt", [
+    ("global", 4, 32, 0), ("global", 16, 64, 0), ("global", 32, 256, 0), ("global", 128, 256, 0),
+    ("smem", 16, 32, 4), ("smem", 32, 64, 4), ("smem", 64, 1024, 4), ("smem", 128, 128, 4),
+    ("smem", 16, 64, 8), ("smem", 64, 512, 8), ("smem", 128, 32, 8), ("auto", 0, 0, 0)])
+def test_ragged_tiles_and_resume(pt, kernel, wpc, threads, wpt):
     inst = synth.wishart_planted(30, 0.5, 21)
     beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
     P = synth.penalty_ladder(3, 0.5, 4.0, 32767)
     # R = 15 (not a multiple of 4), 7 runs, interval 7, resumed once, a trailing partial block
     ctx, orc = both(pt, inst, ("max_edges", 3), beta, P, 7, 0xDEADBEEF12345,
-                    [(35, 7), (20, 7), (7, 7)], target=inst.E_planted, wpc=wpc, threads=threads)
+                    [(35, 7), (20, 7), (7, 7)], target=inst.E_planted, wpc=wpc, threads=threads,
+                    kernel=kernel, wpt=wpt)
     assert_same(pt, ctx, orc)
+
+
+@pytest.mark.parametrize("kernel,wpt", [("global", 0), ("smem", 4), ("smem", 8)])
+def test_degree_layouts_both_kernels(pt, kernel, wpt):
+    """Specialised neighbour layouts DC = 4 and 6 (max-degree and fixed-copy
+    sparsifications), on both sweep kernels."""
+    for N, rule, seed in ((40, ("max_degree", 4), 3), (12, ("fixed", 2), 5), (13, ("fixed", 3), 6)):
+        inst = synth.wishart_planted(N, 0.5, seed)
+        beta = synth.beta_ladder(4, 0.2, 2.0, inst.scale)
+        P = synth.penalty_ladder(4, 0.5, 4.0, 32767)
+        ctx, orc = both(pt, inst, rule, beta, P, 3, 77, [(24, 3)], kernel=kernel,
+                        wpc=16 if kernel == "smem" else 0, wpt=wpt)
+        assert_same(pt, ctx, orc)
 
 
 def test_generic_degree_kernel_with_fields(pt):

@@ -135,9 +135,10 @@ def test_heatbath_matches_sigmoid(beta, H):
     p_ref = _sigmoid(b32 * H)
     assert abs(p_real - p_ref) <= 2e-6, (p_real, p_ref)
     if H == 0:
-        assert count == 2**22
+        # d = 2 exactly; u = (m+1) 2^-23 < 1/2 for m = 0 .. 2^22 - 2
+        assert count == 2**22 - 1
     if H > 0:
-        assert count > 2**22  # the field favours +1 when E(+1) < E(-1)
+        assert count > 2**22 - 1  # the field favours +1 when E(+1) < E(-1)
 
 
 @pytest.mark.parametrize("x", [0.0, 1.5, -1e-7, -0.01, -0.69314718, -1.0, -5.0, -16.0, -40.0])
