@@ -196,6 +196,73 @@ const char *pt2d_strerror(int status);
 /* Last CUDA error code (cudaError_t) recorded by the context, 0 if none. */
 int pt2d_cuda_error(const pt2d_ctx *ctx);
 
+/* ---- batched persistent form ------------------------------------------------ */
+/* Many independent 2D-PT problems of uneven size (each an instance with its own
+ * ladders, runs and seed) simulated by one persistent kernel (Algorithm 1 for
+ * each run).  A CTA owns one whole run (I * J <= 128 replicas) and carries it
+ * through the requested events: sweeps, f and g of the final sweep, the swap
+ * event and the bottom-right record, without leaving the kernel; CTAs take
+ * runs from a work list sorted by decreasing size.  A run's spins stay in
+ * shared memory for the launch when they fit.  Launches are replayed from a
+ * CUDA graph.  Each run follows exactly the trajectory of a context created
+ * with pt2d_create on the same instance and ladders, run with the same seed
+ * (run r of an instance uses run index r).
+ *
+ * Memory: the batch owns a device pool (or uses opt->workspace); instances are
+ * added and removed at any time between launches (continuous batching), and
+ * pt2d_batch_add fails with PT2D_ERR_OOM, leaving the batch unchanged, when
+ * the pool has no room.  All calls are on the batch stream (opt->stream, or a
+ * stream the batch creates). */
+typedef struct pt2d_batch pt2d_batch;
+
+/* pool_bytes: device bytes for instances (ignored with opt->workspace, whose
+ * size then includes the batch's bookkeeping); max_coupling_degree: largest
+ * number of coupling neighbours of any spin that will be added (<= 6; links
+ * <= 2 per spin); max_runs: most runs alive at once.  opt: stream, workspace,
+ * trace_capacity, threads_per_cta (128..1024), sweep_kernel (1 = keep spins in
+ * global memory), device.  Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED. */
+int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_degree,
+                      int32_t max_runs, const pt2d_options *opt);
+
+/* Device bytes pt2d_batch_add would take for this problem (0 if invalid). */
+size_t pt2d_batch_instance_bytes(const pt2d_batch *b, const pt2d_instance *inst, int32_t I,
+                                 int32_t J, int32_t runs);
+
+/* Add a problem: instance, ladders (as for pt2d_create), `runs` runs seeded by
+ * `seed`, target[runs] (solved iff bottom-right g == 0 and f <= target) or
+ * NULL.  Its spins are initialised at its first event.  *id receives the
+ * problem's id.  Errors: INVALID_ARG (also I * J > 128 or a degree above the
+ * batch's), OOM (pool full), CUDA. */
+int pt2d_batch_add(pt2d_batch *b, const pt2d_instance *inst, int32_t I, const float *beta,
+                   int32_t J, const int32_t *P, int32_t runs, uint64_t seed,
+                   const int64_t *target, int64_t *id);
+
+/* Remove a problem and return its memory to the pool.  Errors: INVALID_ARG. */
+int pt2d_batch_remove(pt2d_batch *b, int64_t id);
+
+/* Advance every run of every problem by `events` swap events of
+ * `swap_interval` sweeps (one launch).  Asynchronous.  Errors: INVALID_ARG,
+ * OOM (more runs than max_runs), CUDA. */
+int pt2d_batch_run(pt2d_batch *b, int32_t events, int32_t swap_interval);
+
+/* Time every launch shape (threads per CTA 256 / 512 / 1024; spins in shared
+ * or global memory) on two launches of `events` events each and keep the
+ * fastest.  The trial launches advance the chains like pt2d_batch_run (every
+ * shape computes the same trajectories).  Outputs may be NULL. */
+int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval,
+                        int32_t *threads_per_cta, int32_t *smem_state_bytes);
+
+/* Copy array `what` (the PT2D_* arrays of pt2d_read, for this problem's runs)
+ * to host memory; synchronises.  Errors: INVALID_ARG, STATE, CUDA. */
+int pt2d_batch_read(pt2d_batch *b, int64_t id, int32_t what, void *host_dst, size_t bytes);
+size_t pt2d_batch_array_bytes(const pt2d_batch *b, int64_t id, int32_t what);
+
+int pt2d_batch_sync(pt2d_batch *b);
+size_t pt2d_batch_free_bytes(const pt2d_batch *b);   /* largest free block of the pool */
+int64_t pt2d_batch_launch_count(const pt2d_batch *b);
+int pt2d_batch_cuda_error(const pt2d_batch *b);
+void pt2d_batch_destroy(pt2d_batch *b);
+
 /* ---- one-shot run without device allocation ------------------------------ */
 /* The paper has no counterpart to this entry point; it exists for callers that
  * cannot call cudaMalloc, for example a host program whose device memory is

@@ -18,7 +18,8 @@ from ._lib import (ACC_B, ACC_P, BEST_EVENT, BEST_F, BEST_STATE, COLORS, COUNTER
                    WALKER_AT, Pt2dError)
 
 __all__ = [
-    "PhysicalInstance", "sparsify", "greedy_color", "PT2D", "Pt2dError", "diag_philox",
+    "PhysicalInstance", "sparsify", "greedy_color", "PT2D", "Batch", "PoolFull", "Pt2dError",
+    "diag_philox",
     "diag_pt_exp", "diag_heatbath", "diag_swap_accept", "STATES", "WALKER_AT", "F", "G",
     "COUNTERS", "TRACE_F", "TRACE_G", "BEST_F", "BEST_EVENT", "BEST_STATE", "SOLVED_EVENT",
     "ACC_P", "ACC_B", "SUM_F", "SUM_G", "N_FEASIBLE", "COLORS", "TARGET",
@@ -225,6 +226,116 @@ class PT2D:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _array_spec(what, runs, R, n, T):
+    q = runs
+    return {
+        STATES: ((q, R, n), np.int8), WALKER_AT: ((q, R), np.int32), F: ((q, R), np.int64),
+        G: ((q, R), np.int64), COUNTERS: ((4,), np.int64), TRACE_F: ((q, T), np.int64),
+        TRACE_G: ((q, T), np.int64), BEST_F: ((q,), np.int64), BEST_EVENT: ((q,), np.int64),
+        BEST_STATE: ((q, n), np.int8), SOLVED_EVENT: ((q,), np.int64),
+        ACC_P: ((q, R), np.int64), ACC_B: ((q, R), np.int64), SUM_F: ((q, R), np.int64),
+        SUM_G: ((q, R), np.int64), N_FEASIBLE: ((q, R), np.int64), COLORS: ((n,), np.int32),
+        TARGET: ((q,), np.int64),
+    }[what]
+
+
+class PoolFull(Pt2dError):
+    """The batch's device pool has no room for this problem (PT2D_ERR_OOM)."""
+
+
+class Batch:
+    """Batched persistent 2D-PT (pt2d_batch_*): many problems of uneven size in
+    one persistent kernel, added and removed between launches."""
+
+    def __init__(self, pool_bytes: int, max_coupling_degree: int = 3, max_runs: int = 4096, *,
+                 stream=None, trace_capacity: int = 1024, threads_per_cta: int = 0,
+                 spins_in_global: bool = False, device: int = -1):
+        L = _lib.lib()
+        opt = _lib.Options()
+        L.pt2d_default_options(C.byref(opt))
+        opt.trace_capacity = int(trace_capacity)
+        opt.threads_per_cta = int(threads_per_cta)
+        opt.sweep_kernel = 1 if spins_in_global else 0
+        opt.device = int(device)
+        self._stream_obj = stream
+        if stream is not None:
+            opt.stream = int(getattr(stream, "cuda_stream", stream))
+        self.trace_capacity = int(trace_capacity)
+        self._b = C.c_void_p()
+        _lib.check(L.pt2d_batch_create(C.byref(self._b), int(pool_bytes), int(max_coupling_degree),
+                                       int(max_runs), C.byref(opt)), "pt2d_batch_create")
+        self._meta = {}
+        self._keep = {}
+
+    def instance_bytes(self, inst: PhysicalInstance, I: int, J: int, runs: int) -> int:
+        cs = inst.c_struct()
+        return int(_lib.lib().pt2d_batch_instance_bytes(self._b, C.byref(cs), int(I), int(J), int(runs)))
+
+    def add(self, inst: PhysicalInstance, beta, P, runs: int, seed: int, target=None) -> int:
+        beta = np.ascontiguousarray(beta, dtype=np.float32)
+        P = np.ascontiguousarray(P, dtype=np.int32)
+        tgt = None if target is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(target, dtype=np.int64), (int(runs),)))
+        cs = inst.c_struct()
+        bid = C.c_int64()
+        st = _lib.lib().pt2d_batch_add(self._b, C.byref(cs), beta.size, _p(beta), P.size, _p(P),
+                                       int(runs), int(seed), _p(tgt), C.byref(bid))
+        if st == -2:
+            raise PoolFull(st, "pt2d_batch_add")
+        _lib.check(st, "pt2d_batch_add")
+        self._meta[bid.value] = (int(runs), beta.size * P.size, int(inst.n))
+        return bid.value
+
+    def remove(self, bid: int) -> None:
+        _lib.check(_lib.lib().pt2d_batch_remove(self._b, int(bid)), "pt2d_batch_remove")
+        self._meta.pop(bid, None)
+
+    def run(self, events: int, swap_interval: int) -> None:
+        st = _lib.lib().pt2d_batch_run(self._b, int(events), int(swap_interval))
+        if st != 0:
+            raise Pt2dError(st, "pt2d_batch_run", _lib.lib().pt2d_batch_cuda_error(self._b))
+
+    def autotune(self, events: int, swap_interval: int):
+        t = C.c_int32()
+        sm = C.c_int32()
+        st = _lib.lib().pt2d_batch_autotune(self._b, int(events), int(swap_interval), C.byref(t),
+                                            C.byref(sm))
+        if st != 0:
+            raise Pt2dError(st, "pt2d_batch_autotune", _lib.lib().pt2d_batch_cuda_error(self._b))
+        return t.value, sm.value
+
+    def read(self, bid: int, what: int) -> np.ndarray:
+        runs, R, n = self._meta[bid]
+        shape, dt = _array_spec(what, runs, R, n, self.trace_capacity)
+        out = np.empty(shape, dtype=dt)
+        st = _lib.lib().pt2d_batch_read(self._b, int(bid), what, _p(out), out.nbytes)
+        if st != 0:
+            raise Pt2dError(st, "pt2d_batch_read", _lib.lib().pt2d_batch_cuda_error(self._b))
+        return out
+
+    def sync(self) -> None:
+        _lib.check(_lib.lib().pt2d_batch_sync(self._b), "pt2d_batch_sync")
+
+    @property
+    def free_bytes(self) -> int:
+        return int(_lib.lib().pt2d_batch_free_bytes(self._b))
+
+    @property
+    def launch_count(self) -> int:
+        return int(_lib.lib().pt2d_batch_launch_count(self._b))
+
+    def close(self) -> None:
+        if getattr(self, "_b", None) and self._b.value:
+            _lib.lib().pt2d_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _diag(name, arrays, outs, count):

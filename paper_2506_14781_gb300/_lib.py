@@ -31,7 +31,10 @@ EXPORTS = [
     "pt2d_write", "pt2d_array_bytes", "pt2d_sync", "pt2d_num_colors", "pt2d_launch_count",
     "pt2d_destroy", "pt2d_strerror", "pt2d_cuda_error", "pt2d_sparsify", "pt2d_greedy_color",
     "pt2d_diag_philox", "pt2d_diag_pt_exp", "pt2d_diag_heatbath", "pt2d_diag_swap_accept",
-    "pt2d_kernel_time", "pt2d_run_noalloc",
+    "pt2d_kernel_time", "pt2d_run_noalloc", "pt2d_batch_create", "pt2d_batch_instance_bytes",
+    "pt2d_batch_add", "pt2d_batch_remove", "pt2d_batch_run", "pt2d_batch_autotune",
+    "pt2d_batch_read", "pt2d_batch_array_bytes", "pt2d_batch_sync", "pt2d_batch_free_bytes",
+    "pt2d_batch_launch_count", "pt2d_batch_cuda_error", "pt2d_batch_destroy",
 ]
 
 
@@ -112,6 +115,24 @@ def lib():
         L.pt2d_kernel_time.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]
         L.pt2d_run_noalloc.argtypes = [vp, i32, vp, i32, vp, i32, i64, i32, C.c_uint64, vp, vp,
                                        vp, vp, vp]
+        L.pt2d_batch_create.argtypes = [C.POINTER(vp), sz, i32, i32, vp]
+        L.pt2d_batch_instance_bytes.argtypes = [vp, vp, i32, i32, i32]
+        L.pt2d_batch_instance_bytes.restype = sz
+        L.pt2d_batch_add.argtypes = [vp, vp, i32, vp, i32, vp, i32, C.c_uint64, vp, C.POINTER(i64)]
+        L.pt2d_batch_remove.argtypes = [vp, i64]
+        L.pt2d_batch_run.argtypes = [vp, i32, i32]
+        L.pt2d_batch_autotune.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.pt2d_batch_read.argtypes = [vp, i64, i32, vp, sz]
+        L.pt2d_batch_array_bytes.argtypes = [vp, i64, i32]
+        L.pt2d_batch_array_bytes.restype = sz
+        L.pt2d_batch_sync.argtypes = [vp]
+        L.pt2d_batch_free_bytes.argtypes = [vp]
+        L.pt2d_batch_free_bytes.restype = sz
+        L.pt2d_batch_launch_count.argtypes = [vp]
+        L.pt2d_batch_launch_count.restype = i64
+        L.pt2d_batch_cuda_error.argtypes = [vp]
+        L.pt2d_batch_destroy.argtypes = [vp]
+        L.pt2d_batch_destroy.restype = None
         for name in EXPORTS:
             getattr(L, name)  # every declared entry point must be exported
         _lib = L

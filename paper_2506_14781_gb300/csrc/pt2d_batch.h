@@ -1,0 +1,57 @@
+// Internal interface of the batched persistent kernel.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace pt2d {
+
+constexpr int kBatchMaxReplicas = 128;  // I * J of one run, padded to a power of two
+
+// Per-run scalars (int64) in the pool.
+enum BatchScalar : int {
+    kScBestF = 0,
+    kScBestEvent = 1,
+    kScSolvedEvent = 2,
+    kScTarget = 3,
+    kScSweeps = 4,
+    kScEvents = 5,
+    kScInited = 6,
+    kScCount = 8,
+};
+
+// One run of one instance.  Offsets are bytes from the pool base.
+struct BatchRun {
+    int64_t state;       // int8 [(n + 1) * Rp], row-major by colour-sorted position
+    int64_t rec;         // int4 [n * rec_vec] packed neighbour records (row indices)
+    int64_t cofs;        // int32 [C + 1]
+    int64_t beta;        // float [I]
+    int64_t P;           // int32 [J]
+    int64_t walker_at;   // int32 [R] slot -> walker
+    int64_t fg;          // int64 f [Rp], then int32 g [Rp] (last event)
+    int64_t stats;       // int64 acc_P, acc_B, sum_f, sum_g, n_feasible [R] each
+    int64_t trace;       // int64 trace_f [trace_cap], then trace_g [trace_cap]
+    int64_t best_state;  // int8 [n] by spin id
+    int64_t scalars;     // int64 [kScCount]
+    uint32_t k0, k1;     // seed
+    int32_t n, C, I, J, R, Rp, run, trace_cap, rec_vec, use_smem;
+    int64_t work;        // n * Rp, for ordering
+};
+
+struct BatchArgs {
+    uint8_t *pool;
+    const BatchRun *runs;  // [n_runs], largest first
+    int32_t n_runs;
+    int32_t *queue;        // work counter, zero at launch
+    int32_t events;        // events per run in this launch
+    int32_t interval;      // sweeps per event
+    int32_t smem_state;    // dynamic shared memory reserved for one run's spins
+};
+
+size_t batch_small_smem_bytes();
+cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state);
+cudaError_t launch_batch(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
+
+}  // namespace pt2d

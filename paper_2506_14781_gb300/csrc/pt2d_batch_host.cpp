@@ -1,0 +1,607 @@
+// Host side of the batched persistent 2D-PT API (include/pt2d.h, pt2d_batch_*):
+// a device memory pool with a first-fit allocator, instances added and removed
+// at any time, run descriptors ordered by decreasing work, launches replayed
+// from a CUDA graph, per-instance reads, and an autotuner for the launch shape.
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pt2d.h"
+#include "pt2d_batch.h"
+#include "pt2d_prep.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// First-fit allocator over [base, base + size) with coalescing on free.
+class Arena {
+   public:
+    void reset(size_t base, size_t size) {
+        free_.clear();
+        if (size) free_[base] = size;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = align_up(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t next = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[next] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = align_up(bytes);
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t largest() const {
+        size_t m = 0;
+        for (const auto &kv : free_) m = std::max(m, kv.second);
+        return m;
+    }
+    size_t total() const {
+        size_t t = 0;
+        for (const auto &kv : free_) t += kv.second;
+        return t;
+    }
+
+   private:
+    std::map<size_t, size_t> free_;
+};
+
+struct Inst {
+    size_t off = 0, bytes = 0;
+    int32_t n = 0, I = 0, J = 0, R = 0, Rp = 0, runs = 0, C = 0, rec_vec = 0;
+    std::vector<int32_t> pos_of, color;
+    std::vector<pt2d::BatchRun> desc;  // one per run
+};
+
+struct Layout1 {  // byte offsets within an instance block
+    size_t rec, cofs, beta, P, total;
+    size_t run0, run_stride;
+    size_t state, walker_at, fg, stats, trace, best_state, scalars;  // relative to a run
+};
+
+Layout1 block_layout(int32_t n, int32_t C, int32_t rec_vec, int32_t I, int32_t J, int32_t R,
+                     int32_t Rp, int32_t runs, int32_t trace_cap) {
+    Layout1 l{};
+    size_t o = 0;
+    l.rec = o;
+    o = align_up(o + static_cast<size_t>(n) * rec_vec * 16);
+    l.cofs = o;
+    o = align_up(o + static_cast<size_t>(C + 1) * 4);
+    l.beta = o;
+    o = align_up(o + static_cast<size_t>(I) * 4);
+    l.P = o;
+    o = align_up(o + static_cast<size_t>(J) * 4);
+    l.run0 = o;
+    size_t r = 0;
+    l.state = r;
+    r = align_up(r + static_cast<size_t>(n + 1) * Rp);
+    l.walker_at = r;
+    r = align_up(r + static_cast<size_t>(R) * 4);
+    l.fg = r;
+    r = align_up(r + static_cast<size_t>(Rp) * 12);
+    l.stats = r;
+    r = align_up(r + static_cast<size_t>(R) * 5 * 8);
+    l.trace = r;
+    r = align_up(r + static_cast<size_t>(trace_cap) * 16);
+    l.best_state = r;
+    r = align_up(r + static_cast<size_t>(n));
+    l.scalars = r;
+    r = align_up(r + pt2d::kScCount * 8);
+    l.run_stride = r;
+    l.total = o + r * static_cast<size_t>(runs);
+    return l;
+}
+
+// Replicas per run padded to a power of two >= 16, so a run's spin rows are
+// whole 16-byte vectors for the shared-memory copies.
+int32_t pow2_at_least(int32_t x) {
+    int32_t p = 16;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct pt2d_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool own_pool = false;
+    uint8_t *pool = nullptr;
+    size_t pool_bytes = 0;
+    int DC = 3;
+    int32_t trace_cap = 0;
+    int32_t max_runs = 0;
+    int threads = 1024;
+    int grid = 0;
+    int smem_state = 0;
+    int smem_state_max = 0;
+    bool use_graph = true;
+    Arena arena;
+    std::map<int64_t, Inst> insts;
+    int64_t next_id = 1;
+    pt2d::BatchRun *d_runs = nullptr;
+    int32_t *d_queue = nullptr;
+    int32_t n_runs = 0;
+    bool dirty = true;
+    cudaGraphExec_t graph = nullptr;
+    int graph_events = -1, graph_interval = -1, graph_threads = -1;
+    int64_t launches = 0;
+    int last_cuda = 0;
+};
+
+namespace {
+
+int fail(pt2d_batch *b, cudaError_t e) {
+    if (b) b->last_cuda = static_cast<int>(e);
+    cudaGetLastError();
+    return PT2D_ERR_CUDA;
+}
+
+#define BK(b, expr)                                \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) return fail(b, _e); \
+    } while (0)
+
+void drop_graph(pt2d_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_events = b->graph_interval = b->graph_threads = -1;
+}
+
+int upload_descriptors(pt2d_batch *b) {
+    std::vector<pt2d::BatchRun> all;
+    for (auto &kv : b->insts)
+        for (auto &d : kv.second.desc) {
+            d.use_smem = static_cast<int64_t>(d.n + 1) * d.Rp <= b->smem_state ? 1 : 0;
+            all.push_back(d);
+        }
+    std::stable_sort(all.begin(), all.end(),
+                     [](const pt2d::BatchRun &x, const pt2d::BatchRun &y) { return x.work > y.work; });
+    if (static_cast<int32_t>(all.size()) > b->max_runs) return PT2D_ERR_OOM;
+    if (!all.empty())
+        BK(b, cudaMemcpyAsync(b->d_runs, all.data(), sizeof(pt2d::BatchRun) * all.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+    b->n_runs = static_cast<int32_t>(all.size());
+    b->dirty = false;
+    drop_graph(b);
+    return PT2D_OK;
+}
+
+int launch(pt2d_batch *b, int32_t events, int32_t interval) {
+    if (b->dirty) {
+        int st = upload_descriptors(b);
+        if (st) return st;
+    }
+    if (b->n_runs == 0 || events == 0) return PT2D_OK;
+    pt2d::BatchArgs a{b->pool, b->d_runs, b->n_runs, b->d_queue, events, interval, b->smem_state};
+    const int grid = std::min(b->grid, b->n_runs);
+    BK(b, pt2d::batch_kernel_attributes(b->DC, 2, b->smem_state));
+    if (!b->use_graph) {
+        BK(b, cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream));
+        BK(b, pt2d::launch_batch(a, b->DC, 2, grid, b->threads, b->stream));
+    } else {
+        if (!b->graph || b->graph_events != events || b->graph_interval != interval ||
+            b->graph_threads != b->threads) {
+            drop_graph(b);
+            cudaGraph_t g = nullptr;
+            BK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream);
+            cudaError_t e2 = pt2d::launch_batch(a, b->DC, 2, grid, b->threads, b->stream);
+            cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
+            if (e1 != cudaSuccess) return fail(b, e1);
+            if (e2 != cudaSuccess) return fail(b, e2);
+            if (e3 != cudaSuccess) return fail(b, e3);
+            cudaError_t e4 = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e4 != cudaSuccess) return fail(b, e4);
+            b->graph_events = events;
+            b->graph_interval = interval;
+            b->graph_threads = b->threads;
+        }
+        BK(b, cudaGraphLaunch(b->graph, b->stream));
+    }
+    b->launches += 1;
+    return PT2D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pt2d_batch_instance_bytes(const pt2d_batch *b, const pt2d_instance *inst, int32_t I,
+                                 int32_t J, int32_t runs) {
+    if (!b || !inst || inst->n < 1 || I < 1 || J < 1 || runs < 1 || I * J > pt2d::kBatchMaxReplicas)
+        return 0;
+    pt2d::Prep pp;
+    pt2d_options o;
+    pt2d_default_options(&o);
+    o.sweep_kernel = 1;
+    if (pt2d::prepare(inst, I, nullptr, J, nullptr, 1, &o, pp, b->DC)) return 0;
+    const int32_t R = I * J;
+    return align_up(block_layout(inst->n, pp.C, pp.rec_vec, I, J, R, pow2_at_least(R), runs, b->trace_cap)
+                        .total);
+}
+
+int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_degree,
+                      int32_t max_runs, const pt2d_options *opt) {
+    if (!out || pool_bytes == 0 || max_runs < 1 || max_coupling_degree < 0 || max_coupling_degree > 6)
+        return PT2D_ERR_INVALID_ARG;
+    *out = nullptr;
+    pt2d_options dflt;
+    pt2d_default_options(&dflt);
+    if (!opt) opt = &dflt;
+    if (opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return PT2D_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PT2D_ERR_UNSUPPORTED;
+    }
+    int major = 0, minor = 0, sms = 0, smem_optin = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (major != 10 || minor != 3) return PT2D_ERR_UNSUPPORTED;
+    pt2d_batch *b = new (std::nothrow) pt2d_batch;
+    if (!b) return PT2D_ERR_OOM;
+    b->device = dev;
+    b->DC = max_coupling_degree <= 3 ? 3 : (max_coupling_degree <= 4 ? 4 : 6);
+    b->trace_cap = std::max<int32_t>(opt->trace_capacity, 0);
+    b->max_runs = max_runs;
+    b->threads = opt->threads_per_cta > 0 ? opt->threads_per_cta : 1024;
+    if (b->threads < 128 || b->threads > 1024 || b->threads % 32) {
+        delete b;
+        return PT2D_ERR_INVALID_ARG;
+    }
+    b->grid = sms > 0 ? sms : 152;
+    b->smem_state_max = std::max(0, smem_optin - static_cast<int>(pt2d::batch_small_smem_bytes()) - 1024);
+    b->smem_state_max &= ~15;
+    b->smem_state = opt->sweep_kernel == 1 ? 0 : b->smem_state_max;
+    if (opt->stream) {
+        b->stream = static_cast<cudaStream_t>(opt->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return PT2D_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    const size_t head = align_up(sizeof(int32_t)) + align_up(sizeof(pt2d::BatchRun) * max_runs);
+    if (opt->workspace) {
+        if (opt->workspace_bytes < head + 4096 || (reinterpret_cast<uintptr_t>(opt->workspace) & 255)) {
+            pt2d_batch_destroy(b);
+            return PT2D_ERR_INVALID_ARG;
+        }
+        b->pool = static_cast<uint8_t *>(opt->workspace);
+        b->pool_bytes = opt->workspace_bytes;
+    } else {
+        if (cudaMalloc(&b->pool, pool_bytes + head) != cudaSuccess) {
+            cudaGetLastError();
+            pt2d_batch_destroy(b);
+            return PT2D_ERR_OOM;
+        }
+        b->own_pool = true;
+        b->pool_bytes = pool_bytes + head;
+    }
+    b->d_queue = reinterpret_cast<int32_t *>(b->pool);
+    b->d_runs = reinterpret_cast<pt2d::BatchRun *>(b->pool + align_up(sizeof(int32_t)));
+    b->arena.reset(head, b->pool_bytes - head);
+    *out = b;
+    return PT2D_OK;
+}
+
+void pt2d_batch_destroy(pt2d_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    if (b->own_pool && b->pool) cudaFree(b->pool);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int pt2d_batch_add(pt2d_batch *b, const pt2d_instance *inst, int32_t I, const float *beta, int32_t J,
+                   const int32_t *P, int32_t runs, uint64_t seed, const int64_t *target,
+                   int64_t *id_out) {
+    if (!b || !inst || !beta || !P || !id_out || runs < 1 || I < 1 || J < 1) return PT2D_ERR_INVALID_ARG;
+    if (I * J > pt2d::kBatchMaxReplicas) return PT2D_ERR_INVALID_ARG;
+    if (runs >= (1 << 27)) return PT2D_ERR_INVALID_ARG;
+    pt2d_options o;
+    pt2d_default_options(&o);
+    o.sweep_kernel = 1;
+    Inst in;
+    pt2d::Prep pp;
+    int st = pt2d::prepare(inst, I, beta, J, P, 1, &o, pp, b->DC);
+    if (st) return st;
+    in.n = pp.n;
+    in.I = I;
+    in.J = J;
+    in.R = I * J;
+    in.Rp = pow2_at_least(in.R);
+    in.runs = runs;
+    in.C = pp.C;
+    in.rec_vec = pp.rec_vec;
+    in.pos_of = pp.pos_of;
+    in.color = pp.color;
+    const Layout1 l = block_layout(in.n, in.C, in.rec_vec, I, J, in.R, in.Rp, runs, b->trace_cap);
+    if (!b->arena.alloc(l.total, &in.off)) return PT2D_ERR_OOM;
+    in.bytes = l.total;
+    cudaSetDevice(b->device);
+    cudaStream_t s = b->stream;
+    uint8_t *base = b->pool + in.off;
+    auto undo = [&](cudaError_t e) {
+        b->arena.release(in.off, in.bytes);
+        return fail(b, e);
+    };
+    cudaError_t e = cudaMemsetAsync(base, 0, l.total, s);
+    if (e != cudaSuccess) return undo(e);
+    e = cudaMemcpyAsync(base + l.rec, pp.rec.data(), sizeof(int32_t) * pp.rec.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + l.cofs, pp.cofs.data(), sizeof(int32_t) * pp.cofs.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + l.beta, beta, sizeof(float) * I, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + l.P, P, sizeof(int32_t) * J, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return undo(e);
+    std::vector<int64_t> scal(static_cast<size_t>(runs) * pt2d::kScCount, 0);
+    for (int32_t r = 0; r < runs; ++r) {
+        pt2d::BatchRun d{};
+        const size_t rb = in.off + l.run0 + l.run_stride * r;
+        d.state = static_cast<int64_t>(rb + l.state);
+        d.rec = static_cast<int64_t>(in.off + l.rec);
+        d.cofs = static_cast<int64_t>(in.off + l.cofs);
+        d.beta = static_cast<int64_t>(in.off + l.beta);
+        d.P = static_cast<int64_t>(in.off + l.P);
+        d.walker_at = static_cast<int64_t>(rb + l.walker_at);
+        d.fg = static_cast<int64_t>(rb + l.fg);
+        d.stats = static_cast<int64_t>(rb + l.stats);
+        d.trace = static_cast<int64_t>(rb + l.trace);
+        d.best_state = static_cast<int64_t>(rb + l.best_state);
+        d.scalars = static_cast<int64_t>(rb + l.scalars);
+        d.k0 = static_cast<uint32_t>(seed);
+        d.k1 = static_cast<uint32_t>(seed >> 32);
+        d.n = in.n;
+        d.C = in.C;
+        d.I = I;
+        d.J = J;
+        d.R = in.R;
+        d.Rp = in.Rp;
+        d.run = r;
+        d.trace_cap = b->trace_cap;
+        d.rec_vec = in.rec_vec;
+        d.work = static_cast<int64_t>(in.n) * in.Rp;
+        in.desc.push_back(d);
+        scal[static_cast<size_t>(r) * pt2d::kScCount + pt2d::kScTarget] = target ? target[r] : INT64_MIN;
+    }
+    for (int32_t r = 0; r < runs; ++r) {
+        e = cudaMemcpyAsync(b->pool + in.desc[r].scalars, scal.data() + static_cast<size_t>(r) * pt2d::kScCount,
+                            pt2d::kScCount * 8, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return undo(e);
+    }
+    // host copies of pp's vectors must outlive the async copies
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return undo(e);
+    const int64_t id = b->next_id++;
+    b->insts.emplace(id, std::move(in));
+    b->dirty = true;
+    *id_out = id;
+    return PT2D_OK;
+}
+
+int pt2d_batch_remove(pt2d_batch *b, int64_t id) {
+    if (!b) return PT2D_ERR_INVALID_ARG;
+    auto it = b->insts.find(id);
+    if (it == b->insts.end()) return PT2D_ERR_INVALID_ARG;
+    // later work on the stream may reuse the block; earlier launches finish first
+    b->arena.release(it->second.off, it->second.bytes);
+    b->insts.erase(it);
+    b->dirty = true;
+    return PT2D_OK;
+}
+
+int pt2d_batch_run(pt2d_batch *b, int32_t events, int32_t swap_interval) {
+    if (!b || events < 0 || swap_interval < 1) return PT2D_ERR_INVALID_ARG;
+    cudaSetDevice(b->device);
+    return launch(b, events, swap_interval);
+}
+
+int pt2d_batch_sync(pt2d_batch *b) {
+    if (!b) return PT2D_ERR_INVALID_ARG;
+    BK(b, cudaStreamSynchronize(b->stream));
+    return PT2D_OK;
+}
+
+int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, int32_t *threads_out,
+                        int32_t *smem_out) {
+    if (!b || events < 1 || swap_interval < 1) return PT2D_ERR_INVALID_ARG;
+    cudaSetDevice(b->device);
+    const int thread_opts[] = {256, 512, 1024};
+    const int smem_opts[] = {b->smem_state_max, 0};
+    float best_ms = -1.0f;
+    int best_t = b->threads, best_s = b->smem_state;
+    cudaEvent_t e0, e1;
+    BK(b, cudaEventCreate(&e0));
+    BK(b, cudaEventCreate(&e1));
+    // Every launch shape computes the same trajectories, so the trial launches are
+    // ordinary progress of the chains.
+    for (int so : smem_opts) {
+        for (int t : thread_opts) {
+            b->threads = t;
+            if (b->smem_state != so) {
+                b->smem_state = so;
+                b->dirty = true;
+            }
+            int st = launch(b, events, swap_interval);  // first launch per shape: not timed
+            if (st) return st;
+            BK(b, cudaEventRecord(e0, b->stream));
+            st = launch(b, events, swap_interval);
+            if (st) return st;
+            BK(b, cudaEventRecord(e1, b->stream));
+            BK(b, cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            BK(b, cudaEventElapsedTime(&ms, e0, e1));
+            if (best_ms < 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best_t = t;
+                best_s = so;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->threads = best_t;
+    if (b->smem_state != best_s) {
+        b->smem_state = best_s;
+        b->dirty = true;
+    }
+    if (threads_out) *threads_out = best_t;
+    if (smem_out) *smem_out = best_s;
+    return PT2D_OK;
+}
+
+size_t pt2d_batch_free_bytes(const pt2d_batch *b) { return b ? b->arena.largest() : 0; }
+
+int64_t pt2d_batch_launch_count(const pt2d_batch *b) { return b ? b->launches : 0; }
+
+int pt2d_batch_cuda_error(const pt2d_batch *b) { return b ? b->last_cuda : 0; }
+
+size_t pt2d_batch_array_bytes(const pt2d_batch *b, int64_t id, int32_t what) {
+    if (!b) return 0;
+    auto it = b->insts.find(id);
+    if (it == b->insts.end()) return 0;
+    const Inst &in = it->second;
+    const size_t RR = static_cast<size_t>(in.runs) * in.R;
+    switch (what) {
+        case PT2D_STATES: return RR * in.n;
+        case PT2D_WALKER_AT: return RR * 4;
+        case PT2D_F:
+        case PT2D_G:
+        case PT2D_ACC_P:
+        case PT2D_ACC_B:
+        case PT2D_SUM_F:
+        case PT2D_SUM_G:
+        case PT2D_N_FEASIBLE: return RR * 8;
+        case PT2D_COUNTERS: return 4 * 8;
+        case PT2D_TRACE_F:
+        case PT2D_TRACE_G: return static_cast<size_t>(in.runs) * b->trace_cap * 8;
+        case PT2D_BEST_F:
+        case PT2D_BEST_EVENT:
+        case PT2D_SOLVED_EVENT:
+        case PT2D_TARGET: return static_cast<size_t>(in.runs) * 8;
+        case PT2D_BEST_STATE: return static_cast<size_t>(in.runs) * in.n;
+        case PT2D_COLORS: return static_cast<size_t>(in.n) * 4;
+        default: return 0;
+    }
+}
+
+int pt2d_batch_read(pt2d_batch *b, int64_t id, int32_t what, void *dst, size_t bytes) {
+    if (!b || !dst) return PT2D_ERR_INVALID_ARG;
+    auto it = b->insts.find(id);
+    if (it == b->insts.end()) return PT2D_ERR_INVALID_ARG;
+    const size_t need = pt2d_batch_array_bytes(b, id, what);
+    if (need == 0 || bytes != need) return PT2D_ERR_INVALID_ARG;
+    const Inst &in = it->second;
+    cudaSetDevice(b->device);
+    BK(b, cudaStreamSynchronize(b->stream));
+    if (what == PT2D_COLORS) {
+        std::memcpy(dst, in.color.data(), need);
+        return PT2D_OK;
+    }
+    auto copy = [&](void *h, int64_t off, size_t nbytes) -> cudaError_t {
+        return cudaMemcpy(h, b->pool + off, nbytes, cudaMemcpyDeviceToHost);
+    };
+    const int32_t R = in.R, n = in.n;
+    for (int32_t r = 0; r < in.runs; ++r) {
+        const pt2d::BatchRun &d = in.desc[r];
+        int64_t sc[pt2d::kScCount];
+        BK(b, copy(sc, d.scalars, sizeof sc));
+        switch (what) {
+            case PT2D_STATES: {
+                if (!sc[pt2d::kScInited]) return PT2D_ERR_STATE;
+                std::vector<int8_t> tmp(static_cast<size_t>(n + 1) * in.Rp);
+                BK(b, copy(tmp.data(), d.state, tmp.size()));
+                int8_t *o = static_cast<int8_t *>(dst) + static_cast<size_t>(r) * R * n;
+                for (int32_t w = 0; w < R; ++w)
+                    for (int32_t a = 0; a < n; ++a)
+                        o[static_cast<size_t>(w) * n + a] = tmp[static_cast<size_t>(in.pos_of[a]) * in.Rp + w];
+                break;
+            }
+            case PT2D_WALKER_AT:
+                BK(b, copy(static_cast<int32_t *>(dst) + static_cast<size_t>(r) * R, d.walker_at, 4 * R));
+                break;
+            case PT2D_F:
+            case PT2D_G: {
+                std::vector<int64_t> f(in.Rp);
+                std::vector<int32_t> g(in.Rp);
+                BK(b, copy(f.data(), d.fg, 8 * in.Rp));
+                BK(b, copy(g.data(), d.fg + 8 * in.Rp, 4 * in.Rp));
+                int64_t *o = static_cast<int64_t *>(dst) + static_cast<size_t>(r) * R;
+                for (int32_t w = 0; w < R; ++w) o[w] = what == PT2D_F ? f[w] : g[w];
+                break;
+            }
+            case PT2D_COUNTERS: {
+                if (r == 0) {
+                    const int64_t ev = sc[pt2d::kScEvents];
+                    int64_t v[4] = {sc[pt2d::kScSweeps], ev, ((ev / 2) % 2 == 0) ? 1 : -1, sc[pt2d::kScInited]};
+                    std::memcpy(dst, v, sizeof v);
+                }
+                break;
+            }
+            case PT2D_TRACE_F:
+            case PT2D_TRACE_G:
+                if (b->trace_cap)
+                    BK(b, copy(static_cast<int64_t *>(dst) + static_cast<size_t>(r) * b->trace_cap,
+                               d.trace + (what == PT2D_TRACE_G ? 8 * b->trace_cap : 0), 8 * b->trace_cap));
+                break;
+            case PT2D_BEST_F: static_cast<int64_t *>(dst)[r] = sc[pt2d::kScInited] ? sc[pt2d::kScBestF] : INT64_MAX; break;
+            case PT2D_BEST_EVENT: static_cast<int64_t *>(dst)[r] = sc[pt2d::kScInited] ? sc[pt2d::kScBestEvent] : -1; break;
+            case PT2D_SOLVED_EVENT: static_cast<int64_t *>(dst)[r] = sc[pt2d::kScInited] ? sc[pt2d::kScSolvedEvent] : -1; break;
+            case PT2D_TARGET: static_cast<int64_t *>(dst)[r] = sc[pt2d::kScTarget]; break;
+            case PT2D_BEST_STATE:
+                BK(b, copy(static_cast<int8_t *>(dst) + static_cast<size_t>(r) * n, d.best_state, n));
+                break;
+            case PT2D_ACC_P:
+            case PT2D_ACC_B:
+            case PT2D_SUM_F:
+            case PT2D_SUM_G:
+            case PT2D_N_FEASIBLE: {
+                const int k = what == PT2D_ACC_P ? 0 : what == PT2D_ACC_B ? 1 : what == PT2D_SUM_F ? 2 : what == PT2D_SUM_G ? 3 : 4;
+                BK(b, copy(static_cast<int64_t *>(dst) + static_cast<size_t>(r) * R, d.stats + 8LL * R * k, 8 * R));
+                break;
+            }
+            default:
+                return PT2D_ERR_INVALID_ARG;
+        }
+    }
+    return PT2D_OK;
+}
+
+}  // extern "C"

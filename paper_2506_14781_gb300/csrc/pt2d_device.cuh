@@ -83,7 +83,7 @@ __device__ __forceinline__ float pow2i(int m) {  // 2^m, -126 <= m <= 127
     return __uint_as_float(static_cast<uint32_t>(m + 127) << 23);
 }
 
-__device__ __noinline__ float pt_exp(float x) {
+static __device__ __noinline__ float pt_exp(float x) {
     const float kL2E = 0x1.715476p+0f;     // RN(log2 e)
     const float kLn2Hi = 0x1.62ep-1f;      // RN(ln 2) with 12 low bits cleared
     const float kLn2Lo = 0x1.0bfbe8p-15f;  // RN(ln 2 - kLn2Hi)
@@ -118,7 +118,7 @@ __device__ __noinline__ float pt_exp(float x) {
 // Heat-bath decision, exact contract: t = beta*float(H); e = pt_exp(-t);
 // d = 1 + e; v = u*d; +1 iff v < 1.
 // ---------------------------------------------------------------------------
-__device__ __noinline__ int heatbath_exact(float beta, int32_t H, uint32_t r) {
+static __device__ __noinline__ int heatbath_exact(float beta, int32_t H, uint32_t r) {
     const float t = __fmul_rn(beta, __int2float_rn(H));
     const float e = pt_exp(-t);
     const float d = __fadd_rn(1.0f, e);

@@ -11,20 +11,12 @@
 
 #include "../../include/pt2d.h"
 #include "pt2d_internal.h"
+#include "pt2d_prep.h"
 
 namespace {
 
 constexpr int64_t kHBound = int64_t(1) << 24;  // |H| must stay exact in float32
 constexpr int64_t kMaxSlots = 8192;             // I * J per run
-
-struct Prep {
-    int32_t n = 0, I = 0, J = 0, R = 0, Rp = 0, runs = 0, C = 0, DC = 0, DL = 0;
-    int64_t Wc = 0;
-    int32_t trace_cap = 0;
-    pt2d::SweepTiling tiling{};
-    int32_t rec_vec = 0, pad_ref = 0;
-    std::vector<int32_t> color, pid, pos_of, cofs, rec;
-};
 
 // Sum of sizes with 256-byte alignment; two passes (size, then assignment).
 struct Carver {
@@ -71,8 +63,12 @@ int check_csr(int32_t n, const int32_t *ptr, const int32_t *col, const int16_t *
     return PT2D_OK;
 }
 
+}  // namespace
+
+namespace pt2d {
+
 int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, const int32_t *P,
-            int32_t runs, const pt2d_options *opt, Prep &pp) {
+            int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc) {
     if (!inst || inst->n < 1 || I < 1 || J < 1 || runs < 1) return PT2D_ERR_INVALID_ARG;
     // the swap kernel keeps one run's slot -> walker map in shared memory
     if (static_cast<int64_t>(I) * J > kMaxSlots) return PT2D_ERR_INVALID_ARG;
@@ -159,7 +155,11 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         dlmax = std::max<int32_t>(dlmax, static_cast<int32_t>(ladj[a].size()));
     }
     int32_t DC, DL;
-    if (dlmax <= 2 && dcmax <= 6) {
+    if (force_dc > 0) {
+        if (dlmax > 2 || dcmax > force_dc) return PT2D_ERR_INVALID_ARG;
+        DC = force_dc;
+        DL = 2;
+    } else if (dlmax <= 2 && dcmax <= 6) {
         DL = 2;
         DC = dcmax <= 3 ? 3 : (dcmax <= 4 ? 4 : 6);
     } else {
@@ -276,6 +276,14 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.Wc = (walkers + slab - 1) / slab * slab;
     return PT2D_OK;
 }
+
+}  // namespace pt2d
+
+namespace {
+
+using pt2d::Prep;
+using pt2d::prepare;
+
 
 }  // namespace
 

@@ -23,144 +23,10 @@
 
 #include "pt2d_device.cuh"
 #include "pt2d_internal.h"
+#include "pt2d_sweep.cuh"
 
 namespace pt2d {
 namespace {
-
-// byte b of x, sign-extended (one PRMT in sign-replicate mode)
-template <int b>
-__device__ __forceinline__ int sbyte(uint32_t x) {
-    constexpr uint32_t n = 8u | b;
-    constexpr uint32_t sel = (n << 12) | (n << 8) | (n << 4) | static_cast<uint32_t>(b);
-    uint32_t d;
-    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(x), "n"(sel));
-    return static_cast<int>(d);
-}
-
-__device__ __forceinline__ int sbyte_rt(uint32_t x, int b) {
-    return static_cast<int>(static_cast<int8_t>(static_cast<uint8_t>(x >> (8 * b))));
-}
-
-// Spin word from the sign bits of four decision values: byte k = 0x01 (+1) when
-// t_k < 0, 0xFF (-1) otherwise.
-__device__ __forceinline__ uint32_t pack_signs(float t0, float t1, float t2, float t3) {
-    uint32_t lo, hi, m;
-    asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(lo) : "r"(__float_as_uint(t0)), "r"(__float_as_uint(t1)));
-    asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(hi) : "r"(__float_as_uint(t2)), "r"(__float_as_uint(t3)));
-    asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(m) : "r"(lo), "r"(hi));
-    return ~m | 0x01010101u;
-}
-
-constexpr int kMaxSlab = 128;  // walkers per CTA
-
-// Packed neighbour record of one position: [nb_0..nb_{DC-1}, lk_0..lk_{DL-1},
-// pid, 2h, 2J_0..2J_{DC-1}] padded to whole int4s.
-template <int DC, int DL>
-struct Rec {
-    static constexpr int kInts = 2 * DC + DL + 2;
-    static constexpr int kVec = (kInts + 3) / 4;
-    int v[kVec * 4];
-    __device__ __forceinline__ void load(const int4 *base, int pos) {
-        const int4 *p = base + static_cast<int64_t>(pos) * kVec;
-#pragma unroll
-        for (int i = 0; i < kVec; ++i) reinterpret_cast<int4 *>(v)[i] = __ldg(p + i);
-    }
-    __device__ __forceinline__ int nb(int k) const { return v[k]; }
-    __device__ __forceinline__ int lk(int l) const { return v[DC + l]; }
-    __device__ __forceinline__ int pid() const { return v[DC + DL]; }
-    __device__ __forceinline__ int h2() const { return v[DC + DL + 1]; }
-    __device__ __forceinline__ int j2(int k) const { return v[DC + DL + 2 + k]; }
-};
-
-struct Quad {
-    float b0, b1, b2, b3;  // beta of each walker's slot
-    float c0, c1, c2, c3;  // -beta * log2(e)
-    int p0, p1, p2, p3;    // P of each walker's slot
-};
-
-__device__ __forceinline__ Quad load_quad(const Walkers &wk, int64_t col) {
-    const float4 bt = *reinterpret_cast<const float4 *>(wk.wbeta + col);
-    const int4 pj = *reinterpret_cast<const int4 *>(wk.wP + col);
-    const float kNegL2E = -1.4426950408889634f;
-    return Quad{bt.x, bt.y, bt.z, bt.w, bt.x * kNegL2E, bt.y * kNegL2E, bt.z * kNegL2E,
-                bt.w * kNegL2E, pj.x, pj.y, pj.z, pj.w};
-}
-
-// New spin word of one quad at one position.  `fetch(row)` returns the quad's
-// spin word of a row (shared or global memory).
-template <int DC, int DL>
-__device__ __forceinline__ uint32_t decide4(const Rec<DC, DL> &rc, const Quad &q, const uint32_t *x,
-                                            const uint32_t *y, const uint4 &r) {
-    int a0 = rc.h2(), a1 = a0, a2 = a0, a3 = a0;
-#pragma unroll
-    for (int k = 0; k < DC; ++k) {
-        const int j = rc.j2(k);
-        a0 += j * sbyte<0>(x[k]);
-        a1 += j * sbyte<1>(x[k]);
-        a2 += j * sbyte<2>(x[k]);
-        a3 += j * sbyte<3>(x[k]);
-    }
-    int l0 = 0, l1 = 0, l2 = 0, l3 = 0;
-#pragma unroll
-    for (int l = 0; l < DL; ++l) {
-        l0 += sbyte<0>(y[l]);
-        l1 += sbyte<1>(y[l]);
-        l2 += sbyte<2>(y[l]);
-        l3 += sbyte<3>(y[l]);
-    }
-    a0 += q.p0 * l0;
-    a1 += q.p1 * l1;
-    a2 += q.p2 * l2;
-    a3 += q.p3 * l3;
-    float t0 = heatbath_fast(q.c0, a0, r.x), t1 = heatbath_fast(q.c1, a1, r.y);
-    float t2 = heatbath_fast(q.c2, a2, r.z), t3 = heatbath_fast(q.c3, a3, r.w);
-    // one branch for the four band tests; inside it the exact contract decides
-    if (fminf(fminf(fabsf(t0), fabsf(t1)), fminf(fabsf(t2), fabsf(t3))) <= kBand) {
-        if (fabsf(t0) <= kBand) t0 = heatbath_exact(q.b0, a0, r.x) > 0 ? -1.0f : 1.0f;
-        if (fabsf(t1) <= kBand) t1 = heatbath_exact(q.b1, a1, r.y) > 0 ? -1.0f : 1.0f;
-        if (fabsf(t2) <= kBand) t2 = heatbath_exact(q.b2, a2, r.z) > 0 ? -1.0f : 1.0f;
-        if (fabsf(t3) <= kBand) t3 = heatbath_exact(q.b3, a3, r.w) > 0 ? -1.0f : 1.0f;
-    }
-    return pack_signs(t0, t1, t2, t3);
-}
-
-template <int DC, int DL, typename Fetch>
-__device__ __forceinline__ uint32_t update4(const Rec<DC, DL> &rc, const Quad &q, Fetch fetch,
-                                            uint32_t sweep, uint32_t lq, uint32_t c3,
-                                            const RoundKeys &rk) {
-    uint32_t x[DC], y[DL];
-#pragma unroll
-    for (int k = 0; k < DC; ++k) x[k] = fetch(rc.nb(k));
-#pragma unroll
-    for (int l = 0; l < DL; ++l) y[l] = fetch(rc.lk(l));
-    const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3), rk);
-    return decide4<DC, DL>(rc, q, x, y, r);
-}
-
-// Eight walkers (two quads) at one position: one 8-byte fetch per neighbour,
-// two independent Philox calls (quads lq and lq + 1).
-template <int DC, int DL, typename Fetch8>
-__device__ __forceinline__ uint2 update8(const Rec<DC, DL> &rc, const Quad &qa, const Quad &qb,
-                                         Fetch8 fetch8, uint32_t sweep, uint32_t lq, uint32_t c3,
-                                         const RoundKeys &rk) {
-    uint32_t xa[DC], ya[DL], xb[DC], yb[DL];
-#pragma unroll
-    for (int k = 0; k < DC; ++k) {
-        const uint2 w = fetch8(rc.nb(k));
-        xa[k] = w.x;
-        xb[k] = w.y;
-    }
-#pragma unroll
-    for (int l = 0; l < DL; ++l) {
-        const uint2 w = fetch8(rc.lk(l));
-        ya[l] = w.x;
-        yb[l] = w.y;
-    }
-    const uint32_t id = static_cast<uint32_t>(rc.pid());
-    const uint4 ra = philox4x32_10(make_uint4(id, sweep, lq, c3), rk);
-    const uint4 rb = philox4x32_10(make_uint4(id, sweep, lq + 1, c3), rk);
-    return make_uint2(decide4<DC, DL>(rc, qa, xa, ya, ra), decide4<DC, DL>(rc, qb, xb, yb, rb));
-}
 
 // Per-walker f and g of the CTA's slab (epilogue of the sweep kernels); the
 // thread owns NQ quads, its walkers are wbase .. wbase + 4 NQ - 1 of the slab.
@@ -250,6 +116,7 @@ __global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
     const int lane_off = WPT * lane;
     const Quad qa = load_quad(wk, col0 + lane_off);
     const Quad qb = NQ == 2 ? load_quad(wk, col0 + lane_off + 4) : qa;
+    const KeysConst keys{rk};
 
     // load the slab, 16 bytes per access
     const int vec_per_row = SW >> 4;
@@ -278,9 +145,9 @@ __global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
                 rc.load(L.rec, pos);
                 int8_t *dst = sm + (pos << sw_shift) + lane_off;
                 if (NQ == 1) {
-                    *reinterpret_cast<uint32_t *>(dst) = update4<DC, DL>(rc, qa, fetch4, sweep, lq, c3, rk);
+                    *reinterpret_cast<uint32_t *>(dst) = update4<DC, DL>(rc, qa, fetch4, sweep, lq, c3, keys);
                 } else {
-                    *reinterpret_cast<uint2 *>(dst) = update8<DC, DL>(rc, qa, qb, fetch8, sweep, lq, c3, rk);
+                    *reinterpret_cast<uint2 *>(dst) = update8<DC, DL>(rc, qa, qb, fetch8, sweep, lq, c3, keys);
                 }
             }
             __syncthreads();
@@ -319,6 +186,7 @@ __global__ void __launch_bounds__(256) k_sweep_global(Layout L, Walkers wk, int 
     const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
     const uint32_t c3 = (run << 4) | kTagSweep;
     const Quad q = load_quad(wk, col);
+    const KeysConst keys{rk};
     int8_t *__restrict__ S = L.S;
     const int64_t Wc = L.Wc;
     auto fetch = [&](int row) -> uint32_t {
@@ -331,7 +199,7 @@ __global__ void __launch_bounds__(256) k_sweep_global(Layout L, Walkers wk, int 
             for (int pos = beg + grp; pos < end; pos += G) {
                 Rec<DC, DL> rc;
                 rc.load(L.rec, pos);
-                const uint32_t w = update4<DC, DL>(rc, q, fetch, sweep, lq, c3, rk);
+                const uint32_t w = update4<DC, DL>(rc, q, fetch, sweep, lq, c3, keys);
                 *reinterpret_cast<uint32_t *>(S + static_cast<int64_t>(pos) * Wc + col) = w;
             }
             __syncthreads();
@@ -479,7 +347,7 @@ __global__ void k_init_walkers(RunState rs, Walkers wk) {
 }
 
 __global__ void k_swap_event(Layout L, RunState rs, Walkers wk, uint32_t k0, uint32_t k1,
-                             int64_t nev, int dir_p, int parity) {
+                             int64_t nev, int dir_p) {
     extern __shared__ int at[];
     __shared__ int s_copy;
     const int run = blockIdx.x;
@@ -488,46 +356,10 @@ __global__ void k_swap_event(Layout L, RunState rs, Walkers wk, uint32_t k0, uin
     const int64_t rb = static_cast<int64_t>(run) * R;
     for (int s = threadIdx.x; s < R; s += blockDim.x) at[s] = rs.walker_at[rb + s];
     __syncthreads();
-    const uint32_t c3 = (static_cast<uint32_t>(run) << 4) | kTagSwap;
-    const uint32_t n32 = static_cast<uint32_t>(nev);
-    if (dir_p) {
-        const int per_row = (J - parity) / 2;
-        const int total = I * per_row;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int i = idx / per_row;
-            const int j = parity + 2 * (idx - i * per_row);
-            const int sa = i * J + j, sb = sa + 1;
-            const int wa = at[sa], wb = at[sb];
-            const long long dP = static_cast<long long>(rs.P[j + 1]) - rs.P[j];
-            const long long dg = static_cast<long long>(wk.g[cb + wb]) - wk.g[cb + wa];
-            const float x = __fmul_rn(rs.beta[i], __ll2float_rn(dP * dg));
-            const uint32_t r = philox4x32_10(make_uint4(static_cast<uint32_t>(sa), n32, 0u, c3), k0, k1).x;
-            if (swap_accept(x, r)) {
-                at[sa] = wb;
-                at[sb] = wa;
-                rs.acc_P[rb + sa] += 1;
-            }
-        }
-    } else {
-        const int per_col = (I - parity) / 2;
-        const int total = J * per_col;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int j = idx / per_col;
-            const int i = parity + 2 * (idx - j * per_col);
-            const int sa = i * J + j, sb = sa + J;
-            const int wa = at[sa], wb = at[sb];
-            const float dbeta = __fsub_rn(rs.beta[i + 1], rs.beta[i]);
-            const long long Ea = wk.f[cb + wa] + static_cast<long long>(rs.P[j]) * wk.g[cb + wa];
-            const long long Eb = wk.f[cb + wb] + static_cast<long long>(rs.P[j]) * wk.g[cb + wb];
-            const float x = __fmul_rn(dbeta, __ll2float_rn(Eb - Ea));
-            const uint32_t r = philox4x32_10(make_uint4(static_cast<uint32_t>(sa), n32, 0u, c3), k0, k1).x;
-            if (swap_accept(x, r)) {
-                at[sa] = wb;
-                at[sb] = wa;
-                rs.acc_B[rb + sa] += 1;
-            }
-        }
-    }
+    const int *gw = wk.g + cb;
+    const long long *fw = reinterpret_cast<const long long *>(wk.f) + cb;
+    swap_pairs(at, [&](int w) { return fw[w]; }, [&](int w) { return gw[w]; }, rs.beta, rs.P, I, J,
+               static_cast<uint32_t>(run), nev, dir_p, k0, k1, rs.acc_P + rb, rs.acc_B + rb);
     __syncthreads();
     for (int s = threadIdx.x; s < R; s += blockDim.x) {
         const int w = at[s];
@@ -682,10 +514,9 @@ cudaError_t launch_swap_event(const Layout &L, const RunState &rs, const Walkers
     // Algorithm 1: direction +1 (P-swaps) for events 1, 2, then -1 (beta-swaps) for
     // 3, 4, ...: the direction flips after every even event; odd events use the
     // pairs starting at the first replica, even events those starting at the second.
-    const int parity = (event % 2 == 0) ? 1 : 0;
-    const int dir_p = (((event - 1) / 2) % 2 == 0) ? 1 : 0;
+    const int dir_p = event_is_pswap(event);
     const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
-    k_swap_event<<<rs.runs, 256, sizeof(int) * rs.R, st>>>(L, rs, wk, k0, k1, event, dir_p, parity);
+    k_swap_event<<<rs.runs, 256, sizeof(int) * rs.R, st>>>(L, rs, wk, k0, k1, event, dir_p);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,29 @@
+// Instance preparation shared by the plain contexts and the batch: validation,
+// greedy colouring, colour-sorted positions and packed neighbour records.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/pt2d.h"
+#include "pt2d_internal.h"
+
+namespace pt2d {
+
+struct Prep {
+    int32_t n = 0, I = 0, J = 0, R = 0, Rp = 0, runs = 0, C = 0, DC = 0, DL = 0;
+    int64_t Wc = 0;
+    int32_t trace_cap = 0;
+    pt2d::SweepTiling tiling{};
+    int32_t rec_vec = 0, pad_ref = 0;
+    std::vector<int32_t> color, pid, pos_of, cofs, rec;
+};
+
+// Validates the instance and ladders (beta / P may be NULL for size queries),
+// colours it, orders spins by colour and packs the neighbour records; with
+// force_dc > 0 the records use that coupling width (links 2) or the call fails.
+// Also chooses the plain-context sweep tiling from `opt` and `runs`.
+int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, const int32_t *P,
+            int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc = 0);
+
+}  // namespace pt2d

@@ -1,0 +1,220 @@
+// Device building blocks shared by the sweep kernels of the plain contexts and
+// the batched persistent kernel: spin-word byte access, packed neighbour
+// records, the four-walker heat-bath update and the swap event of Algorithm 1.
+#pragma once
+
+#include <cstdint>
+
+#include "pt2d_device.cuh"
+#include "pt2d_internal.h"
+
+namespace pt2d {
+
+// Philox key sources for update4: round keys from the kernel's parameter space
+// (one seed per launch), or a base key advanced per round (a seed per run).
+struct KeysConst {
+    RoundKeys rk;
+    __device__ __forceinline__ uint4 operator()(uint4 x) const { return philox4x32_10(x, rk); }
+};
+struct KeysBase {
+    uint32_t k0, k1;
+    __device__ __forceinline__ uint4 operator()(uint4 x) const { return philox4x32_10(x, k0, k1); }
+};
+
+// byte b of x, sign-extended (one PRMT in sign-replicate mode)
+template <int b>
+__device__ __forceinline__ int sbyte(uint32_t x) {
+    constexpr uint32_t n = 8u | b;
+    constexpr uint32_t sel = (n << 12) | (n << 8) | (n << 4) | static_cast<uint32_t>(b);
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(x), "n"(sel));
+    return static_cast<int>(d);
+}
+
+__device__ __forceinline__ int sbyte_rt(uint32_t x, int b) {
+    return static_cast<int>(static_cast<int8_t>(static_cast<uint8_t>(x >> (8 * b))));
+}
+
+// Spin word from the sign bits of four decision values: byte k = 0x01 (+1) when
+// t_k < 0, 0xFF (-1) otherwise.
+__device__ __forceinline__ uint32_t pack_signs(float t0, float t1, float t2, float t3) {
+    uint32_t lo, hi, m;
+    asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(lo) : "r"(__float_as_uint(t0)), "r"(__float_as_uint(t1)));
+    asm("prmt.b32 %0, %1, %2, 0x00FB;" : "=r"(hi) : "r"(__float_as_uint(t2)), "r"(__float_as_uint(t3)));
+    asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(m) : "r"(lo), "r"(hi));
+    return ~m | 0x01010101u;
+}
+
+constexpr int kMaxSlab = 128;  // walkers per CTA
+
+// Packed neighbour record of one position: [nb_0..nb_{DC-1}, lk_0..lk_{DL-1},
+// pid, 2h, 2J_0..2J_{DC-1}] padded to whole int4s.
+template <int DC, int DL>
+struct Rec {
+    static constexpr int kInts = 2 * DC + DL + 2;
+    static constexpr int kVec = (kInts + 3) / 4;
+    int v[kVec * 4];
+    __device__ __forceinline__ void load(const int4 *base, int pos) {
+        const int4 *p = base + static_cast<int64_t>(pos) * kVec;
+#pragma unroll
+        for (int i = 0; i < kVec; ++i) reinterpret_cast<int4 *>(v)[i] = __ldg(p + i);
+    }
+    __device__ __forceinline__ int nb(int k) const { return v[k]; }
+    __device__ __forceinline__ int lk(int l) const { return v[DC + l]; }
+    __device__ __forceinline__ int pid() const { return v[DC + DL]; }
+    __device__ __forceinline__ int h2() const { return v[DC + DL + 1]; }
+    __device__ __forceinline__ int j2(int k) const { return v[DC + DL + 2 + k]; }
+};
+
+struct Quad {
+    float b0, b1, b2, b3;  // beta of each walker's slot
+    float c0, c1, c2, c3;  // -beta * log2(e)
+    int p0, p1, p2, p3;    // P of each walker's slot
+};
+
+__device__ __forceinline__ Quad load_quad(const Walkers &wk, int64_t col) {
+    const float4 bt = *reinterpret_cast<const float4 *>(wk.wbeta + col);
+    const int4 pj = *reinterpret_cast<const int4 *>(wk.wP + col);
+    const float kNegL2E = -1.4426950408889634f;
+    return Quad{bt.x, bt.y, bt.z, bt.w, bt.x * kNegL2E, bt.y * kNegL2E, bt.z * kNegL2E,
+                bt.w * kNegL2E, pj.x, pj.y, pj.z, pj.w};
+}
+
+// New spin word of one quad at one position.  `fetch(row)` returns the quad's
+// spin word of a row (shared or global memory).
+template <int DC, int DL>
+__device__ __forceinline__ uint32_t decide4(const Rec<DC, DL> &rc, const Quad &q, const uint32_t *x,
+                                            const uint32_t *y, const uint4 &r) {
+    int a0 = rc.h2(), a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        const int j = rc.j2(k);
+        a0 += j * sbyte<0>(x[k]);
+        a1 += j * sbyte<1>(x[k]);
+        a2 += j * sbyte<2>(x[k]);
+        a3 += j * sbyte<3>(x[k]);
+    }
+    int l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+#pragma unroll
+    for (int l = 0; l < DL; ++l) {
+        l0 += sbyte<0>(y[l]);
+        l1 += sbyte<1>(y[l]);
+        l2 += sbyte<2>(y[l]);
+        l3 += sbyte<3>(y[l]);
+    }
+    a0 += q.p0 * l0;
+    a1 += q.p1 * l1;
+    a2 += q.p2 * l2;
+    a3 += q.p3 * l3;
+    float t0 = heatbath_fast(q.c0, a0, r.x), t1 = heatbath_fast(q.c1, a1, r.y);
+    float t2 = heatbath_fast(q.c2, a2, r.z), t3 = heatbath_fast(q.c3, a3, r.w);
+    // one branch for the four band tests; inside it the exact contract decides
+    if (fminf(fminf(fabsf(t0), fabsf(t1)), fminf(fabsf(t2), fabsf(t3))) <= kBand) {
+        if (fabsf(t0) <= kBand) t0 = heatbath_exact(q.b0, a0, r.x) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t1) <= kBand) t1 = heatbath_exact(q.b1, a1, r.y) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t2) <= kBand) t2 = heatbath_exact(q.b2, a2, r.z) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t3) <= kBand) t3 = heatbath_exact(q.b3, a3, r.w) > 0 ? -1.0f : 1.0f;
+    }
+    return pack_signs(t0, t1, t2, t3);
+}
+
+template <int DC, int DL, typename Fetch, typename Keys>
+__device__ __forceinline__ uint32_t update4(const Rec<DC, DL> &rc, const Quad &q, Fetch fetch,
+                                            uint32_t sweep, uint32_t lq, uint32_t c3,
+                                            const Keys &keys) {
+    uint32_t x[DC], y[DL];
+#pragma unroll
+    for (int k = 0; k < DC; ++k) x[k] = fetch(rc.nb(k));
+#pragma unroll
+    for (int l = 0; l < DL; ++l) y[l] = fetch(rc.lk(l));
+    const uint4 r = keys(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3));
+    return decide4<DC, DL>(rc, q, x, y, r);
+}
+
+// Eight walkers (two quads) at one position: one 8-byte fetch per neighbour,
+// two independent Philox calls (quads lq and lq + 1).
+template <int DC, int DL, typename Fetch8>
+__device__ __forceinline__ uint2 update8(const Rec<DC, DL> &rc, const Quad &qa, const Quad &qb,
+                                         Fetch8 fetch8, uint32_t sweep, uint32_t lq, uint32_t c3,
+                                         const KeysConst &keys) {
+    uint32_t xa[DC], ya[DL], xb[DC], yb[DL];
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        const uint2 w = fetch8(rc.nb(k));
+        xa[k] = w.x;
+        xb[k] = w.y;
+    }
+#pragma unroll
+    for (int l = 0; l < DL; ++l) {
+        const uint2 w = fetch8(rc.lk(l));
+        ya[l] = w.x;
+        yb[l] = w.y;
+    }
+    const uint32_t id = static_cast<uint32_t>(rc.pid());
+    const uint4 ra = keys(make_uint4(id, sweep, lq, c3));
+    const uint4 rb = keys(make_uint4(id, sweep, lq + 1, c3));
+    return make_uint2(decide4<DC, DL>(rc, qa, xa, ya, ra), decide4<DC, DL>(rc, qb, xb, yb, rb));
+}
+
+// The pair loop of one swap event of Algorithm 1 for one run, by the calling
+// CTA's threads (pairs of one event are disjoint, so they run in parallel).
+// at: slot -> walker (shared memory, permuted in place); fw / gw: f and g by
+// walker; acc_P / acc_B: accepted swaps by lower slot.  Event n uses the pairs
+// starting at the first replica when n is odd and at the second when n is
+// even; dir_p selects P-swaps inside rows (Eq. 2), otherwise beta-swaps inside
+// columns (Eq. 3).  Uniform: Philox SWAP stream at (lower slot, n, 0).
+template <typename FW, typename GW>
+__device__ __forceinline__ void swap_pairs(int *at, FW fw, GW gw, const float *beta,
+                                           const int32_t *P, int I, int J, uint32_t run,
+                                           int64_t nev, int dir_p, uint32_t k0, uint32_t k1,
+                                           int64_t *acc_P, int64_t *acc_B) {
+    const int parity = (nev % 2 == 0) ? 1 : 0;
+    const uint32_t c3 = (run << 4) | kTagSwap;
+    const uint32_t n32 = static_cast<uint32_t>(nev);
+    if (dir_p) {
+        const int per_row = (J - parity) / 2;
+        const int total = I * per_row;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int i = idx / per_row;
+            const int j = parity + 2 * (idx - i * per_row);
+            const int sa = i * J + j, sb = sa + 1;
+            const int wa = at[sa], wb = at[sb];
+            const long long dP = static_cast<long long>(P[j + 1]) - P[j];
+            const long long dg = static_cast<long long>(gw(wb)) - gw(wa);
+            const float x = __fmul_rn(beta[i], __ll2float_rn(dP * dg));
+            const uint32_t r = philox4x32_10(make_uint4(static_cast<uint32_t>(sa), n32, 0u, c3), k0, k1).x;
+            if (swap_accept(x, r)) {
+                at[sa] = wb;
+                at[sb] = wa;
+                acc_P[sa] += 1;
+            }
+        }
+    } else {
+        const int per_col = (I - parity) / 2;
+        const int total = J * per_col;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int j = idx / per_col;
+            const int i = parity + 2 * (idx - j * per_col);
+            const int sa = i * J + j, sb = sa + J;
+            const int wa = at[sa], wb = at[sb];
+            const float dbeta = __fsub_rn(beta[i + 1], beta[i]);
+            const long long Ea = fw(wa) + static_cast<long long>(P[j]) * gw(wa);
+            const long long Eb = fw(wb) + static_cast<long long>(P[j]) * gw(wb);
+            const float x = __fmul_rn(dbeta, __ll2float_rn(Eb - Ea));
+            const uint32_t r = philox4x32_10(make_uint4(static_cast<uint32_t>(sa), n32, 0u, c3), k0, k1).x;
+            if (swap_accept(x, r)) {
+                at[sa] = wb;
+                at[sb] = wa;
+                acc_B[sa] += 1;
+            }
+        }
+    }
+}
+
+// Direction of event n (Algorithm 1): +1 (P-swaps) for n = 1, 2, then -1 for
+// 3, 4, and so on, flipping after every even event.
+__host__ __device__ __forceinline__ int event_is_pswap(int64_t nev) {
+    return ((nev - 1) / 2) % 2 == 0 ? 1 : 0;
+}
+
+}  // namespace pt2d

@@ -1,0 +1,138 @@
+"""Batched persistent form vs the plain contexts and the oracle (tolerance zero).
+
+Every problem in a batch must follow exactly the trajectory a plain context
+with the same instance, ladders, seed and run count follows: spins, slot maps,
+f, g, swap counts, traces, best states and counters, whatever the launch
+shape, the placement of the spins (shared or global memory), the chunking of
+the events into launches, and the other problems sharing the batch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pt():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2506_14781_gb300 import build as b
+
+    b.build()
+    import paper_2506_14781_gb300 as m
+
+    return m
+
+
+WHATS = ["STATES", "WALKER_AT", "F", "G", "COUNTERS", "TRACE_F", "TRACE_G", "BEST_F", "BEST_EVENT",
+         "BEST_STATE", "SOLVED_EVENT", "ACC_P", "ACC_B", "SUM_F", "SUM_G", "N_FEASIBLE", "COLORS"]
+
+
+def _problem(pt, N, alpha, seed, rule, I, J, runs):
+    inst = synth.wishart_planted(N, alpha, seed)
+    phys = pt.sparsify(inst.Jq, *rule)
+    beta = synth.beta_ladder(I, 0.1, 2.0, inst.scale)
+    P = synth.penalty_ladder(J, 0.5, 4.0, 32767)
+    return dict(inst=inst, phys=phys, beta=beta, P=P, runs=runs, seed=1000 + seed,
+                target=inst.E_planted)
+
+
+def _plain(pt, pr, sweeps, interval, trace):
+    ctx = pt.PT2D(pr["phys"], pr["beta"], pr["P"], pr["runs"], trace_capacity=trace)
+    ctx.write(pt.TARGET, np.full(pr["runs"], pr["target"], np.int64))
+    ctx.run(sweeps, interval, pr["seed"])
+    return ctx
+
+
+def _assert_same(pt, batch, bid, ctx):
+    for w in WHATS:
+        a = batch.read(bid, getattr(pt, w))
+        b = ctx.read(getattr(pt, w))
+        if not np.array_equal(a, b):
+            bad = np.argwhere(a != b)
+            raise AssertionError(f"{w} differs at {bad[:5].tolist()} ({len(bad)} entries)")
+
+
+def _mixed(pt):
+    return [
+        _problem(pt, 12, 0.5, 1, ("max_degree", 4), 4, 4, 2),     # R = 16
+        _problem(pt, 30, 0.25, 2, ("max_degree", 4), 5, 3, 1),    # R = 15 (ragged)
+        _problem(pt, 57, 0.75, 3, ("max_degree", 4), 16, 8, 1),   # R = 128, n ~ 1.5k
+        _problem(pt, 90, 0.5, 4, ("max_degree", 4), 12, 8, 1),    # R = 96 (padded to 128)
+        _problem(pt, 40, 0.5, 5, ("max_edges", 3), 8, 8, 3),      # R = 64
+        _problem(pt, 160, 0.5, 6, ("max_degree", 4), 16, 8, 1),   # n ~ 12.6k: global memory
+    ]
+
+
+@pytest.mark.parametrize("spins_in_global,threads", [(False, 0), (True, 0), (False, 256)])
+def test_batch_matches_plain_contexts(pt, spins_in_global, threads):
+    probs = _mixed(pt)
+    trace = 16
+    batch = pt.Batch(1 << 30, max_coupling_degree=3, max_runs=64, trace_capacity=trace,
+                     threads_per_cta=threads, spins_in_global=spins_in_global)
+    ids = [batch.add(p["phys"], p["beta"], p["P"], p["runs"], p["seed"], p["target"]) for p in probs]
+    # 7 events of 5 sweeps, in three launches
+    batch.run(2, 5)
+    batch.run(4, 5)
+    batch.run(1, 5)
+    for pr, bid in zip(probs, ids):
+        ctx = _plain(pt, pr, 35, 5, trace)
+        _assert_same(pt, batch, bid, ctx)
+        ctx.close()
+    batch.close()
+
+
+def test_batch_add_remove_between_launches(pt):
+    a = _problem(pt, 20, 0.5, 11, ("max_degree", 4), 4, 4, 1)
+    b = _problem(pt, 45, 0.75, 12, ("max_degree", 4), 8, 4, 2)
+    c = _problem(pt, 33, 0.25, 13, ("max_degree", 4), 6, 5, 1)
+    batch = pt.Batch(1 << 28, max_coupling_degree=3, trace_capacity=8)
+    ia = batch.add(a["phys"], a["beta"], a["P"], a["runs"], a["seed"], a["target"])
+    ib = batch.add(b["phys"], b["beta"], b["P"], b["runs"], b["seed"], b["target"])
+    batch.run(3, 4)
+    batch.remove(ia)
+    ic = batch.add(c["phys"], c["beta"], c["P"], c["runs"], c["seed"], c["target"])
+    batch.run(4, 4)
+    _assert_same(pt, batch, ib, _plain(pt, b, 28, 4, 8))
+    _assert_same(pt, batch, ic, _plain(pt, c, 16, 4, 8))
+
+
+def test_batch_pool_full_and_autotune(pt):
+    a = _problem(pt, 60, 0.5, 21, ("max_degree", 4), 16, 8, 1)
+    probe = pt.Batch(1 << 26, max_coupling_degree=3, trace_capacity=4)
+    need = probe.instance_bytes(a["phys"], 16, 8, 1)
+    probe.close()
+    assert need > 0
+    batch = pt.Batch(2 * need + need // 2, max_coupling_degree=3, trace_capacity=4)
+    i1 = batch.add(a["phys"], a["beta"], a["P"], 1, a["seed"], a["target"])
+    i2 = batch.add(a["phys"], a["beta"], a["P"], 1, a["seed"] + 1, a["target"])
+    with pytest.raises(pt.PoolFull):
+        batch.add(a["phys"], a["beta"], a["P"], 1, a["seed"] + 2, a["target"])
+    threads, smem = batch.autotune(2, 3)  # 6 shapes x 2 launches of 2 events
+    assert threads in (256, 512, 1024)
+    batch.run(2, 3)
+    _assert_same(pt, batch, i1, _plain(pt, a, 13 * 2 * 3, 3, 4))
+    a2 = dict(a, seed=a["seed"] + 1)
+    _assert_same(pt, batch, i2, _plain(pt, a2, 13 * 2 * 3, 3, 4))
+
+
+def test_batch_matches_oracle_on_tiny_config(pt, tiny_config):
+    cfg = tiny_config
+    phys_p = pt.sparsify(cfg["inst"].Jq, "fixed", 2)
+    batch = pt.Batch(1 << 24, max_coupling_degree=6, trace_capacity=64)
+    bid = batch.add(phys_p, cfg["beta"], cfg["P"], 2, 7, cfg["inst"].E_planted)
+    batch.run(50, 2)
+    orc = oracle.OracleRun(oracle.OracleInstance(oracle.sparsify(cfg["inst"].Jq, "fixed", 2)),
+                           cfg["beta"], cfg["P"], [0, 1], 7, trace_cap=64,
+                           target=cfg["inst"].E_planted)
+    orc.run(100, 2)
+    for w, attr in (("STATES", "spins"), ("WALKER_AT", "walker_at"), ("F", "f"), ("G", "g"),
+                    ("TRACE_F", "trace_f"), ("TRACE_G", "trace_g"), ("BEST_F", "best_f"),
+                    ("BEST_STATE", "best_state"), ("ACC_P", "acc_P"), ("ACC_B", "acc_B"),
+                    ("SUM_F", "sum_f"), ("N_FEASIBLE", "n_feasible")):
+        assert np.array_equal(batch.read(bid, getattr(pt, w)), getattr(orc, attr)), w
