@@ -335,6 +335,192 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batched(args):
+    """Uneven-batch workload: planted Wishart instances with N uniform on
+    {50..400} and alpha in {0.25, 0.5, 0.75}, each copy-chain sparsified to
+    physical degree <= 4, I = 16 x J = 8, one run each, swap interval 50.
+    Times the batched persistent form against the one-instance-per-launch form
+    on the same events (identical trajectories), then continues the batched
+    form to `--tts-events` events for time-to-planted-ground-state."""
+    import torch
+
+    import paper_2506_14781_gb300 as pt
+    import synth
+
+    interval, I, J = 50, 16, 8
+    t0 = time.perf_counter()
+    probs = []
+    for N, alpha, seed in synth.batch_specs(args.instances, 1000):
+        inst = synth.wishart_planted(N, alpha, seed)
+        phys = pt.sparsify(inst.Jq, "max_degree", 4)
+        probs.append((inst, phys, synth.beta_ladder(I, 0.1, 2.0, inst.scale),
+                      synth.penalty_ladder(J, 0.5, 4.0, 32767), seed))
+    gen_s = time.perf_counter() - t0
+    spins = sum(p[1].n for p in probs)
+    upd_per_event = spins * I * J * interval
+    stream = torch.cuda.Stream()
+    probe = pt.Batch(1 << 22, 3, 8, stream=stream, trace_capacity=args.tts_events)
+    need = sum(probe.instance_bytes(p[1], I, J, 1) for p in probs)
+    probe.close()
+    batch = pt.Batch(int(need * 1.02) + (64 << 20), 3, len(probs), stream=stream,
+                     trace_capacity=args.tts_events)
+    ids = [batch.add(p[1], p[2], p[3], 1, p[4], p[0].E_planted) for p in probs]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    tuned = None
+    done_events = 0
+    if args.autotune:
+        tuned = batch.autotune(1, interval)
+        done_events += 12
+    batch.run(1, interval)
+    done_events += 1
+    E = args.steps
+    ev0.record(stream)
+    batch.run(E, interval)
+    ev1.record(stream)
+    ev1.synchronize()
+    t_batched = ev0.elapsed_time(ev1) / 1e3
+    done_events += E
+    # one-instance-per-launch form: a context per instance, run one after the other
+    plain = None
+    if not args.no_plain:
+        ctxs = [pt.PT2D(p[1], p[2], p[3], 1, stream=stream, trace_capacity=1) for p in probs]
+        for c, p in zip(ctxs, probs):
+            c.run(interval, interval, p[4])
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for c, p in zip(ctxs, probs):
+            c.run(E * interval, interval, p[4])
+        ev1.record(stream)
+        ev1.synchronize()
+        t_plain = ev0.elapsed_time(ev1) / 1e3
+        launches = sum(c.launch_count for c in ctxs)
+        for c in ctxs:
+            c.close()
+        plain = {"seconds": t_plain, "updates_per_s": upd_per_event * E / t_plain,
+                 "launches_total": int(launches)}
+    # continue the batched form for time to planted ground state
+    t_tts = t_batched
+    chunk = 20
+    while done_events < args.tts_events:
+        k = min(chunk, args.tts_events - done_events)
+        ev0.record(stream)
+        batch.run(k, interval)
+        ev1.record(stream)
+        ev1.synchronize()
+        t_tts += ev0.elapsed_time(ev1) / 1e3
+        done_events += k
+    sec_per_event = t_batched / E
+    solved = np.array([batch.read(i, pt.SOLVED_EVENT)[0] for i in ids])
+    Ns = np.array([p[0].N for p in probs])
+    ok = solved >= 0
+    tts = {
+        "target": "bottom-right g=0 and f <= planted energy",
+        "events_run": int(done_events), "sweeps_run": int(done_events * interval),
+        "solved": int(ok.sum()), "instances": len(probs),
+        "median_sweeps_to_solve": float(np.median(solved[ok] * interval)) if ok.any() else None,
+        "p90_sweeps_to_solve": float(np.percentile(solved[ok] * interval, 90)) if ok.any() else None,
+        "median_seconds_to_solve_batched": float(np.median(solved[ok]) * sec_per_event) if ok.any() else None,
+        "solved_by_N": {f"{lo}-{lo + 49}": [int(ok[(Ns >= lo) & (Ns < lo + 50)].sum()),
+                                             int(((Ns >= lo) & (Ns < lo + 50)).sum())]
+                        for lo in range(50, 401, 50)},
+    }
+    line = {
+        "metric": "spin updates/sec and time-to-planted-ground-state (batched vs plain)",
+        "value": upd_per_event * E / t_batched, "unit": UNIT, "n_gpus": 1, "steps": E,
+        "warmup": 1, "ms_per_step": t_batched / E * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8 spins, int32 fields, f32 decisions",
+        "data": "synthetic (seeded planted Wishart instances)",
+        "config": {"workload": f"{len(probs)} planted Wishart instances, N~U{{50..400}}, alpha in "
+                               f"{{0.25,0.5,0.75}}, physical degree <= 4, I=16 x J=8, 1 run each, "
+                               f"swap every 50 sweeps", "physical_spins_total": int(spins),
+                   "instance_generation_s": gen_s},
+        "batched": {"seconds": t_batched, "updates_per_s": upd_per_event * E / t_batched,
+                    "launches": 1, "autotuned_threads_smem": tuned},
+        "plain": plain,
+        "speedup_batched_over_plain": (plain["seconds"] / t_batched) if plain else None,
+        "tts": tts,
+    }
+    print(json.dumps(line))
+
+
+def run_serving(args):
+    """Serving workload: a Poisson stream of constrained Ising requests at
+    `--rates` requests per minute for `--duration` seconds each.  A request is a
+    planted Wishart problem (N uniform on 50..800, alpha uniform on
+    [0.25, 0.75], <= 3 original edges per copy) with an I = 16 x J = 8 grid, run
+    until its bottom-right replica is feasible at the planted energy or 5 x 10^4
+    sweeps.  Problems are drawn from 256 pre-generated instances, each request
+    with its own seed, so instance generation stays out of the timed loop."""
+    import torch  # noqa: F401  (CUDA context for the library)
+
+    import paper_2506_14781_gb300 as pt
+    import synth
+
+    specs = synth.request_specs(256, 5)
+    pool = []
+    for N, alpha, seed in specs:
+        inst = synth.wishart_planted(N, alpha, seed)
+        phys = pt.sparsify(inst.Jq, "max_edges", 3)
+        pool.append((inst, phys, synth.beta_ladder(16, 0.1, 2.0, inst.scale),
+                     synth.penalty_ladder(8, 0.5, 4.0, 32767)))
+    results = []
+    for rate in args.rates:
+        arrivals = synth.poisson_arrivals(rate, args.duration, 5 + int(rate))
+        rng = np.random.default_rng(int(rate))
+        picks = rng.integers(0, len(pool), arrivals.size)
+        srv = pt.Server(args.pool_gb << 30, 3, args.max_requests, 50, args.events_per_step)
+        ids = []
+        t0 = time.perf_counter()
+        nxt = 0
+        steps = 0
+        updates = 0
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < arrivals.size and arrivals[nxt] <= now:
+                inst, phys, beta, P = pool[picks[nxt]]
+                ids.append((srv.submit(phys, beta, P, 77 + nxt, inst.E_planted, 50000), phys.n))
+                nxt += 1
+            if now > args.duration + args.drain:
+                break
+            active, queued, _ = srv.step()
+            steps += 1
+            if active == 0 and queued == 0:
+                if nxt >= arrivals.size:
+                    break
+                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+        wall = time.perf_counter() - t0
+        lat, solved, done = [], 0, 0
+        for rid, n in ids:
+            st = srv.status(rid)
+            if st["state"] == "done":
+                done += 1
+                lat.append(st["t_done"] - st["t_submit"])
+                solved += st["solved_event"] >= 0
+                updates += n * 128 * st["sweeps_done"]
+        srv.close()
+        lat = np.array(lat)
+        results.append({
+            "rate_per_min": rate, "submitted": len(ids), "completed": done, "solved": int(solved),
+            "unfinished_at_end": len(ids) - done, "wall_s": wall, "steps": steps,
+            "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "solves_per_s": solved / wall, "completed_per_s": done / wall,
+            "spin_updates_per_s_completed": updates / wall,
+        })
+    line = {
+        "metric": "serving p50/p99 latency and solves/sec", "value": results[0]["solves_per_s"],
+        "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "Poisson stream of planted Wishart requests, N~U[50,800], "
+                               "alpha~U[0.25,0.75], <=3 edges/copy, I=16 x J=8, stop at g=0 + "
+                               "planted energy or 5e4 sweeps", "duration_s": args.duration,
+                   "drain_s": args.drain, "events_per_step": args.events_per_step,
+                   "pool_gb": args.pool_gb, "max_resident": args.max_requests},
+        "loads": results,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,11 +529,26 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="n200", choices=["n200", "batched", "serving"])
+    ap.add_argument("--rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
+    ap.add_argument("--duration", type=float, default=30.0)
+    ap.add_argument("--drain", type=float, default=30.0)
+    ap.add_argument("--events-per-step", type=int, default=20)
+    ap.add_argument("--pool-gb", type=int, default=16)
+    ap.add_argument("--max-requests", type=int, default=1024)
+    ap.add_argument("--instances", type=int, default=1024)
+    ap.add_argument("--tts-events", type=int, default=400)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

@@ -257,11 +257,77 @@ int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval,
 int pt2d_batch_read(pt2d_batch *b, int64_t id, int32_t what, void *host_dst, size_t bytes);
 size_t pt2d_batch_array_bytes(const pt2d_batch *b, int64_t id, int32_t what);
 
+/* Status of every problem after the last launch (synchronises): ids[k],
+ * solved_event[k] (earliest event at which one of its runs was solved, -1 if
+ * none) and events_done[k], for at most `capacity` problems; *count = number
+ * of problems.  Problems added since the last launch are not listed.
+ * Errors: INVALID_ARG, CUDA. */
+int pt2d_batch_poll(pt2d_batch *b, int64_t *ids, int64_t *solved_event, int64_t *events_done,
+                    int32_t capacity, int32_t *count);
+
 int pt2d_batch_sync(pt2d_batch *b);
 size_t pt2d_batch_free_bytes(const pt2d_batch *b);   /* largest free block of the pool */
 int64_t pt2d_batch_launch_count(const pt2d_batch *b);
 int pt2d_batch_cuda_error(const pt2d_batch *b);
 void pt2d_batch_destroy(pt2d_batch *b);
+
+/* ---- continuous-batching server ------------------------------------------- */
+/* A request loop over the batched form: requests (one constrained Ising
+ * problem each, with its ladders, seed, target energy and sweep limit) wait in
+ * a FIFO queue; pt2d_server_step admits queued requests in order while the
+ * device pool has room, advances every resident request by `events_per_step`
+ * swap events in one batched launch, and evicts those that are solved (the
+ * bottom-right replica has g == 0 and f <= target) or have used max_sweeps,
+ * keeping each one's lowest-energy feasible state.  A request's result does
+ * not depend on the other requests resident with it. */
+typedef struct pt2d_server pt2d_server;
+
+#define PT2D_REQUEST_QUEUED 0
+#define PT2D_REQUEST_RUNNING 1
+#define PT2D_REQUEST_DONE 2
+#define PT2D_REQUEST_CANCELLED 3
+#define PT2D_REQUEST_FAILED 4
+
+typedef struct {
+    int32_t state;         /* PT2D_REQUEST_*                                     */
+    int32_t error;         /* status code when FAILED                            */
+    int32_t n;             /* physical spins                                      */
+    int64_t best_f;        /* lowest bottom-right f with g == 0 (INT64_MAX: none) */
+    int64_t best_event;    /* event of best_f, -1 if none                         */
+    int64_t solved_event;  /* first event with g == 0 and f <= target, -1 if none */
+    int64_t sweeps_done;
+    double t_submit, t_admit, t_done;  /* seconds since the server was created    */
+} pt2d_request_status;
+
+/* pool_bytes: device bytes for resident problems; max_requests: most resident
+ * at once; swap_interval: sweeps per event; events_per_step: events per
+ * launch.  opt as for pt2d_batch_create.  Errors: those of pt2d_batch_create. */
+int pt2d_server_create(pt2d_server **out, size_t pool_bytes, int32_t max_coupling_degree,
+                       int32_t max_requests, int32_t swap_interval, int32_t events_per_step,
+                       const pt2d_options *opt);
+
+/* Queue a request (the problem is copied).  Errors: INVALID_ARG. */
+int pt2d_server_submit(pt2d_server *s, const pt2d_instance *inst, int32_t I, const float *beta,
+                       int32_t J, const int32_t *P, uint64_t seed, int64_t target,
+                       int64_t max_sweeps, int64_t *request_id);
+
+/* Admit, run one launch, evict finished requests; reports resident, queued
+ * and just-finished counts (outputs may be NULL).  Synchronises.  Errors: CUDA. */
+int pt2d_server_step(pt2d_server *s, int32_t *active, int32_t *queued, int32_t *finished);
+
+/* State and results of a request; best_state[n] (spins by id) is filled for a
+ * finished request when not NULL.  Errors: INVALID_ARG. */
+int pt2d_server_status(pt2d_server *s, int64_t request_id, pt2d_request_status *status,
+                       int8_t *best_state);
+
+/* Cancel a queued or resident request (its memory returns to the pool). */
+int pt2d_server_cancel(pt2d_server *s, int64_t request_id);
+
+/* Drop a finished, cancelled or failed request's record.  Errors: STATE. */
+int pt2d_server_forget(pt2d_server *s, int64_t request_id);
+
+size_t pt2d_server_free_bytes(const pt2d_server *s);
+void pt2d_server_destroy(pt2d_server *s);
 
 /* ---- one-shot run without device allocation ------------------------------ */
 /* The paper has no counterpart to this entry point; it exists for callers that

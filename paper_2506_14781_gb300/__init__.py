@@ -18,7 +18,8 @@ from ._lib import (ACC_B, ACC_P, BEST_EVENT, BEST_F, BEST_STATE, COLORS, COUNTER
                    WALKER_AT, Pt2dError)
 
 __all__ = [
-    "PhysicalInstance", "sparsify", "greedy_color", "PT2D", "Batch", "PoolFull", "Pt2dError",
+    "PhysicalInstance", "sparsify", "greedy_color", "PT2D", "Batch", "PoolFull", "Server",
+    "Pt2dError",
     "diag_philox",
     "diag_pt_exp", "diag_heatbath", "diag_swap_accept", "STATES", "WALKER_AT", "F", "G",
     "COUNTERS", "TRACE_F", "TRACE_G", "BEST_F", "BEST_EVENT", "BEST_STATE", "SOLVED_EVENT",
@@ -330,6 +331,76 @@ class Batch:
         if getattr(self, "_b", None) and self._b.value:
             _lib.lib().pt2d_batch_destroy(self._b)
             self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (pt2d_server_*)."""
+
+    def __init__(self, pool_bytes: int, max_coupling_degree: int = 3, max_requests: int = 1024,
+                 swap_interval: int = 50, events_per_step: int = 10, *, stream=None,
+                 threads_per_cta: int = 0, spins_in_global: bool = True, device: int = -1):
+        L = _lib.lib()
+        opt = _lib.Options()
+        L.pt2d_default_options(C.byref(opt))
+        opt.threads_per_cta = int(threads_per_cta)
+        opt.sweep_kernel = 1 if spins_in_global else 0
+        opt.device = int(device)
+        self._stream_obj = stream
+        if stream is not None:
+            opt.stream = int(getattr(stream, "cuda_stream", stream))
+        self._s = C.c_void_p()
+        _lib.check(L.pt2d_server_create(C.byref(self._s), int(pool_bytes), int(max_coupling_degree),
+                                        int(max_requests), int(swap_interval), int(events_per_step),
+                                        C.byref(opt)), "pt2d_server_create")
+
+    def submit(self, inst: PhysicalInstance, beta, P, seed: int, target: int, max_sweeps: int) -> int:
+        beta = np.ascontiguousarray(beta, dtype=np.float32)
+        P = np.ascontiguousarray(P, dtype=np.int32)
+        cs = inst.c_struct()
+        rid = C.c_int64()
+        _lib.check(_lib.lib().pt2d_server_submit(self._s, C.byref(cs), beta.size, _p(beta), P.size,
+                                                 _p(P), int(seed), int(target), int(max_sweeps),
+                                                 C.byref(rid)), "pt2d_server_submit")
+        return rid.value
+
+    def step(self):
+        a, q, f = C.c_int32(), C.c_int32(), C.c_int32()
+        _lib.check(_lib.lib().pt2d_server_step(self._s, C.byref(a), C.byref(q), C.byref(f)),
+                   "pt2d_server_step")
+        return a.value, q.value, f.value
+
+    def status(self, rid: int, with_state: bool = False) -> dict:
+        st = _lib.RequestStatus()
+        L = _lib.lib()
+        _lib.check(L.pt2d_server_status(self._s, int(rid), C.byref(st), None), "pt2d_server_status")
+        out = {k: getattr(st, k) for k, _ in _lib.RequestStatus._fields_}
+        out["state"] = _lib.REQUEST_STATES[st.state]
+        if with_state and st.state == 2:
+            s = np.zeros(st.n, np.int8)
+            _lib.check(L.pt2d_server_status(self._s, int(rid), C.byref(st), _p(s)), "pt2d_server_status")
+            out["best_state"] = s
+        return out
+
+    def cancel(self, rid: int) -> None:
+        _lib.check(_lib.lib().pt2d_server_cancel(self._s, int(rid)), "pt2d_server_cancel")
+
+    def forget(self, rid: int) -> None:
+        _lib.check(_lib.lib().pt2d_server_forget(self._s, int(rid)), "pt2d_server_forget")
+
+    @property
+    def free_bytes(self) -> int:
+        return int(_lib.lib().pt2d_server_free_bytes(self._s))
+
+    def close(self) -> None:
+        if getattr(self, "_s", None) and self._s.value:
+            _lib.lib().pt2d_server_destroy(self._s)
+            self._s = C.c_void_p()
 
     def __del__(self):
         try:

@@ -34,7 +34,9 @@ EXPORTS = [
     "pt2d_kernel_time", "pt2d_run_noalloc", "pt2d_batch_create", "pt2d_batch_instance_bytes",
     "pt2d_batch_add", "pt2d_batch_remove", "pt2d_batch_run", "pt2d_batch_autotune",
     "pt2d_batch_read", "pt2d_batch_array_bytes", "pt2d_batch_sync", "pt2d_batch_free_bytes",
-    "pt2d_batch_launch_count", "pt2d_batch_cuda_error", "pt2d_batch_destroy",
+    "pt2d_batch_launch_count", "pt2d_batch_cuda_error", "pt2d_batch_destroy", "pt2d_batch_poll",
+    "pt2d_server_create", "pt2d_server_submit", "pt2d_server_step", "pt2d_server_status",
+    "pt2d_server_cancel", "pt2d_server_forget", "pt2d_server_free_bytes", "pt2d_server_destroy",
 ]
 
 
@@ -64,6 +66,24 @@ class Options(C.Structure):
         ("sweep_kernel", C.c_int32),
         ("walkers_per_thread", C.c_int32),
     ]
+
+
+class RequestStatus(C.Structure):
+    _fields_ = [
+        ("state", C.c_int32),
+        ("error", C.c_int32),
+        ("n", C.c_int32),
+        ("best_f", C.c_int64),
+        ("best_event", C.c_int64),
+        ("solved_event", C.c_int64),
+        ("sweeps_done", C.c_int64),
+        ("t_submit", C.c_double),
+        ("t_admit", C.c_double),
+        ("t_done", C.c_double),
+    ]
+
+
+REQUEST_STATES = {0: "queued", 1: "running", 2: "done", 3: "cancelled", 4: "failed"}
 
 
 class Pt2dError(RuntimeError):
@@ -133,6 +153,18 @@ def lib():
         L.pt2d_batch_cuda_error.argtypes = [vp]
         L.pt2d_batch_destroy.argtypes = [vp]
         L.pt2d_batch_destroy.restype = None
+        L.pt2d_batch_poll.argtypes = [vp, vp, vp, vp, i32, C.POINTER(i32)]
+        L.pt2d_server_create.argtypes = [C.POINTER(vp), sz, i32, i32, i32, i32, vp]
+        L.pt2d_server_submit.argtypes = [vp, vp, i32, vp, i32, vp, C.c_uint64, i64, i64,
+                                         C.POINTER(i64)]
+        L.pt2d_server_step.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.pt2d_server_status.argtypes = [vp, i64, vp, vp]
+        L.pt2d_server_cancel.argtypes = [vp, i64]
+        L.pt2d_server_forget.argtypes = [vp, i64]
+        L.pt2d_server_free_bytes.argtypes = [vp]
+        L.pt2d_server_free_bytes.restype = sz
+        L.pt2d_server_destroy.argtypes = [vp]
+        L.pt2d_server_destroy.restype = None
         for name in EXPORTS:
             getattr(L, name)  # every declared entry point must be exported
         _lib = L

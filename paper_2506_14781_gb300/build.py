@@ -22,7 +22,8 @@ LIB = os.path.join(HERE, "libpt2d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
-SOURCES = ["pt2d_kernels.cu", "pt2d_host.cpp", "pt2d_noalloc.cu", "pt2d_batch.cu", "pt2d_batch_host.cpp"]
+SOURCES = ["pt2d_kernels.cu", "pt2d_host.cpp", "pt2d_noalloc.cu", "pt2d_batch.cu", "pt2d_batch_host.cpp",
+           "pt2d_server.cpp"]
 
 
 def _nvcc() -> str:

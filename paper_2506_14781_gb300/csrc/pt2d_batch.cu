@@ -249,6 +249,12 @@ __device__ void run_events(const BatchArgs &a, const BatchRun &d, uint8_t *dsm) 
     }
 }
 
+__device__ void write_status(const BatchArgs &a, int item, const BatchRun &d) {
+    const int64_t *sc = reinterpret_cast<const int64_t *>(a.pool + d.scalars);
+    a.status[2 * item] = sc[kScSolvedEvent];
+    a.status[2 * item + 1] = sc[kScEvents];
+}
+
 template <int DC, int DL>
 __global__ void __launch_bounds__(1024, 1) k_batch(BatchArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
@@ -261,6 +267,8 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchArgs a) {
         if (item >= a.n_runs) break;
         const BatchRun d = a.runs[item];
         run_events<DC, DL>(a, d, dsm);
+        __syncthreads();
+        if (threadIdx.x == 0) write_status(a, item, d);
     }
 }
 

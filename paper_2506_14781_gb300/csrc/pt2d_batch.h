@@ -48,6 +48,7 @@ struct BatchArgs {
     int32_t events;        // events per run in this launch
     int32_t interval;      // sweeps per event
     int32_t smem_state;    // dynamic shared memory reserved for one run's spins
+    int64_t *status;       // [n_runs][2]: solved event (-1 none), events done, per launch order
 };
 
 size_t batch_small_smem_bytes();

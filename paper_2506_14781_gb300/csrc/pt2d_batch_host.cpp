@@ -150,6 +150,8 @@ struct pt2d_batch {
     int64_t next_id = 1;
     pt2d::BatchRun *d_runs = nullptr;
     int32_t *d_queue = nullptr;
+    int64_t *d_status = nullptr;                      // [max_runs][2]
+    std::vector<std::pair<int64_t, int32_t>> order;  // launch order: (id, run)
     int32_t n_runs = 0;
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
@@ -179,14 +181,20 @@ void drop_graph(pt2d_batch *b) {
 }
 
 int upload_descriptors(pt2d_batch *b) {
-    std::vector<pt2d::BatchRun> all;
+    std::vector<std::pair<pt2d::BatchRun, std::pair<int64_t, int32_t>>> tagged;
     for (auto &kv : b->insts)
         for (auto &d : kv.second.desc) {
             d.use_smem = static_cast<int64_t>(d.n + 1) * d.Rp <= b->smem_state ? 1 : 0;
-            all.push_back(d);
+            tagged.push_back({d, {kv.first, d.run}});
         }
-    std::stable_sort(all.begin(), all.end(),
-                     [](const pt2d::BatchRun &x, const pt2d::BatchRun &y) { return x.work > y.work; });
+    std::stable_sort(tagged.begin(), tagged.end(),
+                     [](const auto &x, const auto &y) { return x.first.work > y.first.work; });
+    std::vector<pt2d::BatchRun> all;
+    b->order.clear();
+    for (const auto &t : tagged) {
+        all.push_back(t.first);
+        b->order.push_back(t.second);
+    }
     if (static_cast<int32_t>(all.size()) > b->max_runs) return PT2D_ERR_OOM;
     if (!all.empty())
         BK(b, cudaMemcpyAsync(b->d_runs, all.data(), sizeof(pt2d::BatchRun) * all.size(),
@@ -203,7 +211,8 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
         if (st) return st;
     }
     if (b->n_runs == 0 || events == 0) return PT2D_OK;
-    pt2d::BatchArgs a{b->pool, b->d_runs, b->n_runs, b->d_queue, events, interval, b->smem_state};
+    pt2d::BatchArgs a{b->pool, b->d_runs, b->n_runs, b->d_queue, events, interval, b->smem_state,
+                      b->d_status};
     const int grid = std::min(b->grid, b->n_runs);
     BK(b, pt2d::batch_kernel_attributes(b->DC, 2, b->smem_state));
     if (!b->use_graph) {
@@ -297,7 +306,8 @@ int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_
         }
         b->own_stream = true;
     }
-    const size_t head = align_up(sizeof(int32_t)) + align_up(sizeof(pt2d::BatchRun) * max_runs);
+    const size_t head = align_up(sizeof(int32_t)) + align_up(sizeof(pt2d::BatchRun) * max_runs) +
+                        align_up(sizeof(int64_t) * 2 * max_runs);
     if (opt->workspace) {
         if (opt->workspace_bytes < head + 4096 || (reinterpret_cast<uintptr_t>(opt->workspace) & 255)) {
             pt2d_batch_destroy(b);
@@ -316,6 +326,8 @@ int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_
     }
     b->d_queue = reinterpret_cast<int32_t *>(b->pool);
     b->d_runs = reinterpret_cast<pt2d::BatchRun *>(b->pool + align_up(sizeof(int32_t)));
+    b->d_status = reinterpret_cast<int64_t *>(b->pool + align_up(sizeof(int32_t)) +
+                                              align_up(sizeof(pt2d::BatchRun) * max_runs));
     b->arena.reset(head, b->pool_bytes - head);
     *out = b;
     return PT2D_OK;
@@ -484,6 +496,44 @@ int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, in
     }
     if (threads_out) *threads_out = best_t;
     if (smem_out) *smem_out = best_s;
+    return PT2D_OK;
+}
+
+int pt2d_batch_poll(pt2d_batch *b, int64_t *ids, int64_t *solved_event, int64_t *events_done,
+                    int32_t capacity, int32_t *count) {
+    if (!b || !count || (capacity > 0 && (!ids || !solved_event || !events_done)))
+        return PT2D_ERR_INVALID_ARG;
+    cudaSetDevice(b->device);
+    std::vector<int64_t> st(2 * b->order.size());
+    if (!st.empty()) {
+        BK(b, cudaMemcpyAsync(st.data(), b->d_status, sizeof(int64_t) * st.size(),
+                              cudaMemcpyDeviceToHost, b->stream));
+    }
+    BK(b, cudaStreamSynchronize(b->stream));
+    // aggregate over runs: solved at the earliest run's solving event
+    std::map<int64_t, std::pair<int64_t, int64_t>> agg;
+    for (size_t i = 0; i < b->order.size(); ++i) {
+        const int64_t id = b->order[i].first;
+        if (!b->insts.count(id)) continue;
+        auto it = agg.find(id);
+        const int64_t se = st[2 * i], ev = st[2 * i + 1];
+        if (it == agg.end()) {
+            agg[id] = {se, ev};
+        } else {
+            if (se >= 0 && (it->second.first < 0 || se < it->second.first)) it->second.first = se;
+            it->second.second = std::min(it->second.second, ev);
+        }
+    }
+    int32_t k = 0;
+    for (const auto &kv : agg) {
+        if (k < capacity) {
+            ids[k] = kv.first;
+            solved_event[k] = kv.second.first;
+            events_done[k] = kv.second.second;
+        }
+        ++k;
+    }
+    *count = k;
     return PT2D_OK;
 }
 

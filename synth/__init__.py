@@ -10,7 +10,7 @@ sharing any method code.
 """
 from .wishart import WishartInstance, wishart_planted
 from .ladders import beta_ladder, penalty_ladder
-from .arrivals import poisson_arrivals, request_specs
+from .arrivals import batch_specs, poisson_arrivals, request_specs
 
 __all__ = [
     "WishartInstance",
@@ -19,4 +19,5 @@ __all__ = [
     "penalty_ladder",
     "poisson_arrivals",
     "request_specs",
+    "batch_specs",
 ]

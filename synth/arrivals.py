@@ -31,3 +31,13 @@ def request_specs(count: int, seed: int, n_min: int = 50, n_max: int = 800,
     alphas = rng.uniform(alpha_min, alpha_max, size=count)
     seeds = rng.integers(1, 2**31 - 1, size=count)
     return [(int(n), float(a), int(s)) for n, a, s in zip(Ns, alphas, seeds)]
+
+
+def batch_specs(count: int, seed: int, n_min: int = 50, n_max: int = 400,
+                alphas=(0.25, 0.5, 0.75)):
+    """Per-instance (N, alpha, instance seed) for a batch of uneven instances:
+    N uniform on {n_min..n_max}, alpha uniform on the given set."""
+    rng = np.random.Generator(np.random.Philox(int(seed) + 104729))
+    Ns = rng.integers(n_min, n_max + 1, size=count)
+    al = rng.choice(np.asarray(alphas, dtype=np.float64), size=count)
+    return [(int(n), float(a), int(seed) + i) for i, (n, a) in enumerate(zip(Ns, al))]
