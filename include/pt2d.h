@@ -199,14 +199,14 @@ int pt2d_cuda_error(const pt2d_ctx *ctx);
 /* ---- batched persistent form ------------------------------------------------ */
 /* Many independent 2D-PT problems of uneven size (each an instance with its own
  * ladders, runs and seed) simulated by one persistent kernel (Algorithm 1 for
- * each run).  A CTA owns one whole run (I * J <= 128 replicas) and carries it
- * through the requested events: sweeps, f and g of the final sweep, the swap
- * event and the bottom-right record, without leaving the kernel; CTAs take
- * runs from a work list sorted by decreasing size.  A run's spins stay in
- * shared memory for the launch when they fit.  Launches are replayed from a
- * CUDA graph.  Each run follows exactly the trajectory of a context created
- * with pt2d_create on the same instance and ladders, run with the same seed
- * (run r of an instance uses run index r).
+ * each run, I * J <= 128 replicas per run).  Each launch advances every run by
+ * one event: a run's replicas are split into slabs, CTAs take slabs from a
+ * work list sorted by decreasing run size and perform the sweeps and f and g
+ * (a slab's spins in shared memory when they fit), and the CTA finishing a
+ * run's last slab performs its swap event and bottom-right record.  Events are
+ * launches replayed from a CUDA graph.  Each run follows exactly the
+ * trajectory of a context created with pt2d_create on the same instance and
+ * ladders, run with the same seed (run r of an instance uses run index r).
  *
  * Memory: the batch owns a device pool (or uses opt->workspace); instances are
  * added and removed at any time between launches (continuous batching), and
@@ -245,10 +245,11 @@ int pt2d_batch_remove(pt2d_batch *b, int64_t id);
  * OOM (more runs than max_runs), CUDA. */
 int pt2d_batch_run(pt2d_batch *b, int32_t events, int32_t swap_interval);
 
-/* Time every launch shape (threads per CTA 256 / 512 / 1024; spins in shared
- * or global memory) on two launches of `events` events each and keep the
- * fastest.  The trial launches advance the chains like pt2d_batch_run (every
- * shape computes the same trajectories).  Outputs may be NULL. */
+/* Time every launch shape (threads per CTA 512 / 1024; slabs held in shared
+ * memory where they fit, or all spins in global memory; 16 or 64 walkers per
+ * global-memory slab) on two launches of `events` events each and keep the
+ * fastest.  The 16 trial launches advance the chains like pt2d_batch_run
+ * (every shape computes the same trajectories).  Outputs may be NULL. */
 int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval,
                         int32_t *threads_per_cta, int32_t *smem_state_bytes);
 

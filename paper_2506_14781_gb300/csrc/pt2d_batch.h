@@ -30,25 +30,37 @@ struct BatchRun {
     int64_t beta;        // float [I]
     int64_t P;           // int32 [J]
     int64_t walker_at;   // int32 [R] slot -> walker
+    int64_t wparam;      // float beta [Rp], then int32 P [Rp]: each walker's current slot values
     int64_t fg;          // int64 f [Rp], then int32 g [Rp] (last event)
     int64_t stats;       // int64 acc_P, acc_B, sum_f, sum_g, n_feasible [R] each
     int64_t trace;       // int64 trace_f [trace_cap], then trace_g [trace_cap]
     int64_t best_state;  // int8 [n] by spin id
     int64_t scalars;     // int64 [kScCount]
+    int64_t counter;     // int32: slabs of this run finished in the current launch
     uint32_t k0, k1;     // seed
-    int32_t n, C, I, J, R, Rp, run, trace_cap, rec_vec, use_smem;
+    int32_t n, C, I, J, R, Rp, run, trace_cap, rec_vec;
+    int32_t sw;          // walkers per slab (power of two, 16..Rp)
+    int32_t nslab;       // Rp / sw
+    int32_t pad;
     int64_t work;        // n * Rp, for ordering
+};
+
+// One slab of one run: the unit a CTA takes from the work list.
+struct BatchItem {
+    int32_t run;   // index into the run array
+    int32_t slab;  // walkers [slab * sw, (slab + 1) * sw) of the run
 };
 
 struct BatchArgs {
     uint8_t *pool;
-    const BatchRun *runs;  // [n_runs], largest first
+    const BatchRun *runs;    // [n_runs]
+    const BatchItem *items;  // [n_items], largest runs first
     int32_t n_runs;
-    int32_t *queue;        // work counter, zero at launch
-    int32_t events;        // events per run in this launch
-    int32_t interval;      // sweeps per event
-    int32_t smem_state;    // dynamic shared memory reserved for one run's spins
-    int64_t *status;       // [n_runs][2]: solved event (-1 none), events done, per launch order
+    int32_t n_items;
+    int32_t *queue;          // work counter, zero at launch
+    int32_t interval;        // sweeps per event
+    int32_t smem_state;      // dynamic shared memory available for one slab's spins
+    int64_t *status;         // [n_runs][2]: solved event (-1 none), events done
 };
 
 size_t batch_small_smem_bytes();

@@ -84,7 +84,7 @@ struct Inst {
 struct Layout1 {  // byte offsets within an instance block
     size_t rec, cofs, beta, P, total;
     size_t run0, run_stride;
-    size_t state, walker_at, fg, stats, trace, best_state, scalars;  // relative to a run
+    size_t state, walker_at, wparam, fg, stats, trace, best_state, scalars, counter;  // per run
 };
 
 Layout1 block_layout(int32_t n, int32_t C, int32_t rec_vec, int32_t I, int32_t J, int32_t R,
@@ -105,6 +105,8 @@ Layout1 block_layout(int32_t n, int32_t C, int32_t rec_vec, int32_t I, int32_t J
     r = align_up(r + static_cast<size_t>(n + 1) * Rp);
     l.walker_at = r;
     r = align_up(r + static_cast<size_t>(R) * 4);
+    l.wparam = r;
+    r = align_up(r + static_cast<size_t>(Rp) * 8);
     l.fg = r;
     r = align_up(r + static_cast<size_t>(Rp) * 12);
     l.stats = r;
@@ -115,6 +117,8 @@ Layout1 block_layout(int32_t n, int32_t C, int32_t rec_vec, int32_t I, int32_t J
     r = align_up(r + static_cast<size_t>(n));
     l.scalars = r;
     r = align_up(r + pt2d::kScCount * 8);
+    l.counter = r;
+    r = align_up(r + 4);
     l.run_stride = r;
     l.total = o + r * static_cast<size_t>(runs);
     return l;
@@ -149,13 +153,17 @@ struct pt2d_batch {
     std::map<int64_t, Inst> insts;
     int64_t next_id = 1;
     pt2d::BatchRun *d_runs = nullptr;
+    pt2d::BatchItem *d_items = nullptr;               // [max_runs * kMaxSlabs]
     int32_t *d_queue = nullptr;
     int64_t *d_status = nullptr;                      // [max_runs][2]
-    std::vector<std::pair<int64_t, int32_t>> order;  // launch order: (id, run)
+    std::vector<std::pair<int64_t, int32_t>> order;  // run array order: (id, run)
+    int32_t n_items = 0;
+    int glob_sw = 32;                                 // slab width when spins stay in global memory
     int32_t n_runs = 0;
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
     int graph_events = -1, graph_interval = -1, graph_threads = -1;
+    static constexpr int kMaxSlabs = pt2d::kBatchMaxReplicas / 16;
     int64_t launches = 0;
     int last_cuda = 0;
 };
@@ -180,26 +188,43 @@ void drop_graph(pt2d_batch *b) {
     b->graph_events = b->graph_interval = b->graph_threads = -1;
 }
 
+// Slab width of a run: the whole run when its spins fit in the shared memory
+// reserved per CTA, else the widest power of two >= 16 that fits, else the
+// global-memory slab width.
+int32_t slab_width(const pt2d_batch *b, int32_t n, int32_t Rp) {
+    for (int32_t sw = Rp; sw >= 16; sw >>= 1)
+        if (static_cast<int64_t>(n + 1) * sw <= b->smem_state) return sw;
+    return std::min<int32_t>(Rp, b->glob_sw);
+}
+
 int upload_descriptors(pt2d_batch *b) {
     std::vector<std::pair<pt2d::BatchRun, std::pair<int64_t, int32_t>>> tagged;
     for (auto &kv : b->insts)
         for (auto &d : kv.second.desc) {
-            d.use_smem = static_cast<int64_t>(d.n + 1) * d.Rp <= b->smem_state ? 1 : 0;
+            d.sw = slab_width(b, d.n, d.Rp);
+            d.nslab = d.Rp / d.sw;
             tagged.push_back({d, {kv.first, d.run}});
         }
     std::stable_sort(tagged.begin(), tagged.end(),
                      [](const auto &x, const auto &y) { return x.first.work > y.first.work; });
+    if (static_cast<int32_t>(tagged.size()) > b->max_runs) return PT2D_ERR_OOM;
     std::vector<pt2d::BatchRun> all;
+    std::vector<pt2d::BatchItem> items;
     b->order.clear();
     for (const auto &t : tagged) {
+        const int32_t idx = static_cast<int32_t>(all.size());
         all.push_back(t.first);
         b->order.push_back(t.second);
+        for (int32_t k = 0; k < t.first.nslab; ++k) items.push_back({idx, k});
     }
-    if (static_cast<int32_t>(all.size()) > b->max_runs) return PT2D_ERR_OOM;
-    if (!all.empty())
+    if (!all.empty()) {
         BK(b, cudaMemcpyAsync(b->d_runs, all.data(), sizeof(pt2d::BatchRun) * all.size(),
                               cudaMemcpyHostToDevice, b->stream));
+        BK(b, cudaMemcpyAsync(b->d_items, items.data(), sizeof(pt2d::BatchItem) * items.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+    }
     b->n_runs = static_cast<int32_t>(all.size());
+    b->n_items = static_cast<int32_t>(items.size());
     b->dirty = false;
     drop_graph(b);
     return PT2D_OK;
@@ -211,24 +236,31 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
         if (st) return st;
     }
     if (b->n_runs == 0 || events == 0) return PT2D_OK;
-    pt2d::BatchArgs a{b->pool, b->d_runs, b->n_runs, b->d_queue, events, interval, b->smem_state,
-                      b->d_status};
-    const int grid = std::min(b->grid, b->n_runs);
+    pt2d::BatchArgs a{b->pool, b->d_runs, b->d_items, b->n_runs, b->n_items, b->d_queue, interval,
+                      b->smem_state, b->d_status};
+    const int grid = std::min(b->grid, b->n_items);
     BK(b, pt2d::batch_kernel_attributes(b->DC, 2, b->smem_state));
+    // one launch per event: the counter is cleared, then every slab of every run
+    auto enqueue = [&]() -> cudaError_t {
+        for (int32_t e = 0; e < events; ++e) {
+            cudaError_t x = cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream);
+            if (x != cudaSuccess) return x;
+            x = pt2d::launch_batch(a, b->DC, 2, grid, b->threads, b->stream);
+            if (x != cudaSuccess) return x;
+        }
+        return cudaSuccess;
+    };
     if (!b->use_graph) {
-        BK(b, cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream));
-        BK(b, pt2d::launch_batch(a, b->DC, 2, grid, b->threads, b->stream));
+        BK(b, enqueue());
     } else {
         if (!b->graph || b->graph_events != events || b->graph_interval != interval ||
             b->graph_threads != b->threads) {
             drop_graph(b);
             cudaGraph_t g = nullptr;
             BK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream);
-            cudaError_t e2 = pt2d::launch_batch(a, b->DC, 2, grid, b->threads, b->stream);
+            cudaError_t e1 = enqueue();
             cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
             if (e1 != cudaSuccess) return fail(b, e1);
-            if (e2 != cudaSuccess) return fail(b, e2);
             if (e3 != cudaSuccess) return fail(b, e3);
             cudaError_t e4 = cudaGraphInstantiate(&b->graph, g, 0);
             cudaGraphDestroy(g);
@@ -239,7 +271,7 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
         }
         BK(b, cudaGraphLaunch(b->graph, b->stream));
     }
-    b->launches += 1;
+    b->launches += events;
     return PT2D_OK;
 }
 
@@ -307,7 +339,8 @@ int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_
         b->own_stream = true;
     }
     const size_t head = align_up(sizeof(int32_t)) + align_up(sizeof(pt2d::BatchRun) * max_runs) +
-                        align_up(sizeof(int64_t) * 2 * max_runs);
+                        align_up(sizeof(int64_t) * 2 * max_runs) +
+                        align_up(sizeof(pt2d::BatchItem) * max_runs * pt2d_batch::kMaxSlabs);
     if (opt->workspace) {
         if (opt->workspace_bytes < head + 4096 || (reinterpret_cast<uintptr_t>(opt->workspace) & 255)) {
             pt2d_batch_destroy(b);
@@ -328,6 +361,9 @@ int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_
     b->d_runs = reinterpret_cast<pt2d::BatchRun *>(b->pool + align_up(sizeof(int32_t)));
     b->d_status = reinterpret_cast<int64_t *>(b->pool + align_up(sizeof(int32_t)) +
                                               align_up(sizeof(pt2d::BatchRun) * max_runs));
+    b->d_items = reinterpret_cast<pt2d::BatchItem *>(
+        b->pool + align_up(sizeof(int32_t)) + align_up(sizeof(pt2d::BatchRun) * max_runs) +
+        align_up(sizeof(int64_t) * 2 * max_runs));
     b->arena.reset(head, b->pool_bytes - head);
     *out = b;
     return PT2D_OK;
@@ -393,6 +429,8 @@ int pt2d_batch_add(pt2d_batch *b, const pt2d_instance *inst, int32_t I, const fl
         d.beta = static_cast<int64_t>(in.off + l.beta);
         d.P = static_cast<int64_t>(in.off + l.P);
         d.walker_at = static_cast<int64_t>(rb + l.walker_at);
+        d.wparam = static_cast<int64_t>(rb + l.wparam);
+        d.counter = static_cast<int64_t>(rb + l.counter);
         d.fg = static_cast<int64_t>(rb + l.fg);
         d.stats = static_cast<int64_t>(rb + l.stats);
         d.trace = static_cast<int64_t>(rb + l.trace);
@@ -455,20 +493,23 @@ int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, in
                         int32_t *smem_out) {
     if (!b || events < 1 || swap_interval < 1) return PT2D_ERR_INVALID_ARG;
     cudaSetDevice(b->device);
-    const int thread_opts[] = {256, 512, 1024};
+    const int thread_opts[] = {512, 1024};
     const int smem_opts[] = {b->smem_state_max, 0};
+    const int gsw_opts[] = {16, 64};
     float best_ms = -1.0f;
-    int best_t = b->threads, best_s = b->smem_state;
+    int best_t = b->threads, best_s = b->smem_state, best_g = b->glob_sw;
     cudaEvent_t e0, e1;
     BK(b, cudaEventCreate(&e0));
     BK(b, cudaEventCreate(&e1));
     // Every launch shape computes the same trajectories, so the trial launches are
     // ordinary progress of the chains.
     for (int so : smem_opts) {
+        for (int gw : gsw_opts)
         for (int t : thread_opts) {
             b->threads = t;
-            if (b->smem_state != so) {
+            if (b->smem_state != so || b->glob_sw != gw) {
                 b->smem_state = so;
+                b->glob_sw = gw;
                 b->dirty = true;
             }
             int st = launch(b, events, swap_interval);  // first launch per shape: not timed
@@ -484,14 +525,16 @@ int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, in
                 best_ms = ms;
                 best_t = t;
                 best_s = so;
+                best_g = gw;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->threads = best_t;
-    if (b->smem_state != best_s) {
+    if (b->smem_state != best_s || b->glob_sw != best_g) {
         b->smem_state = best_s;
+        b->glob_sw = best_g;
         b->dirty = true;
     }
     if (threads_out) *threads_out = best_t;
