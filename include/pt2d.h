@@ -105,15 +105,17 @@ typedef struct {
     void *workspace;         /* caller-owned device memory, or NULL: library allocates */
     size_t workspace_bytes;  /* size of `workspace` (see pt2d_workspace_size)      */
     int32_t trace_capacity;  /* events kept in the bottom-right trace (default 1024) */
-    int32_t walkers_per_cta; /* sweep tiling: 4..128 (16..128 in shared memory), power of
-                                two; 0 = automatic                                  */
+    int32_t walkers_per_cta; /* sweep tiling: 4..128 (16..128 int8 in shared memory,
+                                8..128 bit-packed), power of two; 0 = automatic      */
     int32_t threads_per_cta; /* multiple of 32, >= walkers_per_cta/4, <= 256 (global
                                 slab) or 1024 (shared slab); 0 = automatic          */
     int32_t device;          /* CUDA device ordinal; -1 = current device            */
     int32_t profile;         /* nonzero: time every kernel launch with CUDA events  */
-    int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 slab in shared
-                                memory (INVALID_ARG if it does not fit)               */
-    int32_t walkers_per_thread; /* shared-memory kernel: 4 or 8; 0 = automatic       */
+    int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 int8 slab in
+                                shared memory, 3 bit-packed slab in shared memory
+                                (2, 3: INVALID_ARG if it does not fit)               */
+    int32_t walkers_per_thread; /* int8 shared-memory kernel: 4 or 8, others: 4;
+                                   0 = automatic                                     */
 } pt2d_options;
 
 typedef struct pt2d_ctx pt2d_ctx;
@@ -177,6 +179,12 @@ int pt2d_sync(pt2d_ctx *ctx);
 /* Number of colours of the context's colouring, and kernel launches queued so far. */
 int pt2d_num_colors(const pt2d_ctx *ctx);
 int64_t pt2d_launch_count(const pt2d_ctx *ctx);
+
+/* Sweep tiling the context chose: out[0] = kernel (1 slab in global memory, 2
+ * int8 slab in shared memory, 3 bit-packed slab in shared memory, 4 generic
+ * degree layout), out[1] = walkers per CTA, out[2] = threads per CTA,
+ * out[3] = walkers per thread.  Host only.  Errors: INVALID_ARG (NULL). */
+int pt2d_tiling(const pt2d_ctx *ctx, int32_t out[4]);
 
 /* Kernel timing of a context created with opt.profile != 0: total device
  * milliseconds and launch count of the sweep kernel (kind 0) or the swap-event

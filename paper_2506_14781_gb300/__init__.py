@@ -105,8 +105,9 @@ class PT2D:
 
     workspace: "library" (the library allocates device memory with cudaMalloc),
     or "torch" (a torch uint8 CUDA tensor owned by this object provides it).
-    sweep_kernel: "auto", "global" (replica slab in global memory) or "smem"
-    (slab held in shared memory for a whole swap interval).
+    sweep_kernel: "auto", "global" (replica slab in global memory), "smem"
+    (int8 slab held in shared memory for a whole swap interval) or "bits"
+    (bit-packed slab in shared memory, for instances whose int8 slab does not fit).
     stream: a torch.cuda.Stream, a raw cudaStream_t (int), or None (default stream).
     """
 
@@ -131,7 +132,7 @@ class PT2D:
         opt.threads_per_cta = int(threads_per_cta)
         opt.device = int(device)
         opt.profile = 1 if profile else 0
-        opt.sweep_kernel = {"auto": 0, "global": 1, "smem": 2}[sweep_kernel]
+        opt.sweep_kernel = {"auto": 0, "global": 1, "smem": 2, "bits": 3}[sweep_kernel]
         opt.walkers_per_thread = int(walkers_per_thread)
         self._stream_obj = stream
         if stream is not None:
@@ -209,6 +210,16 @@ class PT2D:
     @property
     def launch_count(self) -> int:
         return int(_lib.lib().pt2d_launch_count(self._ctx))
+
+    @property
+    def tiling(self) -> dict:
+        """Sweep tiling chosen at creation: kernel, walkers and threads per CTA,
+        walkers per thread."""
+        out = (C.c_int32 * 4)()
+        _lib.check(_lib.lib().pt2d_tiling(self._ctx, out), "pt2d_tiling", self._ctx)
+        kernel = {1: "global", 2: "smem", 3: "bits", 4: "generic"}[out[0]]
+        return dict(kernel=kernel, walkers_per_cta=out[1], threads_per_cta=out[2],
+                    walkers_per_thread=out[3])
 
     def close(self) -> None:
         if getattr(self, "_ctx", None) and self._ctx.value:

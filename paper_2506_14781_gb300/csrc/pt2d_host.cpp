@@ -212,7 +212,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         }
     }
     const int mode = opt ? opt->sweep_kernel : 0;
-    if (mode < 0 || mode > 2) return PT2D_ERR_INVALID_ARG;
+    if (mode < 0 || mode > 3) return PT2D_ERR_INVALID_ARG;
     const bool specialised = DL == 2 && (DC == 3 || DC == 4 || DC == 6);
     const int64_t walkers = static_cast<int64_t>(runs) * pp.Rp;
     auto fits = [&](int sw) {
@@ -234,8 +234,37 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
             }
         }
     }
+    // bit-packed shared-memory slab when the int8 one does not fit (or when forced)
+    int bw = 0;
+    auto fits_bits = [&](int cand) {
+        return pt2d::bits_sweep_bytes(n, cand) + pt2d::kSweepStaticSmem <= static_cast<size_t>(smem_max);
+    };
+    if (specialised && (mode == 3 || (mode == 0 && sw == 0))) {
+        sw = 0;
+        if (req_w) {
+            if (req_w >= 8 && fits_bits(req_w)) bw = req_w;
+        } else {
+            for (int cand = 128; cand >= 8; cand /= 2) {
+                if (!fits_bits(cand)) continue;
+                bw = cand;
+                if ((walkers + cand - 1) / cand >= sms) break;
+            }
+        }
+        if (mode == 3 && bw == 0) return PT2D_ERR_INVALID_ARG;
+    }
     if (mode == 2 && sw == 0) return PT2D_ERR_INVALID_ARG;
     int ql, threads, wpt = 4;
+    if (bw) {
+        if (opt && opt->walkers_per_thread != 0 && opt->walkers_per_thread != 4)
+            return PT2D_ERR_INVALID_ARG;
+        ql = bw / 4;
+        int32_t widest = 0;
+        for (int32_t c = 0; c < C; ++c) widest = std::max(widest, pp.cofs[c + 1] - pp.cofs[c]);
+        const int64_t want = (static_cast<int64_t>(widest) * ql + 31) / 32 * 32;
+        threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta
+                                                    : static_cast<int>(std::min<int64_t>(1024, want));
+        if (threads < 32 || threads > 1024 || threads % 32 || threads < ql) return PT2D_ERR_INVALID_ARG;
+    } else
     if (sw) {
         ql = sw / 4;
         const int req_t = opt ? opt->walkers_per_thread : 0;
@@ -265,13 +294,16 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.tiling.lanes_per_spin = ql;
     pp.tiling.threads = threads;
     pp.tiling.smem = sw != 0;
+    pp.tiling.bits = bw != 0;
     pp.tiling.walkers_per_thread = wpt;
-    if (sw) {  // neighbour references become byte offsets into the shared-memory slab
+    // neighbour references become byte offsets into the shared-memory slab
+    const int scale = sw ? sw : (bw ? bw / 8 : 1);
+    if (scale > 1) {
         const size_t ri2 = static_cast<size_t>(pp.rec_vec) * 4;
         for (int32_t p = 0; p < n; ++p)
-            for (int32_t k = 0; k < DC + DL; ++k) pp.rec[static_cast<size_t>(p) * ri2 + k] *= sw;
+            for (int32_t k = 0; k < DC + DL; ++k) pp.rec[static_cast<size_t>(p) * ri2 + k] *= scale;
     }
-    pp.pad_ref = sw ? n * sw : n;
+    pp.pad_ref = n * scale;
     const int64_t slab = 4LL * ql;
     pp.Wc = (walkers + slab - 1) / slab * slab;
     return PT2D_OK;
@@ -545,6 +577,17 @@ int pt2d_kernel_time(pt2d_ctx *c, int32_t kind, double *ms, int64_t *launches) {
 
 int pt2d_cuda_error(const pt2d_ctx *c) { return c ? c->last_cuda : 0; }
 int pt2d_num_colors(const pt2d_ctx *c) { return c ? c->pp.C : 0; }
+
+int pt2d_tiling(const pt2d_ctx *c, int32_t out[4]) {
+    if (!c || !out) return PT2D_ERR_INVALID_ARG;
+    const pt2d::SweepTiling &t = c->pp.tiling;
+    const bool specialised = c->pp.DL == 2 && (c->pp.DC == 3 || c->pp.DC == 4 || c->pp.DC == 6);
+    out[0] = t.bits ? 3 : t.smem ? 2 : specialised ? 1 : 4;
+    out[1] = 4 * t.lanes_per_spin;
+    out[2] = t.threads;
+    out[3] = t.walkers_per_thread;
+    return PT2D_OK;
+}
 int64_t pt2d_launch_count(const pt2d_ctx *c) { return c ? c->launches : 0; }
 
 int pt2d_run(pt2d_ctx *c, int64_t sweeps, int32_t interval, uint64_t seed) {

@@ -65,10 +65,13 @@ struct SweepTiling {
     int threads;         // threads per CTA
     bool smem;           // slab in shared memory (k_sweep_smem) or global (k_sweep_global)
     int walkers_per_thread;  // 4, or 8 in the shared-memory kernel
+    bool bits;           // slab bit-packed in shared memory (k_sweep_bits)
 };
 
 // Dynamic shared memory of k_sweep_smem for n spins and a slab of W walkers.
 size_t smem_sweep_bytes(int32_t n, int walkers_per_cta);
+// Dynamic shared memory of k_sweep_bits (slab of bits plus the nibble table).
+size_t bits_sweep_bytes(int32_t n, int walkers_per_cta);
 constexpr size_t kSweepStaticSmem = 2048;  // epilogue reduction arrays and slack
 
 cudaError_t launch_init(const Layout &L, const RunState &rs, const Walkers &wk, uint64_t seed,

@@ -171,6 +171,93 @@ __global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
     energies<DC, DL, NQ>(L, wk, fetch_q, own_q, lane_off, grp, G, SW, col0);
 }
 
+// Spin bits of four int8 spins: bit k is 1 iff byte k holds -1 (0xFF); the
+// multiply gathers the four sign bits (no two product bits share a position).
+__device__ __forceinline__ uint32_t bits_of_word(uint32_t w) {
+    const uint32_t m = (w >> 7) & 0x01010101u;
+    return ((m * 0x00204081u) >> 21) & 0xFu;
+}
+
+// Sweep block with the slab bit-packed in shared memory: (n + 1) rows x SW/8
+// bytes, bit k of a byte = spin of one walker (1 = -1), for instances whose
+// int8 slab does not fit.  A thread owns one nibble (4 walkers); a 16-entry
+// table expands a nibble to four int8 spins so the field and decision code is
+// the int8 kernel's; the two nibbles of a byte are merged with one shuffle.
+// Missing copy links (a bit cannot hold 0) are skipped by predicate.
+template <int DC, int DL>
+__global__ void __launch_bounds__(1024, 1) k_sweep_bits(Layout L, Walkers wk, int sw_shift,
+                                                        int32_t quads_per_run, RoundKeys rk,
+                                                        uint32_t sweep0, int32_t nsweeps) {
+    extern __shared__ __align__(16) uint8_t smb[];
+    const int SW = 1 << sw_shift;  // walkers per CTA, >= 8
+    const int B = SW >> 3;         // bytes per spin row
+    const int QL = SW >> 2;        // threads per spin row (two per byte)
+    const int lane_q = threadIdx.x & (QL - 1);
+    const int grp = threadIdx.x >> (sw_shift - 2);
+    const int G = blockDim.x >> (sw_shift - 2);
+    const int byte_lane = lane_q >> 1;
+    const int nib_shift = (lane_q & 1) * 4;
+    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * SW;
+    const int64_t quad = col0 / 4 + lane_q;
+    const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
+    const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
+    const uint32_t c3 = (run << 4) | kTagSweep;
+    const Quad q = load_quad(wk, col0 + 4 * lane_q);
+    const KeysConst keys{rk};
+    const int n = L.n;
+    uint8_t *bits = smb;
+    uint32_t *lut = reinterpret_cast<uint32_t *>(smb + ((static_cast<int64_t>(n + 1) * B + 15) & ~15LL));
+    if (threadIdx.x < 16) {
+        uint32_t w = 0;
+        for (int k = 0; k < 4; ++k) w |= ((threadIdx.x >> k) & 1u ? 0xFFu : 0x01u) << (8 * k);
+        lut[threadIdx.x] = w;
+    }
+    // load: 8 int8 spins of global memory -> one byte of bits
+    const int64_t nbytes = static_cast<int64_t>(n + 1) * B;
+    for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {
+        const int64_t row = i / B;
+        const int b = static_cast<int>(i - row * B);
+        const uint2 v = *reinterpret_cast<const uint2 *>(L.S + row * L.Wc + col0 + 8 * b);
+        bits[i] = static_cast<uint8_t>(bits_of_word(v.x) | (bits_of_word(v.y) << 4));
+    }
+    __syncthreads();
+
+    // neighbour references in the records are byte offsets row * B
+    auto fetch = [&](int off) -> uint32_t { return lut[(bits[off + byte_lane] >> nib_shift) & 0xF]; };
+    const int pad = L.pad_ref;
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
+        for (int c = 0; c < L.C; ++c) {
+            const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                Rec<DC, DL> rc;
+                rc.load(L.rec, pos);
+                uint32_t x[DC], y[DL];
+#pragma unroll
+                for (int k = 0; k < DC; ++k) x[k] = fetch(rc.nb(k));
+#pragma unroll
+                for (int l = 0; l < DL; ++l) y[l] = rc.lk(l) != pad ? fetch(rc.lk(l)) : 0u;
+                const uint4 r = keys(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3));
+                const uint32_t nib = bits_of_word(decide4<DC, DL>(rc, q, x, y, r));
+                const uint32_t other = __shfl_xor_sync(0x3u << (threadIdx.x & 30), nib, 1);
+                if ((lane_q & 1) == 0) bits[pos * B + byte_lane] = static_cast<uint8_t>(nib | (other << 4));
+            }
+            __syncthreads();
+        }
+    }
+    // write back rows 0..n-1 as int8 spins
+    const int64_t nb_out = static_cast<int64_t>(n) * B;
+    for (int64_t i = threadIdx.x; i < nb_out; i += blockDim.x) {
+        const int64_t row = i / B;
+        const int b = static_cast<int>(i - row * B);
+        const uint32_t byte = bits[i];
+        *reinterpret_cast<uint2 *>(L.S + row * L.Wc + col0 + 8 * b) = make_uint2(lut[byte & 0xF], lut[byte >> 4]);
+    }
+    auto fetch_q = [&](int off, int) -> uint32_t { return fetch(off); };
+    auto own_q = [&](int p, int) -> uint32_t { return fetch(p * B); };
+    energies<DC, DL, 1>(L, wk, fetch_q, own_q, 4 * lane_q, grp, G, SW, col0);
+}
+
 // Sweep block with the slab in global memory.
 template <int DC, int DL>
 __global__ void __launch_bounds__(256) k_sweep_global(Layout L, Walkers wk, int ql_shift,
@@ -457,6 +544,22 @@ cudaError_t launch_smem(const Layout &L, const Walkers &wk, const SweepTiling &t
 }
 
 template <int DC, int DL>
+cudaError_t launch_bits_variant(const Layout &L, const Walkers &wk, const SweepTiling &tl,
+                                int32_t qpr, const RoundKeys &rk, uint32_t sweep0,
+                                int32_t nsweeps, cudaStream_t st) {
+    int shift = 0;
+    while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
+    const size_t smem = bits_sweep_bytes(L.n, 1 << shift);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_bits<DC, DL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
+    k_sweep_bits<DC, DL><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
+    return cudaGetLastError();
+}
+
+template <int DC, int DL>
 cudaError_t launch_global_variant(const Layout &L, const Walkers &wk, const SweepTiling &tl,
                                   int32_t qpr, const RoundKeys &rk, uint32_t sweep0,
                                   int32_t nsweeps, cudaStream_t st) {
@@ -471,6 +574,10 @@ cudaError_t launch_global_variant(const Layout &L, const Walkers &wk, const Swee
 
 size_t smem_sweep_bytes(int32_t n, int walkers_per_cta) {
     return static_cast<size_t>(n + 1) * static_cast<size_t>(walkers_per_cta);
+}
+
+size_t bits_sweep_bytes(int32_t n, int walkers_per_cta) {
+    return ((static_cast<size_t>(n + 1) * (walkers_per_cta / 8) + 15) & ~static_cast<size_t>(15)) + 64;
 }
 
 // ---- launchers --------------------------------------------------------------
@@ -490,6 +597,12 @@ cudaError_t launch_sweeps(const Layout &L, const Walkers &wk, const SweepTiling 
                           int32_t quads_per_run, uint64_t seed, uint32_t sweep0, int32_t nsweeps,
                           cudaStream_t st) {
     const RoundKeys rk = round_keys(seed);
+    if (tl.bits) {
+        if (L.DC == 3 && L.DL == 2) return launch_bits_variant<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        if (L.DC == 4 && L.DL == 2) return launch_bits_variant<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        if (L.DC == 6 && L.DL == 2) return launch_bits_variant<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        return cudaErrorInvalidValue;
+    }
     if (tl.smem) {
         if (L.DC == 3 && L.DL == 2) return launch_smem<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
         if (L.DC == 4 && L.DL == 2) return launch_smem<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);

@@ -159,7 +159,8 @@ def test_tiny_config_bit_exact_full_length(pt, tiny_config):
 @pytest.mark.parametrize("kernel,wpc,threads,wpt", [
     ("global", 4, 32, 0), ("global", 16, 64, 0), ("global", 32, 256, 0), ("global", 128, 256, 0),
     ("smem", 16, 32, 4), ("smem", 32, 64, 4), ("smem", 64, 1024, 4), ("smem", 128, 128, 4),
-    ("smem", 16, 64, 8), ("smem", 64, 512, 8), ("smem", 128, 32, 8), ("auto", 0, 0, 0)])
+    ("smem", 16, 64, 8), ("smem", 64, 512, 8), ("smem", 128, 32, 8), ("bits", 8, 32, 0),
+    ("bits", 16, 64, 0), ("bits", 64, 1024, 0), ("bits", 128, 96, 0), ("auto", 0, 0, 0)])
 def test_ragged_tiles_and_resume(pt, kernel, wpc, threads, wpt):
     inst = synth.wishart_planted(30, 0.5, 21)
     beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
@@ -168,10 +169,12 @@ def test_ragged_tiles_and_resume(pt, kernel, wpc, threads, wpt):
     ctx, orc = both(pt, inst, ("max_edges", 3), beta, P, 7, 0xDEADBEEF12345,
                     [(35, 7), (20, 7), (7, 7)], target=inst.E_planted, wpc=wpc, threads=threads,
                     kernel=kernel, wpt=wpt)
+    if kernel != "auto":
+        assert ctx.tiling["kernel"] == kernel and ctx.tiling["walkers_per_cta"] == wpc
     assert_same(pt, ctx, orc)
 
 
-@pytest.mark.parametrize("kernel,wpt", [("global", 0), ("smem", 4), ("smem", 8)])
+@pytest.mark.parametrize("kernel,wpt", [("global", 0), ("smem", 4), ("smem", 8), ("bits", 0)])
 def test_degree_layouts_both_kernels(pt, kernel, wpt):
     """Specialised neighbour layouts DC = 4 and 6 (max-degree and fixed-copy
     sparsifications), on both sweep kernels."""
@@ -180,7 +183,7 @@ def test_degree_layouts_both_kernels(pt, kernel, wpt):
         beta = synth.beta_ladder(4, 0.2, 2.0, inst.scale)
         P = synth.penalty_ladder(4, 0.5, 4.0, 32767)
         ctx, orc = both(pt, inst, rule, beta, P, 3, 77, [(24, 3)], kernel=kernel,
-                        wpc=16 if kernel == "smem" else 0, wpt=wpt)
+                        wpc={"smem": 16, "bits": 8}.get(kernel, 0), wpt=wpt)
         assert_same(pt, ctx, orc)
 
 
@@ -328,6 +331,8 @@ def test_n800_full_size_sampled_walkers(pt):
     seed = 4242
     runs = 16
     ctx = pt.PT2D(phys_p, beta, P, runs, trace_capacity=4)
+    # the automatic tiling holds this instance bit-packed in shared memory, 8 walkers a CTA
+    assert ctx.tiling["kernel"] == "bits" and ctx.tiling["walkers_per_cta"] == 8
     ctx.run(2, 2, seed)
     oinst = oracle.OracleInstance(oracle.sparsify(inst.Jq, "max_edges", 3))
     f_gpu = ctx.read(pt.F)
