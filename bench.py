@@ -403,9 +403,8 @@ def run_batched(args):
     done_events = 0
     if args.autotune:
         tuned = batch.autotune(1, interval)
-        done_events += 12
     batch.run(1, interval)
-    done_events += 1
+    done_events = int(batch.read(ids[0], pt.COUNTERS)[1])  # trial launches advance the chains
     ev0.record(stream)
     batch.run(E, interval)
     ev1.record(stream)
@@ -471,7 +470,7 @@ def run_batched(args):
                                f"swap every 50 sweeps", "physical_spins_total": int(spins),
                    "instance_generation_s": gen_s},
         "batched": {"seconds": t_batched, "updates_per_s": upd_per_event * E / t_batched,
-                    "launches": 1, "autotuned_threads_smem": tuned},
+                    "launches": 1, "shape": batch.shape, "autotuned": tuned is not None},
         "plain": plain,
         "speedup_batched_over_plain": (plain["seconds"] / t_batched) if plain else None,
         "tts": tts,

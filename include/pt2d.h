@@ -227,8 +227,10 @@ typedef struct pt2d_batch pt2d_batch;
  * size then includes the batch's bookkeeping); max_coupling_degree: largest
  * number of coupling neighbours of any spin that will be added (<= 6; links
  * <= 2 per spin); max_runs: most runs alive at once.  opt: stream, workspace,
- * trace_capacity, threads_per_cta (128..1024), sweep_kernel (1 = keep spins in
- * global memory), device.  Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED. */
+ * trace_capacity, and the initial launch shape (pt2d_batch_shape below):
+ * threads_per_cta (0 = 1024), sweep_kernel (= storage), walkers_per_cta
+ * (= global_width, 0 = 32); balance starts at 2.  device.
+ * Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED. */
 int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_degree,
                       int32_t max_runs, const pt2d_options *opt);
 
@@ -253,13 +255,38 @@ int pt2d_batch_remove(pt2d_batch *b, int64_t id);
  * OOM (more runs than max_runs), CUDA. */
 int pt2d_batch_run(pt2d_batch *b, int32_t events, int32_t swap_interval);
 
-/* Time every launch shape (threads per CTA 512 / 1024; slabs held in shared
- * memory where they fit, or all spins in global memory; 16 or 64 walkers per
- * global-memory slab) on two launches of `events` events each and keep the
- * fastest.  The 16 trial launches advance the chains like pt2d_batch_run
- * (every shape computes the same trajectories).  Outputs may be NULL. */
+/* Launch shape of a batch.  Every shape computes the same trajectories.
+ *   threads_per_cta  128..1024, multiple of 32
+ *   storage          where a run's slab of spins lives during an event: 0 =
+ *                    int8 in shared memory where it fits, else bit-packed in
+ *                    shared memory where that fits, else int8 in global
+ *                    memory; 1 = always global; 2 = no bit-packed slabs; 3 = no
+ *                    int8 shared-memory slabs
+ *   global_width     walkers per slab of runs kept in global memory (16..128,
+ *                    power of two)
+ *   balance          0, or k >= 1: a run is split into slabs of at most
+ *                    (total spins x replicas) / (k x CTAs) spin-walkers each,
+ *                    down to the narrowest slab its storage allows, so that
+ *                    large runs do not leave other CTAs idle at the event's end */
+typedef struct pt2d_batch_shape {
+    int32_t threads_per_cta;
+    int32_t storage;
+    int32_t global_width;
+    int32_t balance;
+} pt2d_batch_shape;
+
+/* Read / set the launch shape (host only; applies from the next launch).
+ * Errors: INVALID_ARG. */
+int pt2d_batch_get_shape(const pt2d_batch *b, pt2d_batch_shape *shape);
+int pt2d_batch_set_shape(pt2d_batch *b, const pt2d_batch_shape *shape);
+
+/* Time candidate launch shapes (storage 0 or 1 x balance 0, 2 or 8 at 1024
+ * threads, then the best of those at 512 threads) on two launches of `events`
+ * events each and keep the fastest, returned in *chosen (may be NULL).  The
+ * trial launches advance the chains like pt2d_batch_run.  Errors as
+ * pt2d_batch_run. */
 int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval,
-                        int32_t *threads_per_cta, int32_t *smem_state_bytes);
+                        pt2d_batch_shape *chosen);
 
 /* Copy array `what` (the PT2D_* arrays of pt2d_read, for this problem's runs)
  * to host memory; synchronises.  Errors: INVALID_ARG, STATE, CUDA. */

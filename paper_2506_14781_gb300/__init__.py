@@ -263,13 +263,19 @@ class Batch:
 
     def __init__(self, pool_bytes: int, max_coupling_degree: int = 3, max_runs: int = 4096, *,
                  stream=None, trace_capacity: int = 1024, threads_per_cta: int = 0,
-                 spins_in_global: bool = False, device: int = -1):
+                 spins_in_global: bool = False, sweep_kernel: str = "auto",
+                 walkers_per_cta: int = 0, device: int = -1):
+        """sweep_kernel: where a run's spins live during an event -- "auto" (int8
+        in shared memory, else bit-packed in shared memory, else global memory),
+        "global", "smem" (no bit-packed slabs) or "bits" (no int8 shared-memory
+        slabs); spins_in_global=True is "global"."""
         L = _lib.lib()
         opt = _lib.Options()
         L.pt2d_default_options(C.byref(opt))
         opt.trace_capacity = int(trace_capacity)
         opt.threads_per_cta = int(threads_per_cta)
-        opt.sweep_kernel = 1 if spins_in_global else 0
+        opt.sweep_kernel = 1 if spins_in_global else {"auto": 0, "global": 1, "smem": 2, "bits": 3}[sweep_kernel]
+        opt.walkers_per_cta = int(walkers_per_cta)
         opt.device = int(device)
         self._stream_obj = stream
         if stream is not None:
@@ -309,14 +315,38 @@ class Batch:
         if st != 0:
             raise Pt2dError(st, "pt2d_batch_run", _lib.lib().pt2d_batch_cuda_error(self._b))
 
-    def autotune(self, events: int, swap_interval: int):
-        t = C.c_int32()
-        sm = C.c_int32()
-        st = _lib.lib().pt2d_batch_autotune(self._b, int(events), int(swap_interval), C.byref(t),
-                                            C.byref(sm))
+    _STORAGE = {"auto": 0, "global": 1, "smem": 2, "bits": 3}
+
+    @staticmethod
+    def _shape_dict(sh) -> dict:
+        names = {v: k for k, v in Batch._STORAGE.items()}
+        return dict(threads_per_cta=sh.threads_per_cta, storage=names[sh.storage],
+                    global_width=sh.global_width, balance=sh.balance)
+
+    @property
+    def shape(self) -> dict:
+        """Launch shape (pt2d_batch_shape): threads_per_cta, storage ("auto",
+        "global", "smem", "bits"), global_width, balance."""
+        sh = _lib.BatchShape()
+        _lib.check(_lib.lib().pt2d_batch_get_shape(self._b, C.byref(sh)), "pt2d_batch_get_shape")
+        return self._shape_dict(sh)
+
+    @shape.setter
+    def shape(self, value: dict) -> None:
+        cur = self.shape
+        cur.update(value)
+        sh = _lib.BatchShape(int(cur["threads_per_cta"]), self._STORAGE[cur["storage"]],
+                             int(cur["global_width"]), int(cur["balance"]))
+        _lib.check(_lib.lib().pt2d_batch_set_shape(self._b, C.byref(sh)), "pt2d_batch_set_shape")
+
+    def autotune(self, events: int, swap_interval: int) -> dict:
+        """Time candidate launch shapes (each trial advances the chains) and keep
+        the fastest; returns it."""
+        sh = _lib.BatchShape()
+        st = _lib.lib().pt2d_batch_autotune(self._b, int(events), int(swap_interval), C.byref(sh))
         if st != 0:
             raise Pt2dError(st, "pt2d_batch_autotune", _lib.lib().pt2d_batch_cuda_error(self._b))
-        return t.value, sm.value
+        return self._shape_dict(sh)
 
     def read(self, bid: int, what: int) -> np.ndarray:
         runs, R, n = self._meta[bid]
@@ -355,12 +385,14 @@ class Server:
 
     def __init__(self, pool_bytes: int, max_coupling_degree: int = 3, max_requests: int = 1024,
                  swap_interval: int = 50, events_per_step: int = 10, *, stream=None,
-                 threads_per_cta: int = 0, spins_in_global: bool = True, device: int = -1):
+                 threads_per_cta: int = 0, spins_in_global: bool = False,
+                 sweep_kernel: str = "auto", device: int = -1):
+        """sweep_kernel / spins_in_global: slab storage, as for Batch."""
         L = _lib.lib()
         opt = _lib.Options()
         L.pt2d_default_options(C.byref(opt))
         opt.threads_per_cta = int(threads_per_cta)
-        opt.sweep_kernel = 1 if spins_in_global else 0
+        opt.sweep_kernel = 1 if spins_in_global else {"auto": 0, "global": 1, "smem": 2, "bits": 3}[sweep_kernel]
         opt.device = int(device)
         self._stream_obj = stream
         if stream is not None:

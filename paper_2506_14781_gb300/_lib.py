@@ -33,6 +33,7 @@ EXPORTS = [
     "pt2d_diag_philox", "pt2d_diag_pt_exp", "pt2d_diag_heatbath", "pt2d_diag_swap_accept",
     "pt2d_kernel_time", "pt2d_run_noalloc", "pt2d_batch_create", "pt2d_batch_instance_bytes",
     "pt2d_batch_add", "pt2d_batch_remove", "pt2d_batch_run", "pt2d_batch_autotune",
+    "pt2d_batch_get_shape", "pt2d_batch_set_shape",
     "pt2d_batch_read", "pt2d_batch_array_bytes", "pt2d_batch_sync", "pt2d_batch_free_bytes",
     "pt2d_batch_launch_count", "pt2d_batch_cuda_error", "pt2d_batch_destroy", "pt2d_batch_poll",
     "pt2d_server_create", "pt2d_server_submit", "pt2d_server_step", "pt2d_server_status",
@@ -65,6 +66,15 @@ class Options(C.Structure):
         ("profile", C.c_int32),
         ("sweep_kernel", C.c_int32),
         ("walkers_per_thread", C.c_int32),
+    ]
+
+
+class BatchShape(C.Structure):
+    _fields_ = [
+        ("threads_per_cta", C.c_int32),
+        ("storage", C.c_int32),
+        ("global_width", C.c_int32),
+        ("balance", C.c_int32),
     ]
 
 
@@ -142,7 +152,9 @@ def lib():
         L.pt2d_batch_add.argtypes = [vp, vp, i32, vp, i32, vp, i32, C.c_uint64, vp, C.POINTER(i64)]
         L.pt2d_batch_remove.argtypes = [vp, i64]
         L.pt2d_batch_run.argtypes = [vp, i32, i32]
-        L.pt2d_batch_autotune.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.pt2d_batch_autotune.argtypes = [vp, i32, i32, C.POINTER(BatchShape)]
+        L.pt2d_batch_get_shape.argtypes = [vp, C.POINTER(BatchShape)]
+        L.pt2d_batch_set_shape.argtypes = [vp, C.POINTER(BatchShape)]
         L.pt2d_batch_read.argtypes = [vp, i64, i32, vp, sz]
         L.pt2d_batch_array_bytes.argtypes = [vp, i64, i32]
         L.pt2d_batch_array_bytes.restype = sz

@@ -120,8 +120,101 @@ __device__ void run_swap(const BatchArgs &a, const BatchRun &d, int run_index, u
     }
 }
 
+// The sweep block of one event for one slab (colour classes separated by
+// __syncthreads).  fetch(row) / fetch_link(row) give the quad's spin word of a
+// neighbour / copy-link row, store(pos, word) writes the new word.
+template <int DC, int DL, typename Fetch, typename FetchLink, typename Store>
+__device__ __forceinline__ void slab_sweeps(const BatchArgs &a, const BatchRun &d, const int4 *rec,
+                                            const int32_t *cofs, const Quad &q, Fetch fetch,
+                                            FetchLink fetch_link, Store store, int grp, int G,
+                                            uint32_t lq, int64_t sweeps_done) {
+    const KeysBase keys{d.k0, d.k1};
+    const uint32_t c3 = (static_cast<uint32_t>(d.run) << 4) | kTagSweep;
+    for (int t = 0; t < a.interval; ++t) {
+        const uint32_t sweep = static_cast<uint32_t>(sweeps_done + t);
+        for (int c = 0; c < d.C; ++c) {
+            const int beg = __ldg(cofs + c), end = __ldg(cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                Rec<DC, DL> rc;
+                rc.load(rec, pos);
+                uint32_t x[DC], y[DL];
+#pragma unroll
+                for (int k = 0; k < DC; ++k) x[k] = fetch(rc.nb(k));
+#pragma unroll
+                for (int l = 0; l < DL; ++l) y[l] = fetch_link(rc.lk(l));
+                const uint4 r = keys(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3));
+                store(pos, decide4<DC, DL>(rc, q, x, y, r));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// f and g of the final sweep for the slab's walkers (Eq. 1), accumulated into
+// s_F / s_G (shared, zeroed by the caller) at the thread's four walkers.
+template <int DC, int DL, typename Fetch>
+__device__ __forceinline__ void slab_energies(const BatchRun &d, const int4 *rec, Fetch fetch, int grp,
+                                              int G, int lane_off, long long *s_F, int *s_G) {
+    const int n = d.n;
+    long long F0 = 0, F1 = 0, F2 = 0, F3 = 0;
+    int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+    for (int pos = grp; pos < n; pos += G) {
+        Rec<DC, DL> rc;
+        rc.load(rec, pos);
+        const uint32_t xs = fetch(pos);
+        const int h4 = 2 * rc.h2();
+        int c0 = h4, c1 = h4, c2 = h4, cc = h4;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) {
+            const uint32_t x = fetch(rc.nb(k));
+            const int j2 = rc.j2(k);
+            c0 += j2 * sbyte<0>(x);
+            c1 += j2 * sbyte<1>(x);
+            c2 += j2 * sbyte<2>(x);
+            cc += j2 * sbyte<3>(x);
+        }
+        F0 += static_cast<long long>(sbyte<0>(xs)) * c0;
+        F1 += static_cast<long long>(sbyte<1>(xs)) * c1;
+        F2 += static_cast<long long>(sbyte<2>(xs)) * c2;
+        F3 += static_cast<long long>(sbyte<3>(xs)) * cc;
+#pragma unroll
+        for (int l = 0; l < DL; ++l) {
+            if (rc.lk(l) == n) continue;  // padding link
+            const uint32_t y = fetch(rc.lk(l));
+            g0 += sbyte<0>(xs) != sbyte<0>(y);
+            g1 += sbyte<1>(xs) != sbyte<1>(y);
+            g2 += sbyte<2>(xs) != sbyte<2>(y);
+            g3 += sbyte<3>(xs) != sbyte<3>(y);
+        }
+    }
+    unsigned long long *uf = reinterpret_cast<unsigned long long *>(s_F);
+    atomicAdd(uf + lane_off + 0, static_cast<unsigned long long>(F0));
+    atomicAdd(uf + lane_off + 1, static_cast<unsigned long long>(F1));
+    atomicAdd(uf + lane_off + 2, static_cast<unsigned long long>(F2));
+    atomicAdd(uf + lane_off + 3, static_cast<unsigned long long>(F3));
+    atomicAdd(s_G + lane_off + 0, g0);
+    atomicAdd(s_G + lane_off + 1, g1);
+    atomicAdd(s_G + lane_off + 2, g2);
+    atomicAdd(s_G + lane_off + 3, g3);
+}
+
+// Initial spin word of one quad at one position (Algorithm 1 input S0, the
+// init stream of the plain kernels).
+template <int DC, int DL>
+__device__ __forceinline__ uint32_t init_word(const BatchRun &d, const int4 *rec, int pos, uint32_t lq) {
+    const uint32_t pid = static_cast<uint32_t>(
+        reinterpret_cast<const int *>(rec)[static_cast<int64_t>(pos) * d.rec_vec * 4 + DC + DL]);
+    const uint4 r = philox4x32_10(make_uint4(pid, 0u, lq, (static_cast<uint32_t>(d.run) << 4) | kTagInit),
+                                  d.k0, d.k1);
+    return pack_signs(r.x < 0x80000000u ? -1.0f : 1.0f, r.y < 0x80000000u ? -1.0f : 1.0f,
+                      r.z < 0x80000000u ? -1.0f : 1.0f, r.w < 0x80000000u ? -1.0f : 1.0f);
+}
+
 // One event of one slab: sweeps, f and g, and the run's swap when this slab is
-// the last of its run to finish.
+// the last of its run to finish.  The slab's spins are int8 in global memory
+// (mode 0), int8 in shared memory (mode 1) or bit-packed in shared memory
+// (mode 2: one bit per walker, a thread owns a nibble, a 16-entry table
+// expands it to int8 spins, the two nibbles of a byte are merged by a shuffle).
 template <int DC, int DL>
 __device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm) {
     const BatchRun d = a.runs[it.run];
@@ -134,18 +227,13 @@ __device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm)
     const int G = blockDim.x / QL;
     const int col0 = it.slab * SW;                 // first walker of the slab
     const int lane_off = 4 * lane_q;               // within the slab
-    const bool smem = static_cast<int64_t>(n + 1) * SW <= a.smem_state;
-    const int64_t stride = smem ? SW : Rp;         // row stride of the spins the slab works on
     int8_t *S_g = reinterpret_cast<int8_t *>(pool + d.state);
-    int8_t *S = smem ? reinterpret_cast<int8_t *>(dsm) : S_g + col0;
     const int4 *rec = reinterpret_cast<const int4 *>(pool + d.rec);
     const int32_t *cofs = reinterpret_cast<const int32_t *>(pool + d.cofs);
     const int64_t *sc = reinterpret_cast<const int64_t *>(pool + d.scalars);
     const bool inited = sc[kScInited] != 0;
     const int64_t sweeps_done = sc[kScSweeps];
-    const uint32_t run = static_cast<uint32_t>(d.run);
-    const uint32_t k0 = d.k0, k1 = d.k1;
-    const int pid_at = DC + DL;
+    const uint32_t lq = static_cast<uint32_t>((col0 >> 2) + lane_q);
 
     // this thread's four walkers: beta and P of their current slots
     Quad q;
@@ -167,112 +255,103 @@ __device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm)
         q = Quad{b[0], b[1], b[2], b[3], b[0] * kNegL2E, b[1] * kNegL2E, b[2] * kNegL2E,
                  b[3] * kNegL2E, p[0], p[1], p[2], p[3]};
     }
-    if (!inited) {
-        // initial state S0 of the slab's walkers from the init stream
-        const int64_t total = static_cast<int64_t>(n) * QL;
-        for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-            const int pos = static_cast<int>(e / QL);
-            const int qq = static_cast<int>(e - static_cast<int64_t>(pos) * QL);
-            const uint32_t pid = static_cast<uint32_t>(
-                reinterpret_cast<const int *>(rec)[static_cast<int64_t>(pos) * d.rec_vec * 4 + pid_at]);
-            const uint32_t lq = static_cast<uint32_t>((col0 >> 2) + qq);
-            const uint4 r = philox4x32_10(make_uint4(pid, 0u, lq, (run << 4) | kTagInit), k0, k1);
-            *reinterpret_cast<uint32_t *>(S + pos * stride + 4 * qq) =
-                pack_signs(r.x < 0x80000000u ? -1.0f : 1.0f, r.y < 0x80000000u ? -1.0f : 1.0f,
-                           r.z < 0x80000000u ? -1.0f : 1.0f, r.w < 0x80000000u ? -1.0f : 1.0f);
-        }
-        for (int i = threadIdx.x; i < SW; i += blockDim.x) S[n * stride + i] = 0;
-    } else if (smem) {
-        const int vec = SW >> 4;
-        const int64_t nvec = static_cast<int64_t>(n + 1) * vec;
-        for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
-            const int64_t row = i / vec;
-            const int part = static_cast<int>(i - row * vec);
-            reinterpret_cast<uint4 *>(S)[i] =
-                *reinterpret_cast<const uint4 *>(S_g + row * Rp + col0 + 16 * part);
-        }
-    }
-    __syncthreads();
-
-    auto fetch = [&](int row) -> uint32_t {
-        return *reinterpret_cast<const uint32_t *>(S + row * stride + lane_off);
-    };
-    const KeysBase keys{k0, k1};
-    const uint32_t c3 = (run << 4) | kTagSweep;
-    const uint32_t lq = static_cast<uint32_t>((col0 >> 2) + lane_q);
-    for (int t = 0; t < a.interval; ++t) {
-        const uint32_t sweep = static_cast<uint32_t>(sweeps_done + t);
-        for (int c = 0; c < d.C; ++c) {
-            const int beg = __ldg(cofs + c), end = __ldg(cofs + c + 1);
-            for (int pos = beg + grp; pos < end; pos += G) {
-                Rec<DC, DL> rc;
-                rc.load(rec, pos);
-                const uint32_t w = update4<DC, DL>(rc, q, fetch, sweep, lq, c3, keys);
-                *reinterpret_cast<uint32_t *>(S + pos * stride + lane_off) = w;
-            }
-            __syncthreads();
-        }
-    }
-    if (smem) {  // write the slab back (rows 0..n, the zero row included)
-        const int vec = SW >> 4;
-        const int64_t nvec = static_cast<int64_t>(n + 1) * vec;
-        for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
-            const int64_t row = i / vec;
-            const int part = static_cast<int>(i - row * vec);
-            *reinterpret_cast<uint4 *>(S_g + row * Rp + col0 + 16 * part) = reinterpret_cast<const uint4 *>(S)[i];
-        }
-    }
-
-    // f and g of the final sweep for the slab's walkers (Eq. 1)
     uint8_t *small = dsm + a.smem_state;
     long long *s_F = reinterpret_cast<long long *>(small);
     int *s_G = reinterpret_cast<int *>(s_F + kMaxR);
-    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
-        s_F[i] = 0;
-        s_G[i] = 0;
-    }
-    __syncthreads();
-    {
-        long long F0 = 0, F1 = 0, F2 = 0, F3 = 0;
-        int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-        for (int pos = grp; pos < n; pos += G) {
-            Rec<DC, DL> rc;
-            rc.load(rec, pos);
-            const uint32_t xs = fetch(pos);
-            const int h4 = 2 * rc.h2();
-            int c0 = h4, c1 = h4, c2 = h4, cc = h4;
-#pragma unroll
-            for (int k = 0; k < DC; ++k) {
-                const uint32_t x = fetch(rc.nb(k));
-                const int j2 = rc.j2(k);
-                c0 += j2 * sbyte<0>(x);
-                c1 += j2 * sbyte<1>(x);
-                c2 += j2 * sbyte<2>(x);
-                cc += j2 * sbyte<3>(x);
+
+    if (d.mode == 2) {
+        const int B = SW >> 3;
+        const int byte_lane = lane_q >> 1;
+        const int nib_shift = (lane_q & 1) * 4;
+        uint8_t *bits = dsm;
+        uint32_t *lut = reinterpret_cast<uint32_t *>(dsm + ((static_cast<int64_t>(n + 1) * B + 15) & ~15LL));
+        if (threadIdx.x < 16) lut[threadIdx.x] = word_of_bits(threadIdx.x);
+        const int64_t nbytes = static_cast<int64_t>(n + 1) * B;
+        for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {
+            const int pos = static_cast<int>(i / B);
+            const int b = static_cast<int>(i - static_cast<int64_t>(pos) * B);
+            uint32_t lo = 0, hi = 0;
+            if (pos == n) {
+            } else if (!inited) {
+                const uint32_t lq0 = static_cast<uint32_t>((col0 >> 2) + 2 * b);
+                lo = bits_of_word(init_word<DC, DL>(d, rec, pos, lq0));
+                hi = bits_of_word(init_word<DC, DL>(d, rec, pos, lq0 + 1));
+            } else {
+                const uint2 v = *reinterpret_cast<const uint2 *>(S_g + static_cast<int64_t>(pos) * Rp + col0 + 8 * b);
+                lo = bits_of_word(v.x);
+                hi = bits_of_word(v.y);
             }
-            F0 += static_cast<long long>(sbyte<0>(xs)) * c0;
-            F1 += static_cast<long long>(sbyte<1>(xs)) * c1;
-            F2 += static_cast<long long>(sbyte<2>(xs)) * c2;
-            F3 += static_cast<long long>(sbyte<3>(xs)) * cc;
-#pragma unroll
-            for (int l = 0; l < DL; ++l) {
-                if (rc.lk(l) == n) continue;
-                const uint32_t y = fetch(rc.lk(l));
-                g0 += sbyte<0>(xs) != sbyte<0>(y);
-                g1 += sbyte<1>(xs) != sbyte<1>(y);
-                g2 += sbyte<2>(xs) != sbyte<2>(y);
-                g3 += sbyte<3>(xs) != sbyte<3>(y);
+            bits[i] = static_cast<uint8_t>(lo | (hi << 4));
+        }
+        __syncthreads();
+        auto fetch = [&](int row) -> uint32_t { return lut[(bits[row * B + byte_lane] >> nib_shift) & 0xF]; };
+        auto fetch_link = [&](int row) -> uint32_t { return row != n ? fetch(row) : 0u; };
+        const unsigned pair = 0x3u << (threadIdx.x & 30);
+        auto store = [&](int pos, uint32_t w) {
+            const uint32_t nib = bits_of_word(w);
+            const uint32_t other = __shfl_xor_sync(pair, nib, 1);
+            if ((lane_q & 1) == 0) bits[pos * B + byte_lane] = static_cast<uint8_t>(nib | (other << 4));
+        };
+        slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch_link, store, grp, G, lq, sweeps_done);
+        const int64_t nout = static_cast<int64_t>(n) * B;  // rows 0..n-1 back as int8 spins
+        for (int64_t i = threadIdx.x; i < nout; i += blockDim.x) {
+            const int64_t row = i / B;
+            const int b = static_cast<int>(i - row * B);
+            const uint32_t byte = bits[i];
+            *reinterpret_cast<uint2 *>(S_g + row * Rp + col0 + 8 * b) = make_uint2(lut[byte & 0xF], lut[byte >> 4]);
+        }
+        for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+            s_F[i] = 0;
+            s_G[i] = 0;
+        }
+        __syncthreads();
+        slab_energies<DC, DL>(d, rec, fetch, grp, G, lane_off, s_F, s_G);
+    } else {
+        const bool smem = d.mode == 1;
+        const int64_t stride = smem ? SW : Rp;         // row stride of the spins the slab works on
+        int8_t *S = smem ? reinterpret_cast<int8_t *>(dsm) : S_g + col0;
+        if (!inited) {
+            const int64_t total = static_cast<int64_t>(n) * QL;
+            for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+                const int pos = static_cast<int>(e / QL);
+                const int qq = static_cast<int>(e - static_cast<int64_t>(pos) * QL);
+                *reinterpret_cast<uint32_t *>(S + pos * stride + 4 * qq) =
+                    init_word<DC, DL>(d, rec, pos, static_cast<uint32_t>((col0 >> 2) + qq));
+            }
+            for (int i = threadIdx.x; i < SW; i += blockDim.x) S[n * stride + i] = 0;
+        } else if (smem) {
+            const int vec = SW >> 4;
+            const int64_t nvec = static_cast<int64_t>(n + 1) * vec;
+            for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
+                const int64_t row = i / vec;
+                const int part = static_cast<int>(i - row * vec);
+                reinterpret_cast<uint4 *>(S)[i] =
+                    *reinterpret_cast<const uint4 *>(S_g + row * Rp + col0 + 16 * part);
             }
         }
-        unsigned long long *uf = reinterpret_cast<unsigned long long *>(s_F);
-        atomicAdd(uf + lane_off + 0, static_cast<unsigned long long>(F0));
-        atomicAdd(uf + lane_off + 1, static_cast<unsigned long long>(F1));
-        atomicAdd(uf + lane_off + 2, static_cast<unsigned long long>(F2));
-        atomicAdd(uf + lane_off + 3, static_cast<unsigned long long>(F3));
-        atomicAdd(s_G + lane_off + 0, g0);
-        atomicAdd(s_G + lane_off + 1, g1);
-        atomicAdd(s_G + lane_off + 2, g2);
-        atomicAdd(s_G + lane_off + 3, g3);
+        __syncthreads();
+        auto fetch = [&](int row) -> uint32_t {
+            return *reinterpret_cast<const uint32_t *>(S + row * stride + lane_off);
+        };
+        auto store = [&](int pos, uint32_t w) {
+            *reinterpret_cast<uint32_t *>(S + pos * stride + lane_off) = w;
+        };
+        slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch, store, grp, G, lq, sweeps_done);
+        if (smem) {  // write the slab back (rows 0..n, the zero row included)
+            const int vec = SW >> 4;
+            const int64_t nvec = static_cast<int64_t>(n + 1) * vec;
+            for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
+                const int64_t row = i / vec;
+                const int part = static_cast<int>(i - row * vec);
+                *reinterpret_cast<uint4 *>(S_g + row * Rp + col0 + 16 * part) = reinterpret_cast<const uint4 *>(S)[i];
+            }
+        }
+        for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+            s_F[i] = 0;
+            s_G[i] = 0;
+        }
+        __syncthreads();
+        slab_energies<DC, DL>(d, rec, fetch, grp, G, lane_off, s_F, s_G);
     }
     __syncthreads();
     {

@@ -39,9 +39,10 @@ struct BatchRun {
     int64_t counter;     // int32: slabs of this run finished in the current launch
     uint32_t k0, k1;     // seed
     int32_t n, C, I, J, R, Rp, run, trace_cap, rec_vec;
-    int32_t sw;          // walkers per slab (power of two, 16..Rp)
+    int32_t sw;          // walkers per slab (power of two, 8..Rp)
     int32_t nslab;       // Rp / sw
-    int32_t pad;
+    int32_t mode;        // slab spins: 0 int8 in global memory, 1 int8 in shared memory,
+                         // 2 bit-packed in shared memory
     int64_t work;        // n * Rp, for ordering
 };
 
@@ -64,6 +65,10 @@ struct BatchArgs {
 };
 
 size_t batch_small_smem_bytes();
+// Shared memory of a bit-packed slab: (n + 1) rows of sw / 8 bytes, then the nibble table.
+inline int64_t batch_bits_bytes(int32_t n, int32_t sw) {
+    return ((static_cast<int64_t>(n + 1) * (sw / 8) + 15) & ~int64_t{15}) + 64;
+}
 cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state);
 cudaError_t launch_batch(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
 

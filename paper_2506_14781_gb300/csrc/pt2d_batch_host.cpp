@@ -159,11 +159,15 @@ struct pt2d_batch {
     std::vector<std::pair<int64_t, int32_t>> order;  // run array order: (id, run)
     int32_t n_items = 0;
     int glob_sw = 32;                                 // slab width when spins stay in global memory
+    int storage = 0;                                  // pt2d_batch_shape::storage
+    int balance = 2;                                  // pt2d_batch_shape::balance
+    bool int8 = true;                                 // int8 shared-memory slabs allowed
+    bool bits = true;                                 // bit-packed shared-memory slabs allowed
     int32_t n_runs = 0;
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
     int graph_events = -1, graph_interval = -1, graph_threads = -1;
-    static constexpr int kMaxSlabs = pt2d::kBatchMaxReplicas / 16;
+    static constexpr int kMaxSlabs = pt2d::kBatchMaxReplicas / 8;
     int64_t launches = 0;
     int last_cuda = 0;
 };
@@ -188,20 +192,71 @@ void drop_graph(pt2d_batch *b) {
     b->graph_events = b->graph_interval = b->graph_threads = -1;
 }
 
-// Slab width of a run: the whole run when its spins fit in the shared memory
-// reserved per CTA, else the widest power of two >= 16 that fits, else the
-// global-memory slab width.
-int32_t slab_width(const pt2d_batch *b, int32_t n, int32_t Rp) {
-    for (int32_t sw = Rp; sw >= 16; sw >>= 1)
-        if (static_cast<int64_t>(n + 1) * sw <= b->smem_state) return sw;
-    return std::min<int32_t>(Rp, b->glob_sw);
+// Slab width and storage of a run: int8 spins in shared memory, the whole run
+// when it fits in the shared memory reserved per CTA, else the widest power of
+// two >= 16 that fits; else the same with bit-packed spins (widths >= 8); else
+// int8 spins in global memory at the global-memory slab width.  Then the width
+// is halved while a slab holds more than `cap` spin-walkers (0 = no cap).
+void slab_shape(const pt2d_batch *b, pt2d::BatchRun &d, int64_t cap) {
+    auto capped = [&](int32_t sw, int32_t narrowest) {
+        while (cap > 0 && sw > narrowest && static_cast<int64_t>(d.n) * sw > cap) sw >>= 1;
+        return sw;
+    };
+    for (int32_t sw = d.Rp; b->int8 && sw >= 16; sw >>= 1)
+        if (static_cast<int64_t>(d.n + 1) * sw <= b->smem_state) {
+            d.sw = capped(sw, 16);
+            d.mode = 1;
+            return;
+        }
+    if (b->smem_state > 0 && b->bits)
+        for (int32_t sw = d.Rp; sw >= 8; sw >>= 1)
+            if (pt2d::batch_bits_bytes(d.n, sw) <= b->smem_state) {
+                d.sw = capped(sw, 8);
+                d.mode = 2;
+                return;
+            }
+    d.sw = capped(std::min<int32_t>(d.Rp, b->glob_sw), 16);
+    d.mode = 0;
+}
+
+bool shape_valid(const pt2d_batch_shape &sh) {
+    return sh.threads_per_cta >= 128 && sh.threads_per_cta <= 1024 && sh.threads_per_cta % 32 == 0 &&
+           sh.storage >= 0 && sh.storage <= 3 && sh.global_width >= 16 &&
+           sh.global_width <= pt2d::kBatchMaxReplicas && (sh.global_width & (sh.global_width - 1)) == 0 &&
+           sh.balance >= 0 && sh.balance <= 1024;
+}
+
+// Install a launch shape; the run descriptors are rebuilt at the next launch
+// when the slab layout changes.
+bool apply_shape(pt2d_batch *b, const pt2d_batch_shape &sh) {
+    if (!shape_valid(sh)) return false;
+    b->threads = sh.threads_per_cta;
+    const int smem_state = sh.storage == 1 ? 0 : b->smem_state_max;
+    if (sh.storage != b->storage || smem_state != b->smem_state || sh.global_width != b->glob_sw ||
+        sh.balance != b->balance)
+        b->dirty = true;
+    b->storage = sh.storage;
+    b->smem_state = smem_state;
+    b->int8 = sh.storage != 3;
+    b->bits = sh.storage != 2;
+    b->glob_sw = sh.global_width;
+    b->balance = sh.balance;
+    return true;
+}
+
+pt2d_batch_shape current_shape(const pt2d_batch *b) {
+    return pt2d_batch_shape{b->threads, b->storage, b->glob_sw, b->balance};
 }
 
 int upload_descriptors(pt2d_batch *b) {
     std::vector<std::pair<pt2d::BatchRun, std::pair<int64_t, int32_t>>> tagged;
+    int64_t total = 0;
+    for (auto &kv : b->insts)
+        for (auto &d : kv.second.desc) total += d.work;
+    const int64_t cap = b->balance > 0 ? total / (static_cast<int64_t>(b->grid) * b->balance) : 0;
     for (auto &kv : b->insts)
         for (auto &d : kv.second.desc) {
-            d.sw = slab_width(b, d.n, d.Rp);
+            slab_shape(b, d, cap);
             d.nslab = d.Rp / d.sw;
             tagged.push_back({d, {kv.first, d.run}});
         }
@@ -210,13 +265,24 @@ int upload_descriptors(pt2d_batch *b) {
     if (static_cast<int32_t>(tagged.size()) > b->max_runs) return PT2D_ERR_OOM;
     std::vector<pt2d::BatchRun> all;
     std::vector<pt2d::BatchItem> items;
+    std::vector<int64_t> item_work;
     b->order.clear();
     for (const auto &t : tagged) {
         const int32_t idx = static_cast<int32_t>(all.size());
         all.push_back(t.first);
         b->order.push_back(t.second);
-        for (int32_t k = 0; k < t.first.nslab; ++k) items.push_back({idx, k});
+        for (int32_t k = 0; k < t.first.nslab; ++k) {
+            items.push_back({idx, k});
+            item_work.push_back(static_cast<int64_t>(t.first.n) * t.first.sw);
+        }
     }
+    // largest slabs first, so the event ends on small ones
+    std::vector<size_t> perm(items.size());
+    for (size_t k = 0; k < perm.size(); ++k) perm[k] = k;
+    std::stable_sort(perm.begin(), perm.end(), [&](size_t x, size_t y) { return item_work[x] > item_work[y]; });
+    std::vector<pt2d::BatchItem> sorted(items.size());
+    for (size_t k = 0; k < perm.size(); ++k) sorted[k] = items[perm[k]];
+    items.swap(sorted);
     if (!all.empty()) {
         BK(b, cudaMemcpyAsync(b->d_runs, all.data(), sizeof(pt2d::BatchRun) * all.size(),
                               cudaMemcpyHostToDevice, b->stream));
@@ -327,7 +393,14 @@ int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_
     b->grid = sms > 0 ? sms : 152;
     b->smem_state_max = std::max(0, smem_optin - static_cast<int>(pt2d::batch_small_smem_bytes()) - 1024);
     b->smem_state_max &= ~15;
-    b->smem_state = opt->sweep_kernel == 1 ? 0 : b->smem_state_max;
+    {
+        const pt2d_batch_shape shape{b->threads, opt->sweep_kernel,
+                                     opt->walkers_per_cta ? opt->walkers_per_cta : 32, 2};
+        if (!apply_shape(b, shape)) {
+            delete b;
+            return PT2D_ERR_INVALID_ARG;
+        }
+    }
     if (opt->stream) {
         b->stream = static_cast<cudaStream_t>(opt->stream);
     } else {
@@ -489,56 +562,66 @@ int pt2d_batch_sync(pt2d_batch *b) {
     return PT2D_OK;
 }
 
-int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, int32_t *threads_out,
-                        int32_t *smem_out) {
+int pt2d_batch_get_shape(const pt2d_batch *b, pt2d_batch_shape *shape) {
+    if (!b || !shape) return PT2D_ERR_INVALID_ARG;
+    *shape = current_shape(b);
+    return PT2D_OK;
+}
+
+int pt2d_batch_set_shape(pt2d_batch *b, const pt2d_batch_shape *shape) {
+    if (!b || !shape) return PT2D_ERR_INVALID_ARG;
+    return apply_shape(b, *shape) ? PT2D_OK : PT2D_ERR_INVALID_ARG;
+}
+
+int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, pt2d_batch_shape *chosen) {
     if (!b || events < 1 || swap_interval < 1) return PT2D_ERR_INVALID_ARG;
     cudaSetDevice(b->device);
-    const int thread_opts[] = {512, 1024};
-    const int smem_opts[] = {b->smem_state_max, 0};
-    const int gsw_opts[] = {16, 64};
+    struct Events {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Events() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } ev;
+    BK(b, cudaEventCreate(&ev.e0));
+    BK(b, cudaEventCreate(&ev.e1));
+    const pt2d_batch_shape start = current_shape(b);
     float best_ms = -1.0f;
-    int best_t = b->threads, best_s = b->smem_state, best_g = b->glob_sw;
-    cudaEvent_t e0, e1;
-    BK(b, cudaEventCreate(&e0));
-    BK(b, cudaEventCreate(&e1));
+    pt2d_batch_shape best = start;
     // Every launch shape computes the same trajectories, so the trial launches are
     // ordinary progress of the chains.
-    for (int so : smem_opts) {
-        for (int gw : gsw_opts)
-        for (int t : thread_opts) {
-            b->threads = t;
-            if (b->smem_state != so || b->glob_sw != gw) {
-                b->smem_state = so;
-                b->glob_sw = gw;
-                b->dirty = true;
-            }
-            int st = launch(b, events, swap_interval);  // first launch per shape: not timed
-            if (st) return st;
-            BK(b, cudaEventRecord(e0, b->stream));
-            st = launch(b, events, swap_interval);
-            if (st) return st;
-            BK(b, cudaEventRecord(e1, b->stream));
-            BK(b, cudaEventSynchronize(e1));
-            float ms = 0.0f;
-            BK(b, cudaEventElapsedTime(&ms, e0, e1));
-            if (best_ms < 0.0f || ms < best_ms) {
-                best_ms = ms;
-                best_t = t;
-                best_s = so;
-                best_g = gw;
-            }
+    auto trial = [&](const pt2d_batch_shape &sh) -> int {
+        apply_shape(b, sh);
+        int st = launch(b, events, swap_interval);  // first launch per shape: not timed
+        if (st) return st;
+        BK(b, cudaEventRecord(ev.e0, b->stream));
+        st = launch(b, events, swap_interval);
+        if (st) return st;
+        BK(b, cudaEventRecord(ev.e1, b->stream));
+        BK(b, cudaEventSynchronize(ev.e1));
+        float ms = 0.0f;
+        BK(b, cudaEventElapsedTime(&ms, ev.e0, ev.e1));
+        if (best_ms < 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best = sh;
         }
+        return PT2D_OK;
+    };
+    for (int storage : {0, 1})
+        for (int balance : {0, 2, 8}) {
+            pt2d_batch_shape sh = start;
+            sh.threads_per_cta = 1024;
+            sh.storage = storage;
+            sh.balance = balance;
+            if (int st = trial(sh)) return st;
+        }
+    {
+        pt2d_batch_shape sh = best;
+        sh.threads_per_cta = 512;
+        if (int st = trial(sh)) return st;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    b->threads = best_t;
-    if (b->smem_state != best_s || b->glob_sw != best_g) {
-        b->smem_state = best_s;
-        b->glob_sw = best_g;
-        b->dirty = true;
-    }
-    if (threads_out) *threads_out = best_t;
-    if (smem_out) *smem_out = best_s;
+    apply_shape(b, best);
+    if (chosen) *chosen = best;
     return PT2D_OK;
 }
 

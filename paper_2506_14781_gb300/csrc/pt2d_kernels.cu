@@ -171,13 +171,6 @@ __global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
     energies<DC, DL, NQ>(L, wk, fetch_q, own_q, lane_off, grp, G, SW, col0);
 }
 
-// Spin bits of four int8 spins: bit k is 1 iff byte k holds -1 (0xFF); the
-// multiply gathers the four sign bits (no two product bits share a position).
-__device__ __forceinline__ uint32_t bits_of_word(uint32_t w) {
-    const uint32_t m = (w >> 7) & 0x01010101u;
-    return ((m * 0x00204081u) >> 21) & 0xFu;
-}
-
 // Sweep block with the slab bit-packed in shared memory: (n + 1) rows x SW/8
 // bytes, bit k of a byte = spin of one walker (1 = -1), for instances whose
 // int8 slab does not fit.  A thread owns one nibble (4 walkers); a 16-entry
@@ -207,11 +200,7 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_bits(Layout L, Walkers wk, in
     const int n = L.n;
     uint8_t *bits = smb;
     uint32_t *lut = reinterpret_cast<uint32_t *>(smb + ((static_cast<int64_t>(n + 1) * B + 15) & ~15LL));
-    if (threadIdx.x < 16) {
-        uint32_t w = 0;
-        for (int k = 0; k < 4; ++k) w |= ((threadIdx.x >> k) & 1u ? 0xFFu : 0x01u) << (8 * k);
-        lut[threadIdx.x] = w;
-    }
+    if (threadIdx.x < 16) lut[threadIdx.x] = word_of_bits(threadIdx.x);
     // load: 8 int8 spins of global memory -> one byte of bits
     const int64_t nbytes = static_cast<int64_t>(n + 1) * B;
     for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {

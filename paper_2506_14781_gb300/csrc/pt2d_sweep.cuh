@@ -156,6 +156,22 @@ __device__ __forceinline__ uint2 update8(const Rec<DC, DL> &rc, const Quad &qa, 
     return make_uint2(decide4<DC, DL>(rc, qa, xa, ya, ra), decide4<DC, DL>(rc, qb, xb, yb, rb));
 }
 
+// Spin bits of four int8 spins: bit k is 1 iff byte k holds -1 (0xFF); the
+// multiply gathers the four sign bits (no two product bits share a position).
+__device__ __forceinline__ uint32_t bits_of_word(uint32_t w) {
+    const uint32_t m = (w >> 7) & 0x01010101u;
+    return ((m * 0x00204081u) >> 21) & 0xFu;
+}
+
+// Nibble -> four int8 spins (bit k set: byte k = -1), the table a bit-packed
+// slab uses to expand a quad's spins.
+__device__ __forceinline__ uint32_t word_of_bits(uint32_t nib) {
+    uint32_t w = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w |= ((nib >> k) & 1u ? 0xFFu : 0x01u) << (8 * k);
+    return w;
+}
+
 // The pair loop of one swap event of Algorithm 1 for one run, by the calling
 // CTA's threads (pairs of one event are disjoint, so they run in parallel).
 // at: slot -> walker (shared memory, permuted in place); fw / gw: f and g by

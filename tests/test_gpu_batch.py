@@ -69,12 +69,13 @@ def _mixed(pt):
     ]
 
 
-@pytest.mark.parametrize("spins_in_global,threads", [(False, 0), (True, 0), (False, 256)])
-def test_batch_matches_plain_contexts(pt, spins_in_global, threads):
+@pytest.mark.parametrize("kernel,threads", [("auto", 0), ("global", 0), ("auto", 256),
+                                            ("bits", 0), ("bits", 128), ("smem", 512)])
+def test_batch_matches_plain_contexts(pt, kernel, threads):
     probs = _mixed(pt)
     trace = 16
     batch = pt.Batch(1 << 30, max_coupling_degree=3, max_runs=64, trace_capacity=trace,
-                     threads_per_cta=threads, spins_in_global=spins_in_global)
+                     threads_per_cta=threads, sweep_kernel=kernel)
     ids = [batch.add(p["phys"], p["beta"], p["P"], p["runs"], p["seed"], p["target"]) for p in probs]
     # 7 events of 5 sweeps, in three launches
     batch.run(2, 5)
@@ -82,6 +83,51 @@ def test_batch_matches_plain_contexts(pt, spins_in_global, threads):
     batch.run(1, 5)
     for pr, bid in zip(probs, ids):
         ctx = _plain(pt, pr, 35, 5, trace)
+        _assert_same(pt, batch, bid, ctx)
+        ctx.close()
+    batch.close()
+
+
+def test_batch_slab_storage_by_size(pt):
+    """Runs whose int8 slab of 16 walkers does not fit in shared memory go to
+    bit-packed slabs (128 KB+ instances: widths 8 and 32 walkers), next to int8
+    shared-memory slabs, in one launch; each matches its plain context."""
+    probs = [
+        _problem(pt, 600, 0.5, 31, ("max_edges", 3), 16, 8, 1),   # n ~ 120k: bits, 8 walkers
+        _problem(pt, 300, 0.5, 32, ("max_edges", 3), 16, 8, 1),   # n ~ 30k: bits, 32 walkers
+        _problem(pt, 150, 0.5, 33, ("max_edges", 3), 16, 8, 2),   # n ~ 7.5k: int8, 16 walkers
+        _problem(pt, 40, 0.5, 34, ("max_edges", 3), 4, 8, 1),     # int8, whole run
+    ]
+    assert probs[0]["phys"].n > 110000
+    batch = pt.Batch(1 << 28, max_coupling_degree=3, max_runs=16, trace_capacity=8)
+    ids = [batch.add(p["phys"], p["beta"], p["P"], p["runs"], p["seed"], p["target"]) for p in probs]
+    batch.run(3, 4)
+    batch.run(2, 4)
+    for pr, bid in zip(probs, ids):
+        ctx = _plain(pt, pr, 20, 4, 8)
+        _assert_same(pt, batch, bid, ctx)
+        ctx.close()
+    batch.close()
+
+
+def test_batch_shape_changes_between_launches(pt):
+    """Switching storage, slab widths, balance and threads between launches
+    leaves every trajectory unchanged."""
+    probs = _mixed(pt)[:5]
+    batch = pt.Batch(1 << 29, max_coupling_degree=3, max_runs=64, trace_capacity=8)
+    ids = [batch.add(p["phys"], p["beta"], p["P"], p["runs"], p["seed"], p["target"]) for p in probs]
+    shapes = [dict(storage="global", global_width=16, balance=0, threads_per_cta=256),
+              dict(storage="bits", balance=64, threads_per_cta=1024),
+              dict(storage="smem", balance=1, threads_per_cta=640),
+              dict(storage="auto", global_width=128, balance=8, threads_per_cta=128)]
+    for sh in shapes:
+        batch.shape = sh
+        assert all(batch.shape[k] == v for k, v in sh.items())
+        batch.run(2, 3)
+    with pytest.raises(pt.Pt2dError):
+        batch.shape = dict(global_width=24)
+    for pr, bid in zip(probs, ids):
+        ctx = _plain(pt, pr, 24, 3, 8)
         _assert_same(pt, batch, bid, ctx)
         ctx.close()
     batch.close()
@@ -113,12 +159,14 @@ def test_batch_pool_full_and_autotune(pt):
     i2 = batch.add(a["phys"], a["beta"], a["P"], 1, a["seed"] + 1, a["target"])
     with pytest.raises(pt.PoolFull):
         batch.add(a["phys"], a["beta"], a["P"], 1, a["seed"] + 2, a["target"])
-    threads, smem = batch.autotune(2, 3)  # 8 shapes x 2 launches of 2 events
-    assert threads in (512, 1024)
+    shape = batch.autotune(2, 3)  # every trial launch advances the chains
+    assert shape["threads_per_cta"] in (512, 1024) and shape == batch.shape
     batch.run(2, 3)
-    _assert_same(pt, batch, i1, _plain(pt, a, 17 * 2 * 3, 3, 4))
+    sweeps = int(batch.read(i1, pt.COUNTERS)[0])
+    assert sweeps % 6 == 0 and sweeps >= 5 * 2 * 3
+    _assert_same(pt, batch, i1, _plain(pt, a, sweeps, 3, 4))
     a2 = dict(a, seed=a["seed"] + 1)
-    _assert_same(pt, batch, i2, _plain(pt, a2, 17 * 2 * 3, 3, 4))
+    _assert_same(pt, batch, i2, _plain(pt, a2, sweeps, 3, 4))
 
 
 def test_batch_matches_oracle_on_tiny_config(pt, tiny_config):
