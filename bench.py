@@ -1,13 +1,16 @@
 """Benchmark of the 2D-PT hot path on GB300.
 
-Workload (default): a planted Wishart instance with N = 200 logical spins,
-alpha = 0.5, copy-chain sparsified to at most 3 original edges per copy
-(13,400 physical spins), an I = 32 x J = 8 replica grid (geometric beta
-0.1..2.0, linear P 0.5..4.0 x 32767), 64 independent runs (16,384 replicas),
-swap interval 50.  One step = one swap event of Algorithm 1 for all runs:
-50 heat-bath sweeps of every replica, f and g of the final sweep, one round
-of P- or beta-swaps and the bottom-right record.  The int8 spin state
+Workload (default, --workload n200): a planted Wishart instance with N = 200
+logical spins, alpha = 0.5, copy-chain sparsified to at most 3 original edges
+per copy (13,400 physical spins), an I = 32 x J = 8 replica grid (geometric
+beta 0.1..5.0 / scale, linear P 0.5..64 x 32767), 64 independent runs (16,384
+replicas), swap interval 50.  One step = one swap event of Algorithm 1 for all
+runs: 50 heat-bath sweeps of every replica, f and g of the final sweep, one
+round of P- or beta-swaps and the bottom-right record.  The int8 spin state
 (220 MB) is larger than L2, so no flush is needed between steps.
+--workload n800: N = 800 (213,551 physical spins), I = 64 x J = 16, 16 runs
+(3.5 GB of spins), same ladders and interval.
+--workload batched / serving: the uneven batch and the request stream.
 
 Metric: spin updates per second (physical spins x replicas x sweeps / time).
 
@@ -31,9 +34,51 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "spin updates/sec"
+METRIC = "spin updates/sec and time-to-planted-ground-state (batched vs plain, same GB300)"
 UNIT = "spin-updates/s"
-WORKLOAD = "wishart-planted N=200 alpha=0.5, <=3 edges/copy (13400 spins), I=32 x J=8, 64 runs, swap every 50 sweeps"
+WORKLOADS = {
+    "n200": dict(N=200, alpha=0.5, inst_seed=2, I=32, J=8, runs=64, interval=50),
+    "n800": dict(N=800, alpha=0.5, inst_seed=3, I=64, J=16, runs=16, interval=50),
+}
+
+
+def workload_name(key, n, runs=None):
+    w = WORKLOADS[key]
+    return (f"wishart-planted N={w['N']} alpha={w['alpha']}, <=3 edges/copy ({n} spins), "
+            f"I={w['I']} x J={w['J']}, {runs or w['runs']} runs, swap every {w['interval']} sweeps")
+
+
+# Algorithmic lane-operations of one spin update under the heat-bath contract,
+# the minimal sequence with a quad of walkers sharing one Philox call: Philox
+# share 10 (10 rounds x 2 wide multiplies + 2 three-input xors, / 4), field 11
+# (3 couplings x (sign, multiply-add) + 2 links x (sign, add) + the P product),
+# decision 8 (convert, scale, exp2, uniform 2, 1 + e, fused test, sign), state
+# traffic 3 (neighbour and record loads, pack and store, per walker).
+OPS_PER_UPDATE = 32.0
+# Algorithmic DRAM bytes per update if the state made one round trip per sweep:
+# one int8 read and one write, plus the neighbour record (5 x 8 B) over 128 walkers.
+BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
+
+# DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# valid only while the kernel sources hash to `src`; the summaries are under profiles/.
+PROFILED_TRAFFIC = {
+    ("n200", "k_sweep_smem"): dict(src="7c005a72229b9f6c", dram_bytes_per_launch=386_748_672,
+                                   profile="profiles/k_sweep_smem_n200.md"),
+    # captured at 4 of the 16 runs and scaled by the walkers
+    ("n800", "k_sweep_bits"): dict(src="7c005a72229b9f6c", dram_bytes_per_launch=19_034_056_000,
+                                   profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
+}
+KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h")
+
+
+def kernel_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_14781_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -52,13 +97,15 @@ BETA_MIN, BETA_MAX, P_MIN, P_MAX = 0.1, 5.0, 0.5, 64.0
 RHO_TARGETS = (0.2, 0.1, 0.05)
 
 
-def make_workload(N=200, alpha=0.5, inst_seed=2, I=32, J=8, runs=64, interval=50):
+def make_workload(key="n200"):
     import synth
 
-    inst = synth.wishart_planted(N, alpha, inst_seed)
-    beta = synth.beta_ladder(I, BETA_MIN, BETA_MAX, inst.scale)
-    P = synth.penalty_ladder(J, P_MIN, P_MAX, 32767)
-    return dict(inst=inst, beta=beta, P=P, runs=runs, interval=interval, I=I, J=J)
+    w = WORKLOADS[key]
+    inst = synth.wishart_planted(w["N"], w["alpha"], w["inst_seed"])
+    beta = synth.beta_ladder(w["I"], BETA_MIN, BETA_MAX, inst.scale)
+    P = synth.penalty_ladder(w["J"], P_MIN, P_MAX, 32767)
+    return dict(inst=inst, beta=beta, P=P, runs=w["runs"], interval=w["interval"], I=w["I"], J=w["J"],
+                key=key)
 
 
 def residual_tts(trace_f, trace_g, events_done, E_planted, N, scale, interval):
@@ -160,7 +207,9 @@ def run_gpu(args):
 
     rank, world, dist = dist_setup(args.gpus)
     dev = torch.cuda.current_device()
-    wl = make_workload()
+    wl = make_workload(args.workload)
+    if args.runs:  # smaller cases of the same kernel, for profiling captures
+        wl["runs"] = args.runs
     inst, beta, P, runs, interval = wl["inst"], wl["beta"], wl["P"], wl["runs"], wl["interval"]
     phys = pt.sparsify(inst.Jq, "max_edges", 3)
     n = phys.n
@@ -205,14 +254,15 @@ def run_gpu(args):
     peaks, peak_src = _peaks()
     avg_launch_ms = sweep_ms / max(sweep_launches, 1)
     updates_per_launch = n * R * runs * interval
-    # algorithmic bytes per update: one int8 write plus one int8 read of the state
-    # (neighbour rows shared within a colour pass), plus the ELL row (4 B index +
-    # 4 B coupling per neighbour, 5 neighbours) amortised over a 128-walker warp
-    algo_bytes = updates_per_launch * (2.0 + 40.0 / 128.0)
+    algo_bytes = updates_per_launch * BYTES_PER_UPDATE
     hbm_achieved = algo_bytes / (avg_launch_ms / 1e3) / 1e9
-    # issue roofline: lane-operations the heat-bath contract needs per update
-    # (Philox4x32-10 share 15, field 10, decision 8), against 152 SMs x 128 lanes x clock
-    ops_per_update = 33.0
+    ops_per_update = OPS_PER_UPDATE
+    tiling = ctx.tiling
+    kernel = {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
+              "generic": "k_sweep_generic"}[tiling["kernel"]]
+    prof = PROFILED_TRAFFIC.get((args.workload, kernel))
+    src_hash = kernel_source_hash()
+    traffic = prof["dram_bytes_per_launch"] if prof and prof["src"] == src_hash else None
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
     alu_achieved = updates_per_launch * ops_per_update / (avg_launch_ms / 1e3) / 1e12
@@ -245,18 +295,22 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "int8 spins, int32 fields, f32 decisions",
         "data": "synthetic (seeded planted Wishart instance)",
-        "config": {"workload": WORKLOAD, "physical_spins": n, "replicas": R * runs,
-                   "sweeps_per_step": interval, "l2": "state 220 MB > L2; no flush",
+        "config": {"workload": workload_name(args.workload, n, runs), "physical_spins": n,
+                   "replicas": R * runs, "sweeps_per_step": interval,
+                   "l2": f"state {n * R * runs / 1e6:.0f} MB > L2 (129 MB); no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "tiling": "automatic"},
+                   "tiling": tiling},
         "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
                      "unit": "Tops/s (lane-ops)", "frac": alu_achieved / alu_peak,
-                     "traffic": None, "kernel": "k_sweep",
+                     "traffic": traffic, "kernel": kernel, "kernel_src": src_hash,
+                     "traffic_source": prof["profile"] if traffic is not None else
+                     "null: no ncu capture of this kernel source",
                      "peak_source": f"{sm_count} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_src} max clock)",
                      "ops_per_update": ops_per_update,
                      "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks.get("hbm_gbs"),
                              "frac": hbm_achieved / peaks.get("hbm_gbs", 6800.0),
-                             "bytes_per_update": 2.0 + 40.0 / 128.0},
+                             "bytes_per_update": BYTES_PER_UPDATE,
+                             "measured_gbs": (traffic / (avg_launch_ms / 1e3) / 1e9) if traffic else None},
                      "avg_launch_ms": avg_launch_ms, "launches": sweep_launches,
                      "share_of_step": sweep_ms / max(elapsed_ms, 1e-9)},
         "e2e": e2e,
@@ -328,10 +382,12 @@ def _oracle_sample(wl, threads, sweeps, state=None):
 
 
 def cpu_baseline(wl, args):
-    threads = os.cpu_count() or 1
-    rate, wall, _ = _oracle_sample(wl, threads, args.cpu_sweeps)
+    threads = min(os.cpu_count() or 1, wl["runs"])
+    sweeps = args.cpu_sweeps if wl["key"] == "n200" else 1
+    rate, wall, _ = _oracle_sample(wl, threads, sweeps)
+    R = wl["I"] * wl["J"]
     return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{threads} runs x 256 replicas x {args.cpu_sweeps} sweeps of the N=200 "
+            "sample": f"{threads} runs x {R} replicas x {sweeps} sweeps of the N={wl['inst'].N} "
                       f"instance (one thread per run), {wall:.1f} s wall"}
 
 
@@ -339,9 +395,11 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = make_workload()
-    threads = os.cpu_count() or 1
-    sweeps = 2
+    key = args.workload if args.workload in WORKLOADS else "n200"
+    wl = make_workload(key)
+    threads = min(os.cpu_count() or 1, wl["runs"])
+    sweeps = 2 if key == "n200" else 1
+    R = wl["I"] * wl["J"]
     state = None
     for _ in range(args.warmup):
         _, _, state = _oracle_sample(wl, threads, sweeps, state)
@@ -357,10 +415,11 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": total_wall / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int8 spins, int64 energies, f32 decisions", "data": "synthetic (seeded planted Wishart instance)",
-        "config": {"workload": WORKLOAD, "sample": f"per step: {threads} runs x 256 replicas x {sweeps} sweeps"},
+        "config": {"workload": workload_name(key, state[0].n),
+                   "sample": f"per step: {threads} runs x {R} replicas x {sweeps} sweeps"},
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{threads} runs x 256 replicas x {sweeps} sweeps per step, one thread per run"},
+                         "sample": f"{threads} runs x {R} replicas x {sweeps} sweeps per step, one thread per run"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -460,7 +519,7 @@ def run_batched(args):
     if plain:
         tts["targets_plain"] = tts_summary(per_inst, plain["seconds"] / E / interval)
     line = {
-        "metric": "spin updates/sec and time-to-planted-ground-state (batched vs plain)",
+        "metric": METRIC,
         "value": upd_per_event * E / t_batched, "unit": UNIT, "n_gpus": 1, "steps": E,
         "warmup": 1, "ms_per_step": t_batched / E * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int8 spins, int32 fields, f32 decisions",
@@ -563,7 +622,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="n200", choices=["n200", "batched", "serving"])
+    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving"])
     ap.add_argument("--rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--drain", type=float, default=30.0)
@@ -571,6 +630,7 @@ def main():
     ap.add_argument("--pool-gb", type=int, default=16)
     ap.add_argument("--max-requests", type=int, default=1024)
     ap.add_argument("--instances", type=int, default=1024)
+    ap.add_argument("--runs", type=int, default=0, help="override the workload's run count")
     ap.add_argument("--tts-events", type=int, default=400)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
