@@ -186,7 +186,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup(n_gpus: int):
+def dist_setup(n_gpus: int, backend: str | None = None):
+    """One process per GPU under torchrun (RANK / WORLD_SIZE / MASTER_* from the
+    environment).  NCCL when CUDA is present, gloo otherwise (the CPU tests of
+    the multi-process path).  Returns (rank, world, torch.distributed or None)."""
     if n_gpus <= 1 or "RANK" not in os.environ:
         return 0, 1, None
     import torch
@@ -195,9 +198,30 @@ def dist_setup(n_gpus: int):
     rank = int(os.environ["RANK"])
     world = int(os.environ["WORLD_SIZE"])
     local = int(os.environ.get("LOCAL_RANK", rank))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl", init_method="env://")
+    if backend is None:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend, init_method="env://")
     return rank, world, dist
+
+
+def max_over_ranks(x: float, dist) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (runs are replicated per rank: weak scaling)."""
+    return units_per_rank * world / max_seconds
 
 
 def run_gpu(args):
@@ -238,10 +262,8 @@ def run_gpu(args):
         end.synchronize()
     torch.cuda.synchronize()
     elapsed_ms = start.elapsed_time(end)
+    elapsed_ms = max_over_ranks(elapsed_ms, dist)
     if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         dist.barrier()
     sweep_ms, sweep_launches = ctx.kernel_time(0)
     swap_ms, _ = ctx.kernel_time(1)
@@ -249,7 +271,7 @@ def run_gpu(args):
     sweep_ms -= ms0
     sweep_launches -= launches0
     swap_ms -= swap_ms0
-    value = updates_per_step * args.steps * world / (elapsed_ms / 1e3)
+    value = job_throughput(updates_per_step * args.steps, world, elapsed_ms / 1e3)
     # roofline of the sweep kernel
     peaks, peak_src = _peaks()
     avg_launch_ms = sweep_ms / max(sweep_launches, 1)
@@ -432,6 +454,8 @@ def run_batched(args):
     Times the batched persistent form against the one-instance-per-launch form
     on the same events (identical trajectories), then continues the batched
     form to `--tts-events` events for time-to-planted-ground-state."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # a one-GPU workload: under torchrun the other ranks do no work
     import torch
 
     import paper_2506_14781_gb300 as pt
@@ -545,6 +569,8 @@ def run_serving(args):
     until its bottom-right replica is feasible at the planted energy or 5 x 10^4
     sweeps.  Problems are drawn from 256 pre-generated instances, each request
     with its own seed, so instance generation stays out of the timed loop."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # a one-GPU workload: under torchrun the other ranks do no work
     import torch  # noqa: F401  (CUDA context for the library)
 
     import paper_2506_14781_gb300 as pt
