@@ -563,12 +563,15 @@ def run_batched(args):
 
 def run_serving(args):
     """Serving workload: a Poisson stream of constrained Ising requests at
-    `--rates` requests per minute for `--duration` seconds each.  A request is a
-    planted Wishart problem (N uniform on 50..800, alpha uniform on
-    [0.25, 0.75], <= 3 original edges per copy) with an I = 16 x J = 8 grid, run
-    until its bottom-right replica is feasible at the planted energy or 5 x 10^4
-    sweeps.  Problems are drawn from 256 pre-generated instances, each request
-    with its own seed, so instance generation stays out of the timed loop."""
+    `--rates` requests per minute for `--duration` seconds each, then up to
+    `--drain` seconds to finish what was admitted.  A request is a planted
+    Wishart problem (N uniform on 50..800, alpha uniform on [0.25, 0.75], <= 3
+    original edges per copy) with an I = 16 x J = 8 grid, run until its
+    bottom-right replica is feasible at the planted energy or 5 x 10^4 sweeps.
+    At most `--max-requests` requests are resident (they share the GPU in one
+    batched launch per step); the rest wait in FIFO order.  Problems are drawn
+    from 256 pre-generated instances, each request with its own seed, so
+    instance generation stays out of the timed loop."""
     if int(os.environ.get("RANK", "0")) != 0:
         return  # a one-GPU workload: under torchrun the other ranks do no work
     import torch  # noqa: F401  (CUDA context for the library)
@@ -583,22 +586,22 @@ def run_serving(args):
         phys = pt.sparsify(inst.Jq, "max_edges", 3)
         pool.append((inst, phys, synth.beta_ladder(16, BETA_MIN, BETA_MAX, inst.scale),
                      synth.penalty_ladder(8, P_MIN, P_MAX, 32767)))
+    max_sweeps, interval = 50000, 50
     results = []
     for rate in args.rates:
         arrivals = synth.poisson_arrivals(rate, args.duration, 5 + int(rate))
         rng = np.random.default_rng(int(rate))
         picks = rng.integers(0, len(pool), arrivals.size)
-        srv = pt.Server(args.pool_gb << 30, 3, args.max_requests, 50, args.events_per_step)
+        srv = pt.Server(args.pool_gb << 30, 3, args.max_requests, interval, args.events_per_step)
         ids = []
         t0 = time.perf_counter()
         nxt = 0
         steps = 0
-        updates = 0
         while True:
             now = time.perf_counter() - t0
             while nxt < arrivals.size and arrivals[nxt] <= now:
                 inst, phys, beta, P = pool[picks[nxt]]
-                ids.append((srv.submit(phys, beta, P, 77 + nxt, inst.E_planted, 50000), phys.n))
+                ids.append((srv.submit(phys, beta, P, 77 + nxt, inst.E_planted, max_sweeps), picks[nxt]))
                 nxt += 1
             if now > args.duration + args.drain:
                 break
@@ -609,23 +612,32 @@ def run_serving(args):
                     break
                 time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
         wall = time.perf_counter() - t0
-        lat, solved, done = [], 0, 0
-        for rid, n in ids:
+        lat, wait, service, rho, solved, done, updates = [], [], [], [], 0, 0, 0
+        for rid, k in ids:
             st = srv.status(rid)
+            inst, phys = pool[k][0], pool[k][1]
             if st["state"] == "done":
                 done += 1
                 lat.append(st["t_done"] - st["t_submit"])
+                wait.append(st["t_admit"] - st["t_submit"])
+                service.append(st["t_done"] - st["t_admit"])
                 solved += st["solved_event"] >= 0
-                updates += n * 128 * st["sweeps_done"]
+                updates += phys.n * 128 * st["sweeps_done"]
+                if st["best_event"] >= 0:
+                    rho.append((st["best_f"] - inst.E_planted) / (inst.N * inst.scale))
         srv.close()
-        lat = np.array(lat)
+
+        def pct(v, q):
+            return float(np.percentile(np.array(v), q)) if v else None
+
         results.append({
             "rate_per_min": rate, "submitted": len(ids), "completed": done, "solved": int(solved),
             "unfinished_at_end": len(ids) - done, "wall_s": wall, "steps": steps,
-            "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
-            "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
+            "p50_queue_wait_s": pct(wait, 50), "p50_service_s": pct(service, 50),
             "solves_per_s": solved / wall, "completed_per_s": done / wall,
             "spin_updates_per_s_completed": updates / wall,
+            "median_best_residual_per_spin": pct(rho, 50),
         })
     line = {
         "metric": "serving p50/p99 latency and solves/sec", "value": results[0]["solves_per_s"],
@@ -634,7 +646,8 @@ def run_serving(args):
                                "alpha~U[0.25,0.75], <=3 edges/copy, I=16 x J=8, stop at g=0 + "
                                "planted energy or 5e4 sweeps", "duration_s": args.duration,
                    "drain_s": args.drain, "events_per_step": args.events_per_step,
-                   "pool_gb": args.pool_gb, "max_resident": args.max_requests},
+                   "swap_interval": interval, "pool_gb": args.pool_gb,
+                   "max_resident": args.max_requests},
         "loads": results,
     }
     print(json.dumps(line))
@@ -654,7 +667,7 @@ def main():
     ap.add_argument("--drain", type=float, default=30.0)
     ap.add_argument("--events-per-step", type=int, default=20)
     ap.add_argument("--pool-gb", type=int, default=16)
-    ap.add_argument("--max-requests", type=int, default=1024)
+    ap.add_argument("--max-requests", type=int, default=128, help="serving: most resident requests")
     ap.add_argument("--instances", type=int, default=1024)
     ap.add_argument("--runs", type=int, default=0, help="override the workload's run count")
     ap.add_argument("--tts-events", type=int, default=400)

@@ -365,6 +365,47 @@ int pt2d_server_forget(pt2d_server *s, int64_t request_id);
 size_t pt2d_server_free_bytes(const pt2d_server *s);
 void pt2d_server_destroy(pt2d_server *s);
 
+/* ---- adaptive ladder schedule (Algorithm 2) ------------------------------- */
+/* Builds the beta and P ladders of a problem with the paper's adaptive schedule
+ * (Appendix, Algorithm 2), so that adjacent replicas swap at similar rates:
+ *   - the first column (penalty P0) adds rows from beta0, each one step
+ *     alpha_beta / sigma_E above the last, until a row's energy spread sigma_E
+ *     is <= sigma_min or max_rows rows exist; each row that steps proposes the
+ *     next penalty P0 + alpha_P / (beta sigma_g), and the next column takes the
+ *     median proposal rounded to an integer;
+ *   - every further column repeats the row walk from beta0 at its own penalty
+ *     (sigma_E floored at sigma_min), and the schedule stops after the column
+ *     whose coldest row has mean g < 1/2, at max_cols columns, or when no row
+ *     proposes a penalty (every population had sigma_g = 0);
+ *   - beta_i is the median over the columns of row i's beta.
+ * A population sample at (beta, P) is n_chain runs of a 1 x 1 context: mcs
+ * heat-bath sweeps from the INIT state (one event, no swap), then E = f + P g
+ * and g of each chain; sigma_E, sigma_g (divide by n_chain) and mean g come from
+ * exact integer sums rounded once to double.  Sample k (in drawing order) uses
+ * seed + k.  Every sample is a context on opt's stream and device (opt may be
+ * NULL), so the result is bit-reproducible and equal to a CPU restatement.
+ * Outputs: beta_out[max_rows] (I_out used), P_out[max_cols] (J_out used),
+ * samples_out (may be NULL): the number of population samples drawn.
+ * Errors: INVALID_ARG (parameters out of range: beta0, sigma_min, the alphas
+ * > 0 and finite, P0 >= 0, caps >= 1, n_chain >= 2, mcs >= 1; a penalty beyond
+ * int32), and any error of pt2d_create / pt2d_run / pt2d_read. */
+typedef struct pt2d_schedule_params {
+    double beta0;        /* first inverse temperature, in 1 / coupling units          */
+    int32_t P0;          /* penalty of the first column, coupling units              */
+    int32_t max_rows;    /* cap on I                                                 */
+    int32_t max_cols;    /* cap on J                                                 */
+    int32_t n_chain;     /* chains per population sample                             */
+    double sigma_min;    /* energy spread at which the first column stops adding rows */
+    double alpha_beta;   /* learning rate of the beta steps                          */
+    double alpha_P;      /* learning rate of the penalty steps                       */
+    int32_t mcs;         /* sweeps per population sample                             */
+    uint64_t seed;       /* sample k uses seed + k                                   */
+} pt2d_schedule_params;
+
+int pt2d_adaptive_schedule(const pt2d_instance *inst, const pt2d_schedule_params *prm,
+                           const pt2d_options *opt, float *beta_out, int32_t *I_out,
+                           int32_t *P_out, int32_t *J_out, int64_t *samples_out);
+
 /* ---- one-shot run without device allocation ------------------------------ */
 /* The paper has no counterpart to this entry point; it exists for callers that
  * cannot call cudaMalloc, for example a host program whose device memory is

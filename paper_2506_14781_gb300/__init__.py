@@ -452,6 +452,30 @@ class Server:
             pass
 
 
+def adaptive_schedule(inst: PhysicalInstance, *, beta0: float, P0: int, max_rows: int,
+                      max_cols: int, sigma_min: float, alpha_beta: float, alpha_P: float,
+                      n_chain: int, mcs: int, seed: int, stream=None, device: int = -1):
+    """Adaptive beta / P ladders of Algorithm 2 (pt2d_adaptive_schedule).
+    Returns (beta float32 [I], P int32 [J], population samples drawn)."""
+    prm = _lib.ScheduleParams(float(beta0), int(P0), int(max_rows), int(max_cols), int(n_chain),
+                              float(sigma_min), float(alpha_beta), float(alpha_P), int(mcs),
+                              int(seed) & ((1 << 64) - 1))
+    opt = _lib.Options()
+    _lib.lib().pt2d_default_options(C.byref(opt))
+    opt.device = int(device)
+    if stream is not None:
+        opt.stream = int(getattr(stream, "cuda_stream", stream))
+    beta = np.zeros(max(int(max_rows), 1), np.float32)
+    P = np.zeros(max(int(max_cols), 1), np.int32)
+    I, J, k = C.c_int32(), C.c_int32(), C.c_int64()
+    cs = inst.c_struct()
+    st = _lib.lib().pt2d_adaptive_schedule(
+        C.byref(cs), C.byref(prm), C.byref(opt), beta.ctypes.data_as(C.POINTER(C.c_float)),
+        C.byref(I), P.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(J), C.byref(k))
+    _lib.check(st, "pt2d_adaptive_schedule")
+    return beta[:I.value].copy(), P[:J.value].copy(), int(k.value)
+
+
 def _diag(name, arrays, outs, count):
     st = getattr(_lib.lib(), name)(*[_p(a) for a in arrays], *[_p(o) for o in outs], int(count))
     _lib.check(st, name)

@@ -38,6 +38,7 @@ EXPORTS = [
     "pt2d_batch_launch_count", "pt2d_batch_cuda_error", "pt2d_batch_destroy", "pt2d_batch_poll",
     "pt2d_server_create", "pt2d_server_submit", "pt2d_server_step", "pt2d_server_status",
     "pt2d_server_cancel", "pt2d_server_forget", "pt2d_server_free_bytes", "pt2d_server_destroy",
+    "pt2d_adaptive_schedule",
 ]
 
 
@@ -75,6 +76,21 @@ class BatchShape(C.Structure):
         ("storage", C.c_int32),
         ("global_width", C.c_int32),
         ("balance", C.c_int32),
+    ]
+
+
+class ScheduleParams(C.Structure):
+    _fields_ = [
+        ("beta0", C.c_double),
+        ("P0", C.c_int32),
+        ("max_rows", C.c_int32),
+        ("max_cols", C.c_int32),
+        ("n_chain", C.c_int32),
+        ("sigma_min", C.c_double),
+        ("alpha_beta", C.c_double),
+        ("alpha_P", C.c_double),
+        ("mcs", C.c_int32),
+        ("seed", C.c_uint64),
     ]
 
 
@@ -153,6 +169,9 @@ def lib():
         L.pt2d_batch_remove.argtypes = [vp, i64]
         L.pt2d_batch_run.argtypes = [vp, i32, i32]
         L.pt2d_batch_autotune.argtypes = [vp, i32, i32, C.POINTER(BatchShape)]
+        L.pt2d_adaptive_schedule.argtypes = [C.POINTER(Instance), C.POINTER(ScheduleParams), vp,
+                                             C.POINTER(C.c_float), C.POINTER(i32), C.POINTER(i32),
+                                             C.POINTER(i32), C.POINTER(C.c_int64)]
         L.pt2d_batch_get_shape.argtypes = [vp, C.POINTER(BatchShape)]
         L.pt2d_batch_set_shape.argtypes = [vp, C.POINTER(BatchShape)]
         L.pt2d_batch_read.argtypes = [vp, i64, i32, vp, sz]
