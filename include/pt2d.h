@@ -116,7 +116,18 @@ typedef struct {
                                 (2, 3: INVALID_ARG if it does not fit)               */
     int32_t walkers_per_thread; /* int8 shared-memory kernel: 4 or 8, others: 4;
                                    0 = automatic                                     */
+    int32_t swap_mode;       /* PT2D_SWAP_2D (0): Algorithm 1.  PT2D_SWAP_JCOLUMN (1):
+                                the paper's J-column PT baseline -- every event is a
+                                beta-swap event (pairs starting at the first row on
+                                odd events, the second on even ones), so replicas
+                                never change column (standard PT per column), and
+                                each event records the last row's replica of lowest
+                                g, then lowest f, then lowest column, instead of the
+                                bottom-right one (trace, best, solved)             */
 } pt2d_options;
+
+#define PT2D_SWAP_2D 0
+#define PT2D_SWAP_JCOLUMN 1
 
 typedef struct pt2d_ctx pt2d_ctx;
 

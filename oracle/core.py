@@ -123,6 +123,7 @@ class _OrcState(C.Structure):
         ("sum_f", C.c_void_p),
         ("sum_g", C.c_void_p),
         ("n_feasible", C.c_void_p),
+        ("mode", C.c_int64),
     ]
 
 
@@ -261,7 +262,11 @@ class OracleRun:
     """State of a set of independent 2D-PT runs (Algorithm 1) on one instance."""
 
     def __init__(self, oinst: OracleInstance, beta, P, run_ids, seed: int, trace_cap: int = 0,
-                 target=None, hist: bool = False, hist_slot: int = -1):
+                 target=None, hist: bool = False, hist_slot: int = -1, mode: int = 0):
+        """mode 0: 2D-PT (Algorithm 1).  mode 1: the J-column PT baseline -- every
+        event is a beta-swap event (odd / even pairs alternating), so replicas
+        never change column, and each event records the last row's replica of
+        lowest g, then lowest f, then lowest column."""
         self.oinst = oinst
         self.beta = np.ascontiguousarray(beta, dtype=np.float32)
         self.P = np.ascontiguousarray(P, dtype=np.int32)
@@ -304,7 +309,7 @@ class OracleRun:
                              _p(self.best_f), _p(self.best_event), _p(self.best_state),
                              _p(self.target), _p(self.solved_event), _p(self.acc_P), _p(self.acc_B),
                              _p(self.hist), self.hist_slot, _p(self.sum_f), _p(self.sum_g),
-                             _p(self.n_feasible))
+                             _p(self.n_feasible), int(mode))
 
     def run(self, sweeps: int, interval: int) -> None:
         rc = lib().orc_pt2d_run(self.oinst.ref, self.I, _p(self.beta), self.J, _p(self.P),

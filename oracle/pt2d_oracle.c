@@ -273,7 +273,26 @@ typedef struct {
     int64_t *sum_f;       /* [n_runs][I*J] per slot: sum of f after events     */
     int64_t *sum_g;       /* [n_runs][I*J] per slot: sum of g                   */
     int64_t *n_feasible;  /* [n_runs][I*J] per slot: count of g == 0            */
+    int64_t mode;         /* 0: 2D-PT (Algorithm 1); 1: J-column PT baseline    */
 } orc_state;
+
+/* The slot an event records.  2D-PT: the bottom-right replica (beta_I, P_J).
+ * J-column PT (standard PT repeated over J columns, the paper's comparison
+ * baseline, whose best feasible energy is picked among the J columns): the
+ * replica of the last row with the lowest g, then the lowest f, then the
+ * lowest column. */
+static int32_t orc_record_slot(int32_t I, int32_t J, const int32_t *at, const int64_t *fw,
+                               const int64_t *gw, int64_t mode)
+{
+    if (mode == 0) return I * J - 1;
+    int32_t best = (I - 1) * J;
+    for (int32_t j = 1; j < J; ++j) {
+        const int32_t s = (I - 1) * J + j;
+        const int64_t g = gw[at[s]], gb = gw[at[best]];
+        if (g < gb || (g == gb && fw[at[s]] < fw[at[best]])) best = s;
+    }
+    return best;
+}
 
 static void orc_swap_slots(int32_t *walker_at, int32_t sa, int32_t sb)
 {
@@ -347,7 +366,7 @@ int orc_pt2d_run(const orc_inst *in, int32_t I, const float *beta, int32_t J, co
         }
         st->counters[0] = 0;
         st->counters[1] = 0;
-        st->counters[2] = 1; /* swap_direction <- 1 */
+        st->counters[2] = st->mode ? -1 : 1; /* swap_direction <- 1 (J-column PT: beta-swaps only) */
         st->counters[3] = 1;
     }
 
@@ -374,8 +393,8 @@ int orc_pt2d_run(const orc_inst *in, int32_t I, const float *beta, int32_t J, co
             const int64_t *gw = st->g + (int64_t)q * R;
             orc_swap_event(I, beta, J, P, fw, gw, at, seed, run, nev, (int)st->counters[2],
                            st->acc_P + (int64_t)q * R, st->acc_B + (int64_t)q * R);
-            /* store spins from the last replica (bottom-right slot) */
-            const int32_t wl = at[R - 1];
+            /* store spins from the last replica (bottom-right slot; J-column PT: best of the last row) */
+            const int32_t wl = at[orc_record_slot(I, J, at, fw, gw, st->mode)];
             const int64_t fl = fw[wl], gl = gw[wl];
             if (st->trace_f && nev - 1 < st->trace_cap) {
                 st->trace_f[(int64_t)q * st->trace_cap + nev - 1] = fl;
@@ -405,7 +424,7 @@ int orc_pt2d_run(const orc_inst *in, int32_t I, const float *beta, int32_t J, co
         }
         st->counters[0] = t0 + interval;
         st->counters[1] = nev;
-        if (even) st->counters[2] = -st->counters[2];
+        if (even && !st->mode) st->counters[2] = -st->counters[2];
     }
     return 0;
 }

@@ -100,6 +100,9 @@ def greedy_color(inst: PhysicalInstance):
     return color, nc.value
 
 
+SWAP_MODES = {"2d": 0, "jcolumn": 1}
+
+
 class PT2D:
     """One 2D-PT context: `runs` independent I x J replica grids on one instance.
 
@@ -109,13 +112,15 @@ class PT2D:
     (int8 slab held in shared memory for a whole swap interval) or "bits"
     (bit-packed slab in shared memory, for instances whose int8 slab does not fit).
     stream: a torch.cuda.Stream, a raw cudaStream_t (int), or None (default stream).
+    swap_mode: "2d" (Algorithm 1) or "jcolumn" (the J-column PT baseline: beta-swaps
+    only, so each column is a standard PT; events record the best last-row replica).
     """
 
     def __init__(self, inst: PhysicalInstance, beta, P, runs: int, *, stream=None,
                  workspace: str = "library", trace_capacity: int = 1024,
                  walkers_per_cta: int = 0, threads_per_cta: int = 0, device: int = -1,
                  profile: bool = False, sweep_kernel: str = "auto",
-                 walkers_per_thread: int = 0):
+                 walkers_per_thread: int = 0, swap_mode: str = "2d"):
         self.inst = inst
         self.beta = np.ascontiguousarray(beta, dtype=np.float32)
         self.P = np.ascontiguousarray(P, dtype=np.int32)
@@ -134,6 +139,7 @@ class PT2D:
         opt.profile = 1 if profile else 0
         opt.sweep_kernel = {"auto": 0, "global": 1, "smem": 2, "bits": 3}[sweep_kernel]
         opt.walkers_per_thread = int(walkers_per_thread)
+        opt.swap_mode = SWAP_MODES[swap_mode]
         self._stream_obj = stream
         if stream is not None:
             opt.stream = int(getattr(stream, "cuda_stream", stream))
@@ -264,7 +270,7 @@ class Batch:
     def __init__(self, pool_bytes: int, max_coupling_degree: int = 3, max_runs: int = 4096, *,
                  stream=None, trace_capacity: int = 1024, threads_per_cta: int = 0,
                  spins_in_global: bool = False, sweep_kernel: str = "auto",
-                 walkers_per_cta: int = 0, device: int = -1):
+                 walkers_per_cta: int = 0, swap_mode: str = "2d", device: int = -1):
         """sweep_kernel: where a run's spins live during an event -- "auto" (int8
         in shared memory, else bit-packed in shared memory, else global memory),
         "global", "smem" (no bit-packed slabs) or "bits" (no int8 shared-memory
@@ -276,6 +282,7 @@ class Batch:
         opt.threads_per_cta = int(threads_per_cta)
         opt.sweep_kernel = 1 if spins_in_global else {"auto": 0, "global": 1, "smem": 2, "bits": 3}[sweep_kernel]
         opt.walkers_per_cta = int(walkers_per_cta)
+        opt.swap_mode = SWAP_MODES[swap_mode]
         opt.device = int(device)
         self._stream_obj = stream
         if stream is not None:
@@ -386,13 +393,14 @@ class Server:
     def __init__(self, pool_bytes: int, max_coupling_degree: int = 3, max_requests: int = 1024,
                  swap_interval: int = 50, events_per_step: int = 10, *, stream=None,
                  threads_per_cta: int = 0, spins_in_global: bool = False,
-                 sweep_kernel: str = "auto", device: int = -1):
-        """sweep_kernel / spins_in_global: slab storage, as for Batch."""
+                 sweep_kernel: str = "auto", swap_mode: str = "2d", device: int = -1):
+        """sweep_kernel / spins_in_global: slab storage; swap_mode: as for Batch."""
         L = _lib.lib()
         opt = _lib.Options()
         L.pt2d_default_options(C.byref(opt))
         opt.threads_per_cta = int(threads_per_cta)
         opt.sweep_kernel = 1 if spins_in_global else {"auto": 0, "global": 1, "smem": 2, "bits": 3}[sweep_kernel]
+        opt.swap_mode = SWAP_MODES[swap_mode]
         opt.device = int(device)
         self._stream_obj = stream
         if stream is not None:

@@ -67,6 +67,7 @@ class Options(C.Structure):
         ("profile", C.c_int32),
         ("sweep_kernel", C.c_int32),
         ("walkers_per_thread", C.c_int32),
+        ("swap_mode", C.c_int32),
     ]
 
 

@@ -67,7 +67,7 @@ __device__ void run_swap(const BatchArgs &a, const BatchRun &d, int run_index, u
     }
     __syncthreads();
     swap_pairs(s_at, [&](int w) { return s_f[w]; }, [&](int w) { return s_g[w]; }, s_beta, s_P, I, J,
-               static_cast<uint32_t>(d.run), nev, event_is_pswap(nev), d.k0, d.k1, acc_P, acc_B);
+               static_cast<uint32_t>(d.run), nev, event_dir_p(nev, d.swap_mode), d.k0, d.k1, acc_P, acc_B);
     __syncthreads();
     for (int w = threadIdx.x; w < Rp; w += blockDim.x) {  // pad walkers keep beta = 0, P = 0
         w_beta[w] = 0.0f;
@@ -89,7 +89,8 @@ __device__ void run_swap(const BatchArgs &a, const BatchRun &d, int run_index, u
             sc[kScBestEvent] = -1;
             sc[kScSolvedEvent] = -1;
         }
-        const int wl = s_at[R - 1];
+        const int wl = s_at[record_slot(s_at, [&](int w) { return s_f[w]; }, [&](int w) { return s_g[w]; },
+                                        I, J, d.swap_mode)];
         const long long fl = s_f[wl];
         const int gl = s_g[wl];
         if (nev - 1 < d.trace_cap) {

@@ -43,6 +43,8 @@ struct BatchRun {
     int32_t nslab;       // Rp / sw
     int32_t mode;        // slab spins: 0 int8 in global memory, 1 int8 in shared memory,
                          // 2 bit-packed in shared memory
+    int32_t swap_mode;   // PT2D_SWAP_2D or PT2D_SWAP_JCOLUMN
+    int32_t pad2;
     int64_t work;        // n * Rp, for ordering
 };
 

@@ -159,6 +159,7 @@ struct pt2d_batch {
     std::vector<std::pair<int64_t, int32_t>> order;  // run array order: (id, run)
     int32_t n_items = 0;
     int glob_sw = 32;                                 // slab width when spins stay in global memory
+    int swap_mode = 0;                                // PT2D_SWAP_2D or PT2D_SWAP_JCOLUMN, all problems
     int storage = 0;                                  // pt2d_batch_shape::storage
     int balance = 2;                                  // pt2d_batch_shape::balance
     bool int8 = true;                                 // int8 shared-memory slabs allowed
@@ -393,6 +394,11 @@ int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_
     b->grid = sms > 0 ? sms : 152;
     b->smem_state_max = std::max(0, smem_optin - static_cast<int>(pt2d::batch_small_smem_bytes()) - 1024);
     b->smem_state_max &= ~15;
+    if (opt->swap_mode != PT2D_SWAP_2D && opt->swap_mode != PT2D_SWAP_JCOLUMN) {
+        delete b;
+        return PT2D_ERR_INVALID_ARG;
+    }
+    b->swap_mode = opt->swap_mode;
     {
         const pt2d_batch_shape shape{b->threads, opt->sweep_kernel,
                                      opt->walkers_per_cta ? opt->walkers_per_cta : 32, 2};
@@ -495,6 +501,7 @@ int pt2d_batch_add(pt2d_batch *b, const pt2d_instance *inst, int32_t I, const fl
     std::vector<int64_t> scal(static_cast<size_t>(runs) * pt2d::kScCount, 0);
     for (int32_t r = 0; r < runs; ++r) {
         pt2d::BatchRun d{};
+        d.swap_mode = b->swap_mode;
         const size_t rb = in.off + l.run0 + l.run_stride * r;
         d.state = static_cast<int64_t>(rb + l.state);
         d.rec = static_cast<int64_t>(in.off + l.rec);
@@ -746,7 +753,8 @@ int pt2d_batch_read(pt2d_batch *b, int64_t id, int32_t what, void *dst, size_t b
             case PT2D_COUNTERS: {
                 if (r == 0) {
                     const int64_t ev = sc[pt2d::kScEvents];
-                    int64_t v[4] = {sc[pt2d::kScSweeps], ev, ((ev / 2) % 2 == 0) ? 1 : -1, sc[pt2d::kScInited]};
+                    const int64_t dir = b->swap_mode ? -1 : (((ev / 2) % 2 == 0) ? 1 : -1);
+                    int64_t v[4] = {sc[pt2d::kScSweeps], ev, dir, sc[pt2d::kScInited]};
                     std::memcpy(dst, v, sizeof v);
                 }
                 break;

@@ -213,6 +213,8 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     }
     const int mode = opt ? opt->sweep_kernel : 0;
     if (mode < 0 || mode > 3) return PT2D_ERR_INVALID_ARG;
+    if (opt && opt->swap_mode != PT2D_SWAP_2D && opt->swap_mode != PT2D_SWAP_JCOLUMN)
+        return PT2D_ERR_INVALID_ARG;
     const bool specialised = DL == 2 && (DC == 3 || DC == 4 || DC == 6);
     const int64_t walkers = static_cast<int64_t>(runs) * pp.Rp;
     auto fits = [&](int sw) {
@@ -519,6 +521,7 @@ int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const floa
     c->rs.P = c->d_P;
     c->rs.trace_cap = pp.trace_cap;
     c->rs.target = c->d_target;
+    c->rs.swap_mode = opt->swap_mode;
     cudaStream_t s = c->stream;
     auto fail = [&](cudaError_t e) {
         c->last_cuda = static_cast<int>(e);
@@ -606,7 +609,7 @@ int pt2d_run(pt2d_ctx *c, int64_t sweeps, int32_t interval, uint64_t seed) {
         CK(c, pt2d::launch_init(c->L, c->rs, c->wk, seed, s));
         c->launches += 2;
         c->inited = 1;
-        c->dir = 1;
+        c->dir = c->rs.swap_mode ? -1 : 1;
         c->sweeps_done = 0;
         c->events_done = 0;
     }
@@ -633,7 +636,7 @@ int pt2d_run(pt2d_ctx *c, int64_t sweeps, int32_t interval, uint64_t seed) {
         c->launches += 2;
         c->sweeps_done += interval;
         c->events_done = event;
-        if (event % 2 == 0) c->dir = -c->dir;
+        if (event % 2 == 0 && !c->rs.swap_mode) c->dir = -c->dir;
     }
     return PT2D_OK;
 }

@@ -58,6 +58,7 @@ struct RunState {
     int8_t *best_state;     // [runs][n]
     const int64_t *target;  // [runs]
     int64_t *solved_event;  // [runs]
+    int32_t swap_mode;      // PT2D_SWAP_2D or PT2D_SWAP_JCOLUMN
 };
 
 struct SweepTiling {

@@ -449,7 +449,8 @@ __global__ void k_swap_event(Layout L, RunState rs, Walkers wk, uint32_t k0, uin
         rs.n_feasible[rb + s] += (gw == 0);
     }
     if (threadIdx.x == 0) {
-        const int wl = at[R - 1];
+        const int wl = at[record_slot(at, [&](int w) { return static_cast<long long>(wk.f[cb + w]); },
+                                      [&](int w) { return wk.g[cb + w]; }, I, J, rs.swap_mode)];
         const long long fl = wk.f[cb + wl];
         const int gl = wk.g[cb + wl];
         if (nev - 1 < rs.trace_cap) {
@@ -616,7 +617,8 @@ cudaError_t launch_swap_event(const Layout &L, const RunState &rs, const Walkers
     // Algorithm 1: direction +1 (P-swaps) for events 1, 2, then -1 (beta-swaps) for
     // 3, 4, ...: the direction flips after every even event; odd events use the
     // pairs starting at the first replica, even events those starting at the second.
-    const int dir_p = event_is_pswap(event);
+    // The J-column PT baseline swaps along beta at every event.
+    const int dir_p = event_dir_p(event, rs.swap_mode);
     const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
     k_swap_event<<<rs.runs, 256, sizeof(int) * rs.R, st>>>(L, rs, wk, k0, k1, event, dir_p);
     return cudaGetLastError();

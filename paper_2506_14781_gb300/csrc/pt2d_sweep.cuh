@@ -172,6 +172,21 @@ __device__ __forceinline__ uint32_t word_of_bits(uint32_t nib) {
     return w;
 }
 
+// The slot an event records: the bottom-right replica (beta_I, P_J) in 2D-PT
+// (swap_mode 0); in the J-column PT baseline (swap_mode 1) the last row's
+// replica of lowest g, then lowest f, then lowest column.
+template <typename FW, typename GW>
+__device__ __forceinline__ int record_slot(const int *at, FW fw, GW gw, int I, int J, int swap_mode) {
+    if (swap_mode == 0) return I * J - 1;
+    int best = (I - 1) * J;
+    for (int j = 1; j < J; ++j) {
+        const int s = (I - 1) * J + j;
+        const long long g = gw(at[s]), gb = gw(at[best]);
+        if (g < gb || (g == gb && fw(at[s]) < fw(at[best]))) best = s;
+    }
+    return best;
+}
+
 // The pair loop of one swap event of Algorithm 1 for one run, by the calling
 // CTA's threads (pairs of one event are disjoint, so they run in parallel).
 // at: slot -> walker (shared memory, permuted in place); fw / gw: f and g by
@@ -231,6 +246,12 @@ __device__ __forceinline__ void swap_pairs(int *at, FW fw, GW gw, const float *b
 // 3, 4, and so on, flipping after every even event.
 __host__ __device__ __forceinline__ int event_is_pswap(int64_t nev) {
     return ((nev - 1) / 2) % 2 == 0 ? 1 : 0;
+}
+
+// Swap direction of event n: P-swaps (1) or beta-swaps (0); the J-column PT
+// baseline (swap_mode 1) swaps along beta at every event.
+__host__ __device__ __forceinline__ int event_dir_p(int64_t nev, int swap_mode) {
+    return swap_mode == 0 ? event_is_pswap(nev) : 0;
 }
 
 }  // namespace pt2d

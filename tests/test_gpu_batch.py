@@ -42,8 +42,9 @@ def _problem(pt, N, alpha, seed, rule, I, J, runs):
                 target=inst.E_planted)
 
 
-def _plain(pt, pr, sweeps, interval, trace):
-    ctx = pt.PT2D(pr["phys"], pr["beta"], pr["P"], pr["runs"], trace_capacity=trace)
+def _plain(pt, pr, sweeps, interval, trace, swap_mode="2d"):
+    ctx = pt.PT2D(pr["phys"], pr["beta"], pr["P"], pr["runs"], trace_capacity=trace,
+                  swap_mode=swap_mode)
     ctx.write(pt.TARGET, np.full(pr["runs"], pr["target"], np.int64))
     ctx.run(sweeps, interval, pr["seed"])
     return ctx
@@ -129,6 +130,22 @@ def test_batch_shape_changes_between_launches(pt):
     for pr, bid in zip(probs, ids):
         ctx = _plain(pt, pr, 24, 3, 8)
         _assert_same(pt, batch, bid, ctx)
+        ctx.close()
+    batch.close()
+
+
+@pytest.mark.parametrize("kernel", ["auto", "global"])
+def test_batch_jcolumn_baseline_matches_plain(pt, kernel):
+    probs = _mixed(pt)[:5]
+    batch = pt.Batch(1 << 29, max_coupling_degree=3, max_runs=64, trace_capacity=16,
+                     sweep_kernel=kernel, swap_mode="jcolumn")
+    ids = [batch.add(p["phys"], p["beta"], p["P"], p["runs"], p["seed"], p["target"]) for p in probs]
+    batch.run(3, 5)
+    batch.run(4, 5)
+    for pr, bid in zip(probs, ids):
+        ctx = _plain(pt, pr, 35, 5, 16, swap_mode="jcolumn")
+        _assert_same(pt, batch, bid, ctx)
+        assert batch.read(bid, pt.ACC_P).sum() == 0
         ctx.close()
     batch.close()
 

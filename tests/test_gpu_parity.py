@@ -55,16 +55,17 @@ def assert_same(pt, ctx, orc, runs_sel=None, trace=True):
 
 
 def both(pt, inst_q, Jrule, beta, P, runs, seed, schedule, *, target=None, trace=64, wpc=0,
-         threads=0, phys=None, kernel="auto", wpt=0):
+         threads=0, phys=None, kernel="auto", wpt=0, swap_mode="2d"):
     if phys is None:
         phys_p = pt.sparsify(inst_q.Jq, *Jrule)
         phys_o = oracle.sparsify(inst_q.Jq, *Jrule)
     else:
         phys_p, phys_o = phys
     ctx = pt.PT2D(phys_p, beta, P, runs, trace_capacity=trace, walkers_per_cta=wpc,
-                  threads_per_cta=threads, sweep_kernel=kernel, walkers_per_thread=wpt)
+                  threads_per_cta=threads, sweep_kernel=kernel, walkers_per_thread=wpt,
+                  swap_mode=swap_mode)
     orc = oracle.OracleRun(oracle.OracleInstance(phys_o), beta, P, list(range(runs)), seed,
-                           trace_cap=trace, target=target)
+                           trace_cap=trace, target=target, mode=pt.SWAP_MODES[swap_mode])
     if target is not None:
         ctx.write(pt.TARGET, np.full(runs, target, np.int64))
     for sweeps, interval in schedule:
@@ -294,6 +295,29 @@ def test_torch_stream_and_workspace(pt, tiny_config):
     b.run(300, 3, 77)
     for what, _ in ARRAYS:
         assert np.array_equal(a.read(getattr(pt, what)), b.read(getattr(pt, what))), what
+
+
+# ---- the J-column PT baseline ----------------------------------------------------------
+@pytest.mark.parametrize("kernel,wpc", [("global", 16), ("smem", 16), ("bits", 8), ("auto", 0)])
+def test_jcolumn_baseline_bit_exact(pt, kernel, wpc):
+    """Beta-swaps only, equal penalties in every column (the paper's comparison:
+    J standard PTs at the mean 2D-PT penalty), best last-row record."""
+    inst = synth.wishart_planted(30, 0.5, 21)
+    beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
+    P_2d = synth.penalty_ladder(3, 0.5, 4.0, 32767)
+    P = np.full(3, int(np.rint(P_2d.mean())), np.int32)
+    ctx, orc = both(pt, inst, ("max_edges", 3), beta, P, 7, 0xABCDEF, [(35, 7), (21, 7)],
+                    target=inst.E_planted, wpc=wpc, kernel=kernel, swap_mode="jcolumn")
+    assert_same(pt, ctx, orc)
+    assert ctx.read(pt.ACC_P).sum() == 0 and ctx.read(pt.COUNTERS)[2] == -1
+
+
+def test_jcolumn_tiny_config_bit_exact(pt, tiny_config):
+    cfg = tiny_config
+    P = np.full(4, int(np.rint(cfg["P"].mean())), np.int32)
+    ctx, orc = both(pt, cfg["inst"], ("fixed", 2), cfg["beta"], P, 2, 7, [(3000, 1)],
+                    target=cfg["inst"].E_planted, trace=128, swap_mode="jcolumn")
+    assert_same(pt, ctx, orc)
 
 
 # ---- full-size configurations, checked on samples the oracle computes -----------------

@@ -38,12 +38,12 @@ def _exact_slot_stats(phys, beta, P):
     return out
 
 
-def _stationarity_z(phys, beta, P, runs=24, sweeps=4000, burn_in=500, seed=7):
+def _stationarity_z(phys, beta, P, runs=24, sweeps=4000, burn_in=500, seed=7, mode=0):
     """Largest |z| over slots of (mean f, mean g, feasible fraction), with the
     standard error taken from the spread over independent runs (after a
     burn-in whose samples are discarded)."""
     oi = oracle.OracleInstance(phys)
-    run = oracle.OracleRun(oi, beta, P, list(range(runs)), seed=seed)
+    run = oracle.OracleRun(oi, beta, P, list(range(runs)), seed=seed, mode=mode)
     run.run(burn_in, 1)
     for a in (run.sum_f, run.sum_g, run.n_feasible):
         a[...] = 0
@@ -206,3 +206,46 @@ def test_stats_match_definitions(tiny_config):
             Ep = oi.cost_f(sp) + Pj * oi.constraint_g(sp)
             Em = oi.cost_f(sm) + Pj * oi.constraint_g(sm)
             assert oi.local_field(s, a, Pj) == Em - Ep
+
+
+# ---- J-column PT baseline (mode 1): standard PT in every column --------------------
+def test_jcolumn_stationarity(tiny_config):
+    """Beta-swaps alone inside each column keep every slot's Boltzmann
+    distribution at its (beta_i, P_j)."""
+    z = _stationarity_z(tiny_config["phys"], tiny_config["beta"], tiny_config["P"], mode=1)
+    assert z < 5.0, z
+
+
+def test_jcolumn_mistake_fails_stationarity(tiny_config, tmp_path):
+    old, new = MUTATIONS["bswap_sign"]
+    src = open(_build.SRC).read()
+    path = _build.compile_variant(src.replace(old, new), str(tmp_path / "liboracle_jc.so"))
+    with core.use_library(path):
+        z = _stationarity_z(tiny_config["phys"], tiny_config["beta"], tiny_config["P"],
+                            runs=8, sweeps=2000, burn_in=200, mode=1)
+    assert z > 8.0, z
+
+
+def test_jcolumn_invariants_and_record(tiny_config):
+    """Replicas never leave their column, no P-swap is ever made, every event
+    swaps along beta with alternating pair parity, and each event records the
+    last-row replica of lowest (g, f), first column on ties."""
+    phys = tiny_config["phys"]
+    oi = oracle.OracleInstance(phys)
+    I = J = 4
+    beta = np.cumsum(np.full(I, 1e-9, dtype=np.float32)).astype(np.float32)  # hot: swaps accepted
+    P = np.array([1, 2, 3, 4], dtype=np.int32)
+    run = oracle.OracleRun(oi, beta, P, [0, 1], seed=3, trace_cap=64, mode=1)
+    for ev in range(1, 41):
+        accB0 = run.acc_B.copy()
+        run.run(1, 1)
+        assert run.counters[2] == -1 and run.acc_P.sum() == 0
+        dB = (run.acc_B - accB0).reshape(2, I, J).sum(axis=(0, 2))
+        rows = np.nonzero(dB)[0]
+        assert len(rows) > 0 and all(r % 2 == (ev + 1) % 2 for r in rows)
+        assert np.all(run.walker_at % J == np.arange(I * J) % J)
+        for q in range(2):
+            last = run.walker_at[q, (I - 1) * J:]
+            keys = [(run.g[q, w], run.f[q, w], j) for j, w in enumerate(last)]
+            g, f, _ = min(keys)
+            assert (run.trace_f[q, ev - 1], run.trace_g[q, ev - 1]) == (f, g)
