@@ -561,6 +561,164 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+def run_compare(args):
+    """2D-PT against the J-column PT baseline (the paper's Fig. 3 comparison
+    shape) on synthetic planted Wishart instances: N in {20, 30, 40, 50},
+    alpha = 0.75, three copies per node, I = 16 x J = 8.  2D-PT uses a linear P
+    ladder; J-column PT runs the same beta ladder in every column at the mean
+    of those penalties, with beta-swaps only, and keeps the best feasible
+    replica of its last row.  Both run as one batch each, `--cmp-events`
+    events of 50 sweeps; reported: the median over instances of the residual
+    energy per spin of the best feasible state so far, rho = (f - E_gs) / (N s),
+    at log-spaced sweep counts, and the sweeps to reach rho <= 0.2 / 0.1 /
+    0.05 / 0 (E_gs: the planted energy or anything lower either method found)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # a one-GPU workload: under torchrun the other ranks do no work
+    import torch
+
+    import paper_2506_14781_gb300 as pt
+    import synth
+
+    I, J, interval, E = 16, 8, 50, args.cmp_events
+    per_N = args.cmp_instances
+    Ns = (20, 30, 40, 50)
+    probs = []
+    for N in Ns:
+        for k in range(per_N):
+            inst = synth.wishart_planted(N, 0.75, 5000 + 100 * N + k)
+            phys = pt.sparsify(inst.Jq, "fixed", 3)
+            probs.append((inst, phys, synth.beta_ladder(I, BETA_MIN, BETA_MAX, inst.scale),
+                          synth.penalty_ladder(J, P_MIN, P_MAX, 32767)))
+    stream = torch.cuda.Stream()
+    out = {}
+    traces = {}
+    for mode in ("2d", "jcolumn"):
+        b = pt.Batch(1 << 30, 3, len(probs), stream=stream, trace_capacity=E, swap_mode=mode)
+        ids = []
+        for k, (inst, phys, beta, P) in enumerate(probs):
+            Pm = P if mode == "2d" else np.full(J, int(np.rint(P.mean())), np.int32)
+            ids.append(b.add(phys, beta, Pm, 1, 777 + k, inst.E_planted))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(E, interval)
+        e1.record(stream)
+        e1.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        tf = np.stack([b.read(i, pt.TRACE_F)[0] for i in ids])
+        tg = np.stack([b.read(i, pt.TRACE_G)[0] for i in ids])
+        traces[mode] = (tf, tg)
+        out[mode] = {"seconds": secs, "feasible_record_fraction": float((tg == 0).mean())}
+        b.close()
+    # ground-state estimate per instance: the planted energy or anything lower found
+    big = np.iinfo(np.int64).max
+    E_gs = []
+    for k, (inst, _, _, _) in enumerate(probs):
+        found = min(int(np.where(traces[m][1][k] == 0, traces[m][0][k], big).min()) for m in traces)
+        E_gs.append(min(int(inst.E_planted), found))
+    E_gs = np.array(E_gs)
+    norm = np.array([inst.N * inst.scale for inst, _, _, _ in probs])
+    checkpoints = sorted({int(x) for x in np.unique(np.round(np.geomspace(1, E, 12)))})
+    Narr = np.array([inst.N for inst, _, _, _ in probs])
+    for mode, (tf, tg) in traces.items():
+        best = np.minimum.accumulate(np.where(tg == 0, tf, big), axis=1)
+        rho = np.where(best < big, (best - E_gs[:, None]) / norm[:, None], np.inf)
+        curve = {}
+        for N in Ns:
+            sel = Narr == N
+            curve[str(N)] = {str(c * interval): float(np.median(rho[sel, c - 1])) for c in checkpoints}
+        tts = {}
+        for target in (0.2, 0.1, 0.05, 0.0):
+            hit = rho <= target + 1e-12
+            first = np.where(hit.any(1), hit.argmax(1) + 1, -1) * interval
+            tts[f"rho<={target}"] = {str(N): {"reached": int((first[Narr == N] > 0).sum()),
+                                              "of": int((Narr == N).sum()),
+                                              "median_sweeps": float(np.median(first[(Narr == N) & (first > 0)]))
+                                              if ((Narr == N) & (first > 0)).any() else None}
+                                     for N in Ns}
+        out[mode].update({"median_rho_by_sweeps": curve, "sweeps_to_target": tts})
+    line = {
+        "metric": "residual energy per spin vs sweeps, 2D-PT vs J-column PT (same replicas)",
+        "value": None, "unit": "rho", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+        "config": {"workload": f"{per_N} planted Wishart instances per N in {list(Ns)}, alpha 0.75, "
+                               f"3 copies per node, I={I} x J={J}, {E} events of {interval} sweeps; "
+                               "J-column PT at the mean 2D-PT penalty"},
+        "results": out,
+    }
+    print(json.dumps(line))
+
+
+def run_fig2(args):
+    """The paper's Fig. 2 experiment shape: a 5-node all-to-all instance with two
+    copies per node (10 physical spins, physical degree 3), one row at beta = 1,
+    penalties P in {2, 4, 6, 8} with P-swaps every 500 sweeps, against the P = 8
+    replica alone; 100 chains each.  The Full Adder couplings are not given, so
+    the instance is seeded with couplings in {+-1, +-2, +-3}.  The last
+    replica's state is sampled after every 500-sweep event; its feasible (g = 0)
+    samples map to logical states (first copy of each chain), and the KL
+    divergence D(p_hat || p) to the exact 5-node Boltzmann distribution at
+    beta = 1 is reported against sweeps, per chain (mean over chains) and pooled
+    over the chains."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # a one-GPU workload: under torchrun the other ranks do no work
+    import torch  # noqa: F401  (CUDA context for the library)
+
+    import paper_2506_14781_gb300 as pt
+
+    rng = np.random.default_rng(3)
+    A = rng.integers(1, 4, size=(5, 5)) * rng.choice([-1, 1], size=(5, 5))
+    Jq = np.triu(A, 1)
+    Jq = (Jq + Jq.T).astype(np.int16)
+    phys = pt.sparsify(Jq, "fixed", 2)
+    # exact logical Boltzmann distribution at beta = 1: f(s) = -sum_{i<j} J_ij s_i s_j
+    states = np.array([[1 - 2 * ((k >> i) & 1) for i in range(5)] for k in range(32)])
+    f_log = -0.5 * np.einsum("ki,ij,kj->k", states, Jq.astype(np.int64), states)
+    w = np.exp(-(f_log - f_log.min()))
+    p_exact = w / w.sum()
+    first = np.array([int(np.nonzero(phys.copy_of == i)[0].min()) for i in range(5)])
+    chains, interval, events = 100, 500, args.fig2_events
+    checkpoints = sorted({int(x) for x in np.unique(np.round(np.geomspace(1, events, 16)))})
+    out = {}
+    for arm, P in (("with_P_swaps", np.array([2, 4, 6, 8], np.int32)),
+                   ("P8_alone", np.array([8], np.int32))):
+        ctx = pt.PT2D(phys, np.array([1.0], np.float32), P, chains, trace_capacity=0)
+        counts = np.zeros((chains, 32), np.int64)
+        curve_chain, curve_pooled = {}, {}
+        for e in range(1, events + 1):
+            ctx.run(interval, interval, 2024)
+            at = ctx.read(pt.WALKER_AT)[:, -1]
+            S = ctx.read(pt.STATES)            # [chains][R][n], by walker
+            s_last = S[np.arange(chains), at]  # the last slot's state per chain
+            g = np.zeros(chains, np.int64)
+            for a in range(phys.n):
+                for k in range(phys.lk_ptr[a], phys.lk_ptr[a + 1]):
+                    g += s_last[:, a] != s_last[:, phys.lk_col[k]]
+            feas = g == 0
+            idx = ((s_last[:, first] < 0).astype(np.int64) << np.arange(5)).sum(1)
+            np.add.at(counts, (np.nonzero(feas)[0], idx[feas]), 1)
+            if e in checkpoints:
+                def kl(c):
+                    q = c / max(c.sum(), 1)
+                    m = q > 0
+                    return float((q[m] * np.log(q[m] / p_exact[m])).sum()) if c.sum() else None
+                per = [kl(counts[c]) for c in range(chains)]
+                per = [x for x in per if x is not None]
+                curve_chain[str(e * interval)] = float(np.mean(per)) if per else None
+                curve_pooled[str(e * interval)] = kl(counts.sum(0))
+        ctx.close()
+        out[arm] = {"kl_mean_over_chains": curve_chain, "kl_pooled": curve_pooled,
+                    "feasible_fraction": float(counts.sum() / (chains * events))}
+    line = {
+        "metric": "KL divergence of the last replica vs sweeps (Fig. 2 shape)", "value": None,
+        "unit": "nats", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+        "config": {"workload": "seeded 5-node all-to-all instance, 2 copies per node (10 spins), "
+                               f"beta = 1, P in {{2,4,6,8}} vs P = 8 alone, {chains} chains, "
+                               f"swap every {interval} sweeps, {events} events, one sample per event"},
+        "results": out,
+    }
+    print(json.dumps(line))
+
+
 def run_serving(args):
     """Serving workload: a Poisson stream of constrained Ising requests at
     `--rates` requests per minute for `--duration` seconds each, then up to
@@ -661,7 +819,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving"])
+    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2"])
+    ap.add_argument("--fig2-events", type=int, default=8000)
+    ap.add_argument("--cmp-events", type=int, default=2000)
+    ap.add_argument("--cmp-instances", type=int, default=64)
     ap.add_argument("--rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--drain", type=float, default=30.0)
@@ -682,6 +843,10 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "compare":
+        run_compare(args)
+    elif args.workload == "fig2":
+        run_fig2(args)
     else:
         run_gpu(args)
 

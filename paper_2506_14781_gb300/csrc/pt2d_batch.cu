@@ -128,8 +128,8 @@ template <int DC, int DL, typename Fetch, typename FetchLink, typename Store>
 __device__ __forceinline__ void slab_sweeps(const BatchArgs &a, const BatchRun &d, const int4 *rec,
                                             const int32_t *cofs, const Quad &q, Fetch fetch,
                                             FetchLink fetch_link, Store store, int grp, int G,
-                                            uint32_t lq, int64_t sweeps_done) {
-    const KeysBase keys{d.k0, d.k1};
+                                            uint32_t lq, int64_t sweeps_done, const uint4 *round_keys) {
+    const KeysShared keys{round_keys};
     const uint32_t c3 = (static_cast<uint32_t>(d.run) << 4) | kTagSweep;
     for (int t = 0; t < a.interval; ++t) {
         const uint32_t sweep = static_cast<uint32_t>(sweeps_done + t);
@@ -259,6 +259,8 @@ __device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm)
     uint8_t *small = dsm + a.smem_state;
     long long *s_F = reinterpret_cast<long long *>(small);
     int *s_G = reinterpret_cast<int *>(s_F + kMaxR);
+    __shared__ uint4 s_keys[5];  // the run's Philox round keys, visible after the next barrier
+    stage_round_keys(s_keys, d.k0, d.k1);
 
     if (d.mode == 2) {
         const int B = SW >> 3;
@@ -293,7 +295,7 @@ __device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm)
             const uint32_t other = __shfl_xor_sync(pair, nib, 1);
             if ((lane_q & 1) == 0) bits[pos * B + byte_lane] = static_cast<uint8_t>(nib | (other << 4));
         };
-        slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch_link, store, grp, G, lq, sweeps_done);
+        slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch_link, store, grp, G, lq, sweeps_done, s_keys);
         const int64_t nout = static_cast<int64_t>(n) * B;  // rows 0..n-1 back as int8 spins
         for (int64_t i = threadIdx.x; i < nout; i += blockDim.x) {
             const int64_t row = i / B;
@@ -337,7 +339,7 @@ __device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm)
         auto store = [&](int pos, uint32_t w) {
             *reinterpret_cast<uint32_t *>(S + pos * stride + lane_off) = w;
         };
-        slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch, store, grp, G, lq, sweeps_done);
+        slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch, store, grp, G, lq, sweeps_done, s_keys);
         if (smem) {  // write the slab back (rows 0..n, the zero row included)
             const int vec = SW >> 4;
             const int64_t nvec = static_cast<int64_t>(n + 1) * vec;

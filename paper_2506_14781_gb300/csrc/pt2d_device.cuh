@@ -21,14 +21,19 @@ constexpr uint32_t kWeyl1 = 0xBB67AE85u;  // 2^32 * (sqrt(3) - 1)
 
 enum : uint32_t { kTagInit = 0u, kTagSweep = 1u, kTagSwap = 2u };
 
+// One Philox4x32 round with round key (k0, k1).
+__device__ __forceinline__ uint4 philox_round(uint4 x, uint32_t k0, uint32_t k1) {
+    const uint32_t lo0 = kPhiloxM0 * x.x;
+    const uint32_t hi0 = __umulhi(kPhiloxM0, x.x);
+    const uint32_t lo1 = kPhiloxM1 * x.z;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, x.z);
+    return make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = kPhiloxM0 * x.x;
-        const uint32_t hi0 = __umulhi(kPhiloxM0, x.x);
-        const uint32_t lo1 = kPhiloxM1 * x.z;
-        const uint32_t hi1 = __umulhi(kPhiloxM1, x.z);
-        x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+        x = philox_round(x, k0, k1);
         k0 += kWeyl0;
         k1 += kWeyl1;
     }
@@ -56,13 +61,7 @@ inline RoundKeys round_keys(uint64_t seed) {
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 x, const RoundKeys &rk) {
 #pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = kPhiloxM0 * x.x;
-        const uint32_t hi0 = __umulhi(kPhiloxM0, x.x);
-        const uint32_t lo1 = kPhiloxM1 * x.z;
-        const uint32_t hi1 = __umulhi(kPhiloxM1, x.z);
-        x = make_uint4(hi1 ^ x.y ^ rk.k0[round], lo1, hi0 ^ x.w ^ rk.k1[round], lo0);
-    }
+    for (int round = 0; round < 10; ++round) x = philox_round(x, rk.k0[round], rk.k1[round]);
     return x;
 }
 
