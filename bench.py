@@ -564,7 +564,9 @@ def run_batched(args):
 def run_compare(args):
     """2D-PT against the J-column PT baseline (the paper's Fig. 3 comparison
     shape) on synthetic planted Wishart instances: N in {20, 30, 40, 50},
-    alpha = 0.75, three copies per node, I = 16 x J = 8.  2D-PT uses a linear P
+    alpha = 0.75, copy chains of <= 3 original edges per copy (the batched
+    kernel's degree limit; the paper's runs used 3 copies per node),
+    I = 16 x J = 8.  2D-PT uses a linear P
     ladder; J-column PT runs the same beta ladder in every column at the mean
     of those penalties, with beta-swaps only, and keeps the best feasible
     replica of its last row.  Both run as one batch each, `--cmp-events`
@@ -586,7 +588,7 @@ def run_compare(args):
     for N in Ns:
         for k in range(per_N):
             inst = synth.wishart_planted(N, 0.75, 5000 + 100 * N + k)
-            phys = pt.sparsify(inst.Jq, "fixed", 3)
+            phys = pt.sparsify(inst.Jq, "max_edges", 3)
             probs.append((inst, phys, synth.beta_ladder(I, BETA_MIN, BETA_MAX, inst.scale),
                           synth.penalty_ladder(J, P_MIN, P_MAX, 32767)))
     stream = torch.cuda.Stream()
@@ -641,7 +643,7 @@ def run_compare(args):
         "metric": "residual energy per spin vs sweeps, 2D-PT vs J-column PT (same replicas)",
         "value": None, "unit": "rho", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
         "config": {"workload": f"{per_N} planted Wishart instances per N in {list(Ns)}, alpha 0.75, "
-                               f"3 copies per node, I={I} x J={J}, {E} events of {interval} sweeps; "
+                               f"<=3 edges per copy, I={I} x J={J}, {E} events of {interval} sweeps; "
                                "J-column PT at the mean 2D-PT penalty"},
         "results": out,
     }
@@ -651,8 +653,8 @@ def run_compare(args):
 def run_fig2(args):
     """The paper's Fig. 2 experiment shape: a 5-node all-to-all instance with two
     copies per node (10 physical spins, physical degree 3), one row at beta = 1,
-    penalties P in {2, 4, 6, 8} with P-swaps every 500 sweeps, against the P = 8
-    replica alone; 100 chains each.  The Full Adder couplings are not given, so
+    penalties P in {2, 4, 6, 8} (in the paper's units of g = (S1 - S2)^2) with
+    P-swaps every 500 sweeps, against the P = 8 replica alone; 100 chains each.  The Full Adder couplings are not given, so
     the instance is seeded with couplings in {+-1, +-2, +-3}.  The last
     replica's state is sampled after every 500-sweep event; its feasible (g = 0)
     samples map to logical states (first copy of each chain), and the KL
@@ -679,8 +681,10 @@ def run_fig2(args):
     chains, interval, events = 100, 500, args.fig2_events
     checkpoints = sorted({int(x) for x in np.unique(np.round(np.geomspace(1, events, 16)))})
     out = {}
-    for arm, P in (("with_P_swaps", np.array([2, 4, 6, 8], np.int32)),
-                   ("P8_alone", np.array([8], np.int32))):
+    # the paper's g = (S1 - S2)^2 is 4 per broken link where this library's g is 1,
+    # so its penalties {2, 4, 6, 8} are {8, 16, 24, 32} here
+    for arm, P in (("with_P_swaps", 4 * np.array([2, 4, 6, 8], np.int32)),
+                   ("P8_alone", 4 * np.array([8], np.int32))):
         ctx = pt.PT2D(phys, np.array([1.0], np.float32), P, chains, trace_capacity=0)
         counts = np.zeros((chains, 32), np.int64)
         curve_chain, curve_pooled = {}, {}
@@ -712,7 +716,7 @@ def run_fig2(args):
         "metric": "KL divergence of the last replica vs sweeps (Fig. 2 shape)", "value": None,
         "unit": "nats", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
         "config": {"workload": "seeded 5-node all-to-all instance, 2 copies per node (10 spins), "
-                               f"beta = 1, P in {{2,4,6,8}} vs P = 8 alone, {chains} chains, "
+                               f"beta = 1, P in 4 x {{2,4,6,8}} vs 4 x 8 alone, {chains} chains, "
                                f"swap every {interval} sweeps, {events} events, one sample per event"},
         "results": out,
     }
@@ -817,7 +821,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--cpu-sweeps", type=int, default=100, help="oracle sample, N=200 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2"])
     ap.add_argument("--fig2-events", type=int, default=8000)
