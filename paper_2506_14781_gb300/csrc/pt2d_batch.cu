@@ -211,13 +211,72 @@ __device__ __forceinline__ uint32_t init_word(const BatchRun &d, const int4 *rec
                       r.z < 0x80000000u ? -1.0f : 1.0f, r.w < 0x80000000u ? -1.0f : 1.0f);
 }
 
+// Sweeps and f/g of one slab of int8 spins, held in shared memory (SMEM: the
+// slab is SW columns wide there, loaded before and written back after) or
+// worked on in place in global memory (row stride Rp).  Separate
+// instantiations keep every spin access in one address space.
+template <int DC, int DL, bool SMEM>
+__device__ __forceinline__ void int8_slab(const BatchArgs &a, const BatchRun &d, const int4 *rec,
+                                          const int32_t *cofs, const Quad &q, int8_t *S_g, int col0,
+                                          int lane_off, int grp, int G, uint32_t lq, bool inited,
+                                          int64_t sweeps_done, const uint4 *keys, long long *s_F,
+                                          int *s_G) {
+    extern __shared__ __align__(16) uint8_t batch_smem[];
+    const int n = d.n, SW = d.sw, QL = SW >> 2;
+    const int64_t Rp = d.Rp;
+    int8_t *const Sg = S_g + col0;
+    int8_t *const Ss = reinterpret_cast<int8_t *>(batch_smem);
+    auto word = [&](int row, int byte) -> uint32_t * {
+        if constexpr (SMEM)
+            return reinterpret_cast<uint32_t *>(Ss + row * SW + byte);
+        else
+            return reinterpret_cast<uint32_t *>(Sg + row * Rp + byte);
+    };
+    if (!inited) {
+        const int64_t total = static_cast<int64_t>(n) * QL;
+        for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+            const int pos = static_cast<int>(e / QL);
+            const int qq = static_cast<int>(e - static_cast<int64_t>(pos) * QL);
+            *word(pos, 4 * qq) = init_word<DC, DL>(d, rec, pos, static_cast<uint32_t>((col0 >> 2) + qq));
+        }
+        for (int i = threadIdx.x; i < SW / 4; i += blockDim.x) *word(n, 4 * i) = 0u;
+    } else if (SMEM) {
+        const int vec = SW >> 4;
+        const int nvec = (n + 1) * vec;
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+            const int row = i / vec;
+            const int part = i - row * vec;
+            reinterpret_cast<uint4 *>(Ss)[i] = *reinterpret_cast<const uint4 *>(Sg + row * Rp + 16 * part);
+        }
+    }
+    __syncthreads();
+    auto fetch = [&](int row) -> uint32_t { return *word(row, lane_off); };
+    auto store = [&](int pos, uint32_t w) { *word(pos, lane_off) = w; };
+    slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch, store, grp, G, lq, sweeps_done, keys);
+    if (SMEM) {  // write the slab back (rows 0..n, the zero row included)
+        const int vec = SW >> 4;
+        const int nvec = (n + 1) * vec;
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+            const int row = i / vec;
+            const int part = i - row * vec;
+            *reinterpret_cast<uint4 *>(Sg + row * Rp + 16 * part) = reinterpret_cast<const uint4 *>(Ss)[i];
+        }
+    }
+    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+        s_F[i] = 0;
+        s_G[i] = 0;
+    }
+    __syncthreads();
+    slab_energies<DC, DL>(d, rec, fetch, grp, G, lane_off, s_F, s_G);
+}
+
 // One event of one slab: sweeps, f and g, and the run's swap when this slab is
 // the last of its run to finish.  The slab's spins are int8 in global memory
 // (mode 0), int8 in shared memory (mode 1) or bit-packed in shared memory
 // (mode 2: one bit per walker, a thread owns a nibble, a 16-entry table
 // expands it to int8 spins, the two nibbles of a byte are merged by a shuffle).
 template <int DC, int DL>
-__device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm) {
+__device__ __forceinline__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm) {
     const BatchRun d = a.runs[it.run];
     uint8_t *pool = a.pool;
     const int n = d.n, Rp = d.Rp, R = d.R, J = d.J;
@@ -266,8 +325,9 @@ __device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm)
         const int B = SW >> 3;
         const int byte_lane = lane_q >> 1;
         const int nib_shift = (lane_q & 1) * 4;
-        uint8_t *bits = dsm;
-        uint32_t *lut = reinterpret_cast<uint32_t *>(dsm + ((static_cast<int64_t>(n + 1) * B + 15) & ~15LL));
+        extern __shared__ __align__(16) uint8_t batch_bits[];  // the dynamic shared memory
+        uint8_t *bits = batch_bits;
+        uint32_t *lut = reinterpret_cast<uint32_t *>(batch_bits + (((n + 1) * B + 15) & ~15));
         if (threadIdx.x < 16) lut[threadIdx.x] = word_of_bits(threadIdx.x);
         const int64_t nbytes = static_cast<int64_t>(n + 1) * B;
         for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {
@@ -309,52 +369,12 @@ __device__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm)
         }
         __syncthreads();
         slab_energies<DC, DL>(d, rec, fetch, grp, G, lane_off, s_F, s_G);
+    } else if (d.mode == 1) {
+        int8_slab<DC, DL, true>(a, d, rec, cofs, q, S_g, col0, lane_off, grp, G, lq, inited, sweeps_done,
+                                s_keys, s_F, s_G);
     } else {
-        const bool smem = d.mode == 1;
-        const int64_t stride = smem ? SW : Rp;         // row stride of the spins the slab works on
-        int8_t *S = smem ? reinterpret_cast<int8_t *>(dsm) : S_g + col0;
-        if (!inited) {
-            const int64_t total = static_cast<int64_t>(n) * QL;
-            for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const int pos = static_cast<int>(e / QL);
-                const int qq = static_cast<int>(e - static_cast<int64_t>(pos) * QL);
-                *reinterpret_cast<uint32_t *>(S + pos * stride + 4 * qq) =
-                    init_word<DC, DL>(d, rec, pos, static_cast<uint32_t>((col0 >> 2) + qq));
-            }
-            for (int i = threadIdx.x; i < SW; i += blockDim.x) S[n * stride + i] = 0;
-        } else if (smem) {
-            const int vec = SW >> 4;
-            const int64_t nvec = static_cast<int64_t>(n + 1) * vec;
-            for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
-                const int64_t row = i / vec;
-                const int part = static_cast<int>(i - row * vec);
-                reinterpret_cast<uint4 *>(S)[i] =
-                    *reinterpret_cast<const uint4 *>(S_g + row * Rp + col0 + 16 * part);
-            }
-        }
-        __syncthreads();
-        auto fetch = [&](int row) -> uint32_t {
-            return *reinterpret_cast<const uint32_t *>(S + row * stride + lane_off);
-        };
-        auto store = [&](int pos, uint32_t w) {
-            *reinterpret_cast<uint32_t *>(S + pos * stride + lane_off) = w;
-        };
-        slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch, store, grp, G, lq, sweeps_done, s_keys);
-        if (smem) {  // write the slab back (rows 0..n, the zero row included)
-            const int vec = SW >> 4;
-            const int64_t nvec = static_cast<int64_t>(n + 1) * vec;
-            for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
-                const int64_t row = i / vec;
-                const int part = static_cast<int>(i - row * vec);
-                *reinterpret_cast<uint4 *>(S_g + row * Rp + col0 + 16 * part) = reinterpret_cast<const uint4 *>(S)[i];
-            }
-        }
-        for (int i = threadIdx.x; i < SW; i += blockDim.x) {
-            s_F[i] = 0;
-            s_G[i] = 0;
-        }
-        __syncthreads();
-        slab_energies<DC, DL>(d, rec, fetch, grp, G, lane_off, s_F, s_G);
+        int8_slab<DC, DL, false>(a, d, rec, cofs, q, S_g, col0, lane_off, grp, G, lq, inited, sweeps_done,
+                                 s_keys, s_F, s_G);
     }
     __syncthreads();
     {

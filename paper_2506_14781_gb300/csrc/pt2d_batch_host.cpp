@@ -614,7 +614,7 @@ int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, pt
         }
         return PT2D_OK;
     };
-    for (int storage : {0, 1})
+    for (int storage : {0, 1, 2})
         for (int balance : {0, 2, 8}) {
             pt2d_batch_shape sh = start;
             sh.threads_per_cta = 1024;
