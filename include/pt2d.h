@@ -87,8 +87,17 @@ extern "C" {
 /* ---- problem description ---------------------------------------------- */
 /* Physical (sparsified) instance.  Host pointers; copied at create time.
  * Couplings: symmetric CSR without self loops, J in int16, f = -sum_{a<b}
- * J_ab s_a s_b - sum_a h_a s_a.  Links (copy constraints): symmetric CSR,
- * g = #{links (a,b): s_a != s_b}.  Column indices need not be sorted. */
+ * J_ab s_a s_b - sum_a h_a s_a.  Links: symmetric CSR of penalty terms,
+ *   g = g0 + sum_{links a<b} K_ab [s_a != s_b] + sum_a k_a [s_a = -1],
+ * the constraint function of Eq. 1 (any quadratic penalty of binary
+ * variables, e.g. one-hot groups, has this form; pt2d_onehot_penalty builds
+ * it).  Copy constraints are K = 1, k = 0, g0 = 0: g = #{links with s_a != s_b}
+ * (lk_w = hk = NULL).  The local field of a spin is then
+ *   H_a = E(s_a=-1) - E(s_a=+1) = 2 sum_b J_ab s_b + 2 h_a + P (sum_l K_al s_l + k_a).
+ * Instances with weights other than K = 1 or any k != 0 run on the generic
+ * sweep kernel of a context (not in batches or servers).  The caller keeps g
+ * >= 0 for every state; g is an int32 per walker (|g0| + sum |K| + sum |k| <
+ * 2^31 is checked).  Column indices need not be sorted. */
 typedef struct {
     int32_t n;              /* physical spins, >= 1                          */
     const int32_t *cp_ptr;  /* [n+1] coupling row pointers                   */
@@ -98,6 +107,10 @@ typedef struct {
     const int32_t *lk_col;  /* [lk_ptr[n]] link neighbours                    */
     const int32_t *h;       /* [n] integer field, or NULL for zero            */
     const int32_t *color;   /* [n] proper colouring, or NULL: greedy (above)  */
+    const int16_t *lk_w;    /* [lk_ptr[n]] penalty weight K of each link entry (equal
+                               both ways), or NULL for all 1                   */
+    const int32_t *hk;      /* [n] penalty field k, or NULL for zero          */
+    int64_t g0;             /* constant term of g                             */
 } pt2d_instance;
 
 typedef struct {
@@ -472,6 +485,19 @@ int pt2d_sparsify(int32_t N, const int16_t *Jq, int32_t rule, int32_t param, int
 /* Greedy colouring of a physical instance (the rule described above).
  * color: [n] output; *n_colors: number of colours.  Errors: INVALID_ARG. */
 int pt2d_greedy_color(const pt2d_instance *inst, int32_t *color, int32_t *n_colors);
+
+/* Penalty terms of one-hot constraints: for groups c of spins (binary x_a =
+ * [s_a = +1]), g = sum_c (sum_{a in c} x_a - 1)^2, written in the links form
+ * of pt2d_instance: each group adds (m - 1)^2 to g0, 2 - m to k_a of each of
+ * its m members and -1 to K of each pair of members (pairs in several groups
+ * add up; pairs that sum to 0 are dropped).  Groups: CSR grp_ptr[n_groups+1],
+ * grp_col (spin ids in [0, n), no repeats within a group).  Outputs lk_ptr[n+1],
+ * lk_col / lk_w [cap] (sorted by column per row), *nnz, hk[n], *g0.
+ * Errors: INVALID_ARG (bad groups, NULL outputs, cap too small: *nnz still
+ * receives the size needed). */
+int pt2d_onehot_penalty(int32_t n, int32_t n_groups, const int32_t *grp_ptr, const int32_t *grp_col,
+                        int32_t *lk_ptr, int32_t *lk_col, int16_t *lk_w, int32_t cap, int32_t *nnz,
+                        int32_t *hk, int64_t *g0);
 
 /* ---- diagnostics: the device arithmetic, element-wise -------------------- */
 /* Each runs the same device functions the sweep and swap kernels use, on

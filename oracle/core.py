@@ -98,6 +98,9 @@ class _OrcInst(C.Structure):
         ("h", C.c_void_p),
         ("color", C.c_void_p),
         ("n_colors", C.c_int32),
+        ("lk_w", C.c_void_p),
+        ("hk", C.c_void_p),
+        ("g0", C.c_int64),
     ]
 
 
@@ -220,6 +223,10 @@ class OracleInstance:
         self.lk_ptr = np.ascontiguousarray(inst.lk_ptr, dtype=np.int32)
         self.lk_col = np.ascontiguousarray(inst.lk_col, dtype=np.int32)
         self.h = None if inst.h is None else np.ascontiguousarray(inst.h, dtype=np.int32)
+        lk_w, hk = getattr(inst, "lk_w", None), getattr(inst, "hk", None)
+        self.lk_w = None if lk_w is None else np.ascontiguousarray(lk_w, dtype=np.int16)
+        self.hk = None if hk is None else np.ascontiguousarray(hk, dtype=np.int32)
+        self.g0 = int(getattr(inst, "g0", 0))
         if color is None:
             color, n_colors = greedy_color(inst.n, self.cp_ptr, self.cp_col, self.lk_ptr, self.lk_col)
         else:
@@ -228,7 +235,8 @@ class OracleInstance:
         self.color = np.ascontiguousarray(color, dtype=np.int32)
         self.n_colors = n_colors
         self._c = _OrcInst(self.n, _p(self.cp_ptr), _p(self.cp_col), _p(self.cp_J), _p(self.lk_ptr),
-                           _p(self.lk_col), _p(self.h), _p(self.color), self.n_colors)
+                           _p(self.lk_col), _p(self.h), _p(self.color), self.n_colors,
+                           _p(self.lk_w), _p(self.hk), self.g0)
 
     @property
     def ref(self):

@@ -177,6 +177,9 @@ typedef struct {
     const int32_t *h; /* may be NULL */
     const int32_t *color;
     int32_t n_colors;
+    const int16_t *lk_w;  /* penalty weight K of each link entry; NULL = all 1        */
+    const int32_t *hk;    /* penalty field k of each spin; NULL = all 0               */
+    int64_t g0;           /* constant term of g                                       */
 } orc_inst;
 
 /* Ising cost f(s) = -sum_{a<b} J_ab s_a s_b - sum_a h_a s_a  (the "f" of Eq. 1). */
@@ -193,28 +196,35 @@ int64_t orc_cost_f(const orc_inst *in, const int8_t *s)
     return f;
 }
 
-/* Copy constraint g(s) = number of links (a,b) with s_a != s_b, i.e.
- * sum (s_a - s_b)^2 / 4; g >= 0 and g = 0 iff all copies agree. */
+/* Constraint function g(s) = g0 + sum_{links a<b} K_ab [s_a != s_b] + sum_a k_a [s_a = -1].
+ * Copy constraints (K = 1, k = 0, g0 = 0): the number of links with s_a != s_b,
+ * i.e. sum (s_a - s_b)^2 / 4; g >= 0 and g = 0 iff all copies agree.  Any
+ * quadratic penalty of binary variables (one-hot, slack) has this form. */
 int64_t orc_constraint_g(const orc_inst *in, const int8_t *s)
 {
-    int64_t g = 0;
-    for (int32_t a = 0; a < in->n; ++a)
+    int64_t g = in->g0;
+    for (int32_t a = 0; a < in->n; ++a) {
         for (int32_t k = in->lk_ptr[a]; k < in->lk_ptr[a + 1]; ++k) {
             int32_t b = in->lk_col[k];
-            if (b > a && s[a] != s[b]) g += 1;
+            if (b > a && s[a] != s[b]) g += in->lk_w ? in->lk_w[k] : 1;
         }
+        if (in->hk && s[a] < 0) g += in->hk[a];
+    }
     return g;
 }
 
-/* H_a = E(s_a=-1) - E(s_a=+1) = 2 sum_b J_ab s_b + 2 h_a + P sum_{links} s_l. */
+/* H_a = E(s_a=-1) - E(s_a=+1) = 2 sum_b J_ab s_b + 2 h_a + P (sum_{links} K_al s_l + k_a)
+ * (g(s_a=-1) - g(s_a=+1) = sum_l K_al s_l + k_a). */
 int32_t orc_local_field(const orc_inst *in, const int8_t *s, int32_t a, int32_t P)
 {
     int64_t H = 0;
     for (int32_t k = in->cp_ptr[a]; k < in->cp_ptr[a + 1]; ++k)
         H += 2 * (int64_t)in->cp_J[k] * s[in->cp_col[k]];
     if (in->h) H += 2 * (int64_t)in->h[a];
+    int64_t L = in->hk ? in->hk[a] : 0;
     for (int32_t k = in->lk_ptr[a]; k < in->lk_ptr[a + 1]; ++k)
-        H += (int64_t)P * s[in->lk_col[k]];
+        L += (int64_t)(in->lk_w ? in->lk_w[k] : 1) * s[in->lk_col[k]];
+    H += (int64_t)P * L;
     return (int32_t)H;
 }
 

@@ -41,6 +41,11 @@ class PhysInstance:
     N: int  # logical spins
     copy_of: np.ndarray  # int32 [n] logical id of each physical spin
     offset: np.ndarray  # int32 [N+1] first physical id of each chain
+    # general penalty terms g = g0 + sum_links K [s_a != s_b] + sum_a k_a [s_a = -1]
+    # (None / 0: copy constraints, K = 1, k = 0)
+    lk_w: np.ndarray | None = None  # int16 [2*links] weight K of each link entry
+    hk: np.ndarray | None = None  # int32 [n] penalty field k
+    g0: int = 0
 
     @property
     def n_links(self) -> int:

@@ -44,6 +44,9 @@ class PhysicalInstance:
     h: np.ndarray | None = None
     color: np.ndarray | None = None
     copy_of: np.ndarray | None = None
+    lk_w: np.ndarray | None = None   # int16 penalty weight K of each link entry (None: 1)
+    hk: np.ndarray | None = None     # int32 penalty field k (None: 0)
+    g0: int = 0                      # constant term of g
 
     def __post_init__(self):
         self.cp_ptr = np.ascontiguousarray(self.cp_ptr, dtype=np.int32)
@@ -55,10 +58,15 @@ class PhysicalInstance:
             self.h = np.ascontiguousarray(self.h, dtype=np.int32)
         if self.color is not None:
             self.color = np.ascontiguousarray(self.color, dtype=np.int32)
+        if self.lk_w is not None:
+            self.lk_w = np.ascontiguousarray(self.lk_w, dtype=np.int16)
+        if self.hk is not None:
+            self.hk = np.ascontiguousarray(self.hk, dtype=np.int32)
 
     def c_struct(self) -> _lib.Instance:
         return _lib.Instance(int(self.n), _p(self.cp_ptr), _p(self.cp_col), _p(self.cp_J),
-                             _p(self.lk_ptr), _p(self.lk_col), _p(self.h), _p(self.color))
+                             _p(self.lk_ptr), _p(self.lk_col), _p(self.h), _p(self.color),
+                             _p(self.lk_w), _p(self.hk), int(self.g0))
 
 
 _RULES = {"fixed": _lib.SPARSIFY_FIXED, "max_edges": _lib.SPARSIFY_MAX_EDGES,
@@ -88,6 +96,28 @@ def sparsify(Jq: np.ndarray, rule: str, param: int) -> PhysicalInstance:
     _lib.check(st, "pt2d_sparsify")
     return PhysicalInstance(n.value, cp_ptr, cp_col[:ncp.value], cp_J[:ncp.value], lk_ptr,
                             lk_col[:nlk.value], copy_of=copy_of)
+
+
+def onehot_penalty(n: int, groups) -> tuple:
+    """Penalty terms (lk_ptr, lk_col, lk_w, hk, g0) of one-hot constraints over
+    `groups` (lists of spin ids): g = sum_c (sum_{a in c} [s_a = +1] - 1)^2
+    (pt2d_onehot_penalty)."""
+    grp_ptr = np.concatenate([[0], np.cumsum([len(g) for g in groups])]).astype(np.int32)
+    grp_col = np.ascontiguousarray(np.concatenate([np.asarray(g, np.int32) for g in groups])
+                                   if groups else np.zeros(0, np.int32), dtype=np.int32)
+    L = _lib.lib()
+    lk_ptr = np.zeros(n + 1, np.int32)
+    hk = np.zeros(n, np.int32)
+    nnz = C.c_int32()
+    g0 = C.c_int64()
+    L.pt2d_onehot_penalty(int(n), len(groups), _p(grp_ptr), _p(grp_col), _p(lk_ptr), None, None, 0,
+                          C.byref(nnz), _p(hk), C.byref(g0))
+    lk_col = np.zeros(max(nnz.value, 1), np.int32)
+    lk_w = np.zeros(max(nnz.value, 1), np.int16)
+    _lib.check(L.pt2d_onehot_penalty(int(n), len(groups), _p(grp_ptr), _p(grp_col), _p(lk_ptr),
+                                     _p(lk_col), _p(lk_w), int(lk_col.size), C.byref(nnz), _p(hk),
+                                     C.byref(g0)), "pt2d_onehot_penalty")
+    return lk_ptr, lk_col[:nnz.value].copy(), lk_w[:nnz.value].copy(), hk, int(g0.value)
 
 
 def greedy_color(inst: PhysicalInstance):

@@ -1,6 +1,7 @@
 // Host side of the 2D-PT C ABI (include/pt2d.h): validation, greedy colouring,
 // device layout, the Algorithm 1 event loop and the read/write interface.
 #include <algorithm>
+#include <map>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -79,8 +80,26 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     if (inst->cp_ptr[n] > 0 && !inst->cp_J) return PT2D_ERR_INVALID_ARG;
     int st = check_csr(n, inst->cp_ptr, inst->cp_col, inst->cp_J, &cadj);
     if (st) return st;
-    st = check_csr(n, inst->lk_ptr, inst->lk_col, nullptr, &ladj);
+    st = check_csr(n, inst->lk_ptr, inst->lk_col, inst->lk_w, &ladj);
     if (st) return st;
+    // penalty terms: link weights K (1 without lk_w), penalty field k, constant g0
+    bool penalty = false;
+    int64_t gbound = std::abs(inst->g0);
+    for (int32_t a = 0; a < n; ++a) {
+        for (auto &e : ladj[a]) {
+            if (!inst->lk_w) e.second = 1;
+            if (e.second != 1) penalty = true;
+            gbound += std::abs(static_cast<int64_t>(e.second));  // each link twice: 2x bound
+        }
+        if (inst->hk) {
+            if (inst->hk[a] != 0) penalty = true;
+            gbound += std::abs(static_cast<int64_t>(inst->hk[a]));
+        }
+    }
+    if (gbound >= (int64_t(1) << 31)) return PT2D_ERR_INVALID_ARG;
+    if (force_dc > 0 && (penalty || inst->g0 != 0)) return PT2D_ERR_INVALID_ARG;
+    pp.penalty = penalty;
+    pp.g0 = static_cast<int32_t>(inst->g0);
     // ladders: beta >= 0 finite and ascending, P >= 0 ascending
     if (beta) {
         for (int32_t i = 0; i < I; ++i) {
@@ -101,7 +120,9 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         int64_t b = 0;
         for (const auto &e : cadj[a]) b += 2 * std::abs(static_cast<int64_t>(e.second));
         if (inst->h) b += 2 * std::abs(static_cast<int64_t>(inst->h[a]));
-        b += Pmax * static_cast<int64_t>(ladj[a].size());
+        int64_t pen = inst->hk ? std::abs(static_cast<int64_t>(inst->hk[a])) : 0;
+        for (const auto &e : ladj[a]) pen += std::abs(static_cast<int64_t>(e.second));
+        b += Pmax * pen;
         if (b >= kHBound) return PT2D_ERR_INVALID_ARG;
     }
     // colouring: given (must be proper) or greedy over couplings and links
@@ -159,15 +180,17 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         if (dlmax > 2 || dcmax > force_dc) return PT2D_ERR_INVALID_ARG;
         DC = force_dc;
         DL = 2;
-    } else if (dlmax <= 2 && dcmax <= 6) {
+    } else if (!penalty && dlmax <= 2 && dcmax <= 6) {
         DL = 2;
         DC = dcmax <= 3 ? 3 : (dcmax <= 4 ? 4 : 6);
     } else {
         DC = std::max(dcmax, 1);
         DL = std::max(dlmax, 1);
     }
-    // packed records: [nb x DC, lk x DL, pid, 2h, 2J x DC], padded to whole int4s
-    const int32_t rec_vec = (2 * DC + DL + 2 + 3) / 4;
+    // packed records: [nb x DC, lk x DL, pid, 2h, 2J x DC], then with penalty terms
+    // [K x DL, k], padded to whole int4s
+    const int32_t rec_ints = 2 * DC + DL + 2 + (penalty ? DL + 1 : 0);
+    const int32_t rec_vec = (rec_ints + 3) / 4;
     const size_t ri = static_cast<size_t>(rec_vec) * 4;
     pp.rec_vec = rec_vec;
     pp.rec.assign(static_cast<size_t>(n) * ri, 0);
@@ -183,6 +206,10 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         for (size_t k = 0; k < ladj[a].size(); ++k) r[DC + k] = pp.pos_of[ladj[a][k].first];
         r[DC + DL] = a;
         r[DC + DL + 1] = inst->h ? 2 * inst->h[a] : 0;
+        if (penalty) {
+            for (size_t k = 0; k < ladj[a].size(); ++k) r[2 * DC + DL + 2 + k] = ladj[a][k].second;
+            r[2 * DC + 2 * DL + 2] = inst->hk ? inst->hk[a] : 0;
+        }
     }
     pp.n = n;
     pp.I = I;
@@ -215,7 +242,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     if (mode < 0 || mode > 3) return PT2D_ERR_INVALID_ARG;
     if (opt && opt->swap_mode != PT2D_SWAP_2D && opt->swap_mode != PT2D_SWAP_JCOLUMN)
         return PT2D_ERR_INVALID_ARG;
-    const bool specialised = DL == 2 && (DC == 3 || DC == 4 || DC == 6);
+    const bool specialised = !penalty && DL == 2 && (DC == 3 || DC == 4 || DC == 6);
     const int64_t walkers = static_cast<int64_t>(runs) * pp.Rp;
     auto fits = [&](int sw) {
         return pt2d::smem_sweep_bytes(n, sw) + pt2d::kSweepStaticSmem <= static_cast<size_t>(smem_max);
@@ -512,6 +539,8 @@ int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const floa
     c->L.DL = pp.DL;
     c->L.rec_vec = pp.rec_vec;
     c->L.pad_ref = pp.pad_ref;
+    c->L.penalty = pp.penalty ? 1 : 0;
+    c->L.g0 = pp.g0;
     c->rs.runs = pp.runs;
     c->rs.I = pp.I;
     c->rs.J = pp.J;
@@ -584,7 +613,8 @@ int pt2d_num_colors(const pt2d_ctx *c) { return c ? c->pp.C : 0; }
 int pt2d_tiling(const pt2d_ctx *c, int32_t out[4]) {
     if (!c || !out) return PT2D_ERR_INVALID_ARG;
     const pt2d::SweepTiling &t = c->pp.tiling;
-    const bool specialised = c->pp.DL == 2 && (c->pp.DC == 3 || c->pp.DC == 4 || c->pp.DC == 6);
+    const bool specialised =
+        !c->pp.penalty && c->pp.DL == 2 && (c->pp.DC == 3 || c->pp.DC == 4 || c->pp.DC == 6);
     out[0] = t.bits ? 3 : t.smem ? 2 : specialised ? 1 : 4;
     out[1] = 4 * t.lanes_per_spin;
     out[2] = t.threads;
@@ -846,6 +876,56 @@ int pt2d_greedy_color(const pt2d_instance *inst, int32_t *color, int32_t *n_colo
     if (st) return st;
     std::memcpy(color, pp.color.data(), sizeof(int32_t) * pp.n);
     *n_colors = pp.C;
+    return PT2D_OK;
+}
+
+int pt2d_onehot_penalty(int32_t n, int32_t n_groups, const int32_t *grp_ptr, const int32_t *grp_col,
+                        int32_t *lk_ptr, int32_t *lk_col, int16_t *lk_w, int32_t cap, int32_t *nnz,
+                        int32_t *hk, int64_t *g0) {
+    if (n < 1 || n_groups < 0 || !grp_ptr || !lk_ptr || !nnz || !hk || !g0) return PT2D_ERR_INVALID_ARG;
+    if (grp_ptr[0] != 0) return PT2D_ERR_INVALID_ARG;
+    for (int32_t c = 0; c < n_groups; ++c)
+        if (grp_ptr[c + 1] < grp_ptr[c]) return PT2D_ERR_INVALID_ARG;
+    if (grp_ptr[n_groups] > 0 && !grp_col) return PT2D_ERR_INVALID_ARG;
+    // (sum_{a in c} x_a - 1)^2 with x_a = 1 - [s_a = -1]:
+    //   (m - 1)^2 + (2 - m) sum_a [s_a = -1] - sum_{a<b in c} [s_a != s_b]
+    std::vector<std::map<int32_t, int64_t>> K(n);
+    std::vector<int64_t> k(n, 0);
+    int64_t c0 = 0;
+    for (int32_t c = 0; c < n_groups; ++c) {
+        const int32_t b = grp_ptr[c], e = grp_ptr[c + 1], m = e - b;
+        std::vector<int32_t> mem(grp_col + b, grp_col + e);
+        std::sort(mem.begin(), mem.end());
+        for (int32_t i = 0; i < m; ++i) {
+            if (mem[i] < 0 || mem[i] >= n || (i > 0 && mem[i] == mem[i - 1])) return PT2D_ERR_INVALID_ARG;
+            k[mem[i]] += 2 - m;
+            for (int32_t j = 0; j < m; ++j)
+                if (j != i) K[mem[i]][mem[j]] -= 1;
+        }
+        c0 += static_cast<int64_t>(m - 1) * (m - 1);
+    }
+    int64_t total = 0;
+    for (int32_t a = 0; a < n; ++a)
+        for (const auto &e : K[a])
+            if (e.second != 0) ++total;
+    if (total > INT32_MAX) return PT2D_ERR_INVALID_ARG;
+    *nnz = static_cast<int32_t>(total);
+    if (total > cap || (total > 0 && (!lk_col || !lk_w))) return PT2D_ERR_INVALID_ARG;
+    int32_t pos = 0;
+    lk_ptr[0] = 0;
+    for (int32_t a = 0; a < n; ++a) {
+        for (const auto &e : K[a]) {
+            if (e.second == 0) continue;
+            if (e.second < INT16_MIN || e.second > INT16_MAX) return PT2D_ERR_INVALID_ARG;
+            lk_col[pos] = e.first;
+            lk_w[pos] = static_cast<int16_t>(e.second);
+            ++pos;
+        }
+        lk_ptr[a + 1] = pos;
+        if (k[a] < INT32_MIN || k[a] > INT32_MAX) return PT2D_ERR_INVALID_ARG;
+        hk[a] = static_cast<int32_t>(k[a]);
+    }
+    *g0 = c0;
     return PT2D_OK;
 }
 

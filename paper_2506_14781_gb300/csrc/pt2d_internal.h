@@ -31,6 +31,8 @@ struct Layout {
     int32_t pad_ref;      // neighbour reference of the zero row (n, or n * SW when scaled)
     const int4 *rec;      // [n][rec_vec]
     const int32_t *cofs;  // [C + 1] colour class offsets (positions)
+    int32_t penalty;      // generic records carry link weights K and the penalty field k
+    int32_t g0;           // constant term of g
 };
 
 struct Walkers {

@@ -90,7 +90,7 @@ __device__ __forceinline__ void energies(const Layout &L, const Walkers &wk, Fet
     __syncthreads();
     for (int i = threadIdx.x; i < slab; i += blockDim.x) {
         wk.f[col0 + i] = -(s_F[i] / 4);
-        wk.g[col0 + i] = s_g[i] / 2;
+        wk.g[col0 + i] = s_g[i] / 2 + L.g0;
     }
 }
 
@@ -319,7 +319,9 @@ __global__ void __launch_bounds__(256) k_sweep_generic(Layout L, Walkers wk, int
                 const int *rc = recs + static_cast<int64_t>(pos) * rec_ints;
                 const int h2 = __ldg(rc + DC + DL + 1);
                 int a[4] = {h2, h2, h2, h2};
-                int l[4] = {0, 0, 0, 0};
+                // penalty part: sum_l K_l s_l + k (K = 1, k = 0 for copy links)
+                const int kk = L.penalty ? __ldg(rc + 2 * DC + 2 * DL + 2) : 0;
+                int l[4] = {kk, kk, kk, kk};
                 for (int k = 0; k < DC; ++k) {
                     const uint32_t x = word(__ldg(rc + k));
                     const int j = __ldg(rc + DC + DL + 2 + k);
@@ -328,8 +330,9 @@ __global__ void __launch_bounds__(256) k_sweep_generic(Layout L, Walkers wk, int
                 }
                 for (int k = 0; k < DL; ++k) {
                     const uint32_t y = word(__ldg(rc + DC + k));
+                    const int w = L.penalty ? __ldg(rc + 2 * DC + DL + 2 + k) : 1;
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) l[b] += sbyte_rt(y, b);
+                    for (int b = 0; b < 4; ++b) l[b] += w * sbyte_rt(y, b);
                 }
                 const uint4 r = philox4x32_10(
                     make_uint4(static_cast<uint32_t>(__ldg(rc + DC + DL)), sweep, lq, c3), rk);
@@ -366,12 +369,19 @@ __global__ void __launch_bounds__(256) k_sweep_generic(Layout L, Walkers wk, int
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) F[b] += static_cast<long long>(sbyte_rt(xs, b)) * cc[b];
+        // twice g: each link from both ends (weight K), twice k of a down spin
         for (int k = 0; k < DL; ++k) {
             const int lp = __ldg(rc + DC + k);
             if (lp == L.pad_ref) continue;
             const uint32_t y = word(lp);
+            const int w = L.penalty ? __ldg(rc + 2 * DC + DL + 2 + k) : 1;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) g[b] += sbyte_rt(xs, b) != sbyte_rt(y, b);
+            for (int b = 0; b < 4; ++b) g[b] += w * (sbyte_rt(xs, b) != sbyte_rt(y, b));
+        }
+        if (L.penalty) {
+            const int k2 = 2 * __ldg(rc + 2 * DC + 2 * DL + 2);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) g[b] += sbyte_rt(xs, b) < 0 ? k2 : 0;
         }
     }
 #pragma unroll
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(256) k_sweep_generic(Layout L, Walkers wk, int
     const int64_t col0 = static_cast<int64_t>(blockIdx.x) * QL * 4;
     for (int i = threadIdx.x; i < 4 * QL; i += blockDim.x) {
         wk.f[col0 + i] = -(s_F[i] / 4);
-        wk.g[col0 + i] = s_g[i] / 2;
+        wk.g[col0 + i] = s_g[i] / 2 + L.g0;
     }
 }
 
@@ -599,11 +609,11 @@ cudaError_t launch_sweeps(const Layout &L, const Walkers &wk, const SweepTiling 
         if (L.DC == 6 && L.DL == 2) return launch_smem<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
         return cudaErrorInvalidValue;
     }
-    if (L.DC == 3 && L.DL == 2)
+    if (!L.penalty && L.DC == 3 && L.DL == 2)
         return launch_global_variant<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
-    if (L.DC == 4 && L.DL == 2)
+    if (!L.penalty && L.DC == 4 && L.DL == 2)
         return launch_global_variant<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
-    if (L.DC == 6 && L.DL == 2)
+    if (!L.penalty && L.DC == 6 && L.DL == 2)
         return launch_global_variant<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
     int shift = 0;
     while ((1 << shift) < tl.lanes_per_spin) ++shift;

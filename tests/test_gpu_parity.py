@@ -297,6 +297,65 @@ def test_torch_stream_and_workspace(pt, tiny_config):
         assert np.array_equal(a.read(getattr(pt, what)), b.read(getattr(pt, what))), what
 
 
+# ---- general constraint functions (penalty terms) -------------------------------------
+def _penalty_pair(pt, n, groups, seed, chains=()):
+    """The same instance for both sides: random couplings and fields, one-hot
+    groups expanded by each side's own routine, optional copy links (K = 1)."""
+    from oracle.penalties import onehot
+
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n), np.int16)
+    for a in range(n):
+        for b in range(a + 1, n):
+            if rng.random() < 0.2:
+                A[a, b] = A[b, a] = rng.integers(-400, 401)
+    cp_ptr = np.concatenate([[0], np.cumsum((A != 0).sum(1))]).astype(np.int32)
+    cp_col = np.concatenate([np.nonzero(A[a])[0] for a in range(n)]).astype(np.int32)
+    cp_J = np.concatenate([A[a][A[a] != 0] for a in range(n)]).astype(np.int16)
+    h = rng.integers(-100, 101, n).astype(np.int32)
+    sides = []
+    for expand in (pt.onehot_penalty, onehot):
+        lk_ptr, lk_col, lk_w, hk, g0 = expand(n, groups)
+        # copy links between chained spins add weight-1 entries
+        rows = [dict(zip(lk_col[lk_ptr[a]:lk_ptr[a + 1]].tolist(), lk_w[lk_ptr[a]:lk_ptr[a + 1]].tolist()))
+                for a in range(n)]
+        for a, b in chains:
+            rows[a][b] = rows[a].get(b, 0) + 1
+            rows[b][a] = rows[b].get(a, 0) + 1
+        ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+        col = np.array([b for r in rows for b in sorted(r)], np.int32)
+        w = np.array([r[b] for r in rows for b in sorted(r)], np.int16)
+        sides.append((ptr, col, w, hk, g0))
+    (p1, c1, w1, k1, g1), (p2, c2, w2, k2, g2) = sides
+    phys_p = pt.PhysicalInstance(n, cp_ptr, cp_col, cp_J, p1, c1, h=h, lk_w=w1, hk=k1, g0=g1)
+    phys_o = oracle.PhysInstance(n, cp_ptr, cp_col, cp_J, p2, c2, h, n, np.arange(n, dtype=np.int32),
+                                 np.arange(n + 1, dtype=np.int32), lk_w=w2, hk=k2, g0=g2)
+    return phys_p, phys_o
+
+
+@pytest.mark.parametrize("swap_mode", ["2d", "jcolumn"])
+def test_general_penalty_terms_bit_exact(pt, swap_mode):
+    """One-hot groups (negative link weights, penalty fields, g0) plus copy links
+    run on the generic kernel, bit-exact with the oracle."""
+    groups = [list(range(k, k + 4)) for k in range(0, 40, 4)] + [[1, 5, 9], [38, 2, 17, 23, 30]]
+    phys = _penalty_pair(pt, 44, groups, 7, chains=[(40, 41), (41, 42), (42, 43)])
+    beta = np.array([2e-4, 5e-4, 1.2e-3, 3e-3], np.float32)
+    P = np.array([50, 200, 600], np.int32)
+    ctx, orc = both(pt, None, None, beta, P, 5, 31337, [(30, 3), (12, 3)], phys=phys, trace=32,
+                    target=-2000, swap_mode=swap_mode)
+    assert ctx.tiling["kernel"] == "generic"
+    assert_same(pt, ctx, orc)
+    assert np.all(ctx.read(pt.G) >= 0)
+
+
+def test_batches_reject_general_penalty_terms(pt):
+    phys, _ = _penalty_pair(pt, 12, [[0, 1, 2], [3, 4, 5, 6]], 2)
+    batch = pt.Batch(1 << 24, 3, 4, trace_capacity=4)
+    with pytest.raises(pt.Pt2dError):
+        batch.add(phys, np.array([1e-3], np.float32), np.array([10], np.int32), 1, 1, 0)
+    batch.close()
+
+
 # ---- the J-column PT baseline ----------------------------------------------------------
 @pytest.mark.parametrize("kernel,wpc", [("global", 16), ("smem", 16), ("bits", 8), ("auto", 0)])
 def test_jcolumn_baseline_bit_exact(pt, kernel, wpc):

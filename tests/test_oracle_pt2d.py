@@ -74,7 +74,7 @@ MUTATIONS = {
     "heatbath_sign": ("float t = beta * Hf;", "float t = -(beta * Hf);"),
     "bswap_sign": ("const float dbeta = beta[b + 1] - beta[b];",
                    "const float dbeta = beta[b] - beta[b + 1];"),
-    "drop_link_field": ("H += (int64_t)P * s[in->lk_col[k]];", "H += 0;"),
+    "drop_link_field": ("H += (int64_t)P * L;", "H += 0;"),
 }
 
 
