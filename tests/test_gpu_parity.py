@@ -82,6 +82,30 @@ def test_philox_matches_oracle(pt):
     assert np.array_equal(pt.diag_philox(ctr, key), ocore.philox_array(ctr, key))
 
 
+def test_philox_matches_curand(pt, tmp_path):
+    """cuRAND's device Philox4_32_10 (a library run on the GPU) gives the same
+    blocks as the library's generator at random counters and 64-bit keys, and
+    so as the oracle's."""
+    import ctypes
+    import os
+    import subprocess
+
+    src = os.path.join(os.path.dirname(__file__), "_curand_philox.cu")
+    lib = str(tmp_path / "libcurand_philox.so")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared",
+                    "-Xcompiler", "-fPIC", src, "-o", lib], check=True, capture_output=True)
+    L = ctypes.CDLL(lib)
+    L.curand_philox.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong]
+    rng = np.random.default_rng(2)
+    n = 50000
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    out = np.zeros((n, 4), np.uint32)
+    assert L.curand_philox(ctr.ctypes.data, key.ctypes.data, out.ctypes.data, n) == 0
+    assert np.array_equal(pt.diag_philox(ctr, key), out)
+    assert np.array_equal(ocore.philox_array(ctr[:2000], key[:2000]), out[:2000])
+
+
 def test_pt_exp_bit_exact_dense(pt):
     lo = np.float32(-104.5).view(np.uint32)  # negative floats: larger bit pattern = more negative
     neg = np.arange(np.uint32(0x80000000), lo + np.uint32(1), 53, dtype=np.uint64).astype(np.uint32)
