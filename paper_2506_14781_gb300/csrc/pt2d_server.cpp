@@ -60,6 +60,7 @@ struct pt2d_server {
     int32_t interval = 50;
     int32_t events_per_step = 10;
     int32_t max_runs = 0;
+    size_t capacity = 0;  // pool bytes when empty: a request needing more can never be admitted
     std::deque<int64_t> queue;
     std::map<int64_t, Request> reqs;
     std::map<int64_t, int64_t> by_batch;  // batch id -> request id
@@ -75,7 +76,6 @@ double now_s(const pt2d_server *s) {
 }
 
 int finish(pt2d_server *s, Request &r) {
-    int64_t v = 0;
     int st = pt2d_batch_read(s->b, r.batch_id, PT2D_BEST_F, &r.best_f, sizeof(int64_t));
     if (!st) st = pt2d_batch_read(s->b, r.batch_id, PT2D_BEST_EVENT, &r.best_event, sizeof(int64_t));
     if (!st) st = pt2d_batch_read(s->b, r.batch_id, PT2D_SOLVED_EVENT, &r.solved_event, sizeof(int64_t));
@@ -83,7 +83,6 @@ int finish(pt2d_server *s, Request &r) {
     if (!st) st = pt2d_batch_read(s->b, r.batch_id, PT2D_COUNTERS, counters, sizeof counters);
     r.best_state.assign(r.n, 0);
     if (!st) st = pt2d_batch_read(s->b, r.batch_id, PT2D_BEST_STATE, r.best_state.data(), r.n);
-    (void)v;
     if (st) return st;
     r.sweeps_done = counters[0];
     pt2d_batch_remove(s->b, r.batch_id);
@@ -117,6 +116,7 @@ int pt2d_server_create(pt2d_server **out, size_t pool_bytes, int32_t max_couplin
         delete s;
         return st;
     }
+    s->capacity = pt2d_batch_free_bytes(s->b);
     s->interval = swap_interval;
     s->events_per_step = events_per_step;
     s->max_runs = max_requests;
@@ -137,7 +137,9 @@ int pt2d_server_submit(pt2d_server *s, const pt2d_instance *inst, int32_t I, con
     if (!s || !inst || !beta || !P || !request_id || inst->n < 1 || I < 1 || J < 1 || max_sweeps < 1 ||
         !inst->cp_ptr || !inst->lk_ptr)
         return PT2D_ERR_INVALID_ARG;
-    if (pt2d_batch_instance_bytes(s->b, inst, I, J, 1) == 0) return PT2D_ERR_INVALID_ARG;
+    const size_t need = pt2d_batch_instance_bytes(s->b, inst, I, J, 1);
+    if (need == 0) return PT2D_ERR_INVALID_ARG;
+    if (need > s->capacity) return PT2D_ERR_OOM;  // would block the FIFO head for ever
     Request r;
     const int32_t n = inst->n;
     r.n = n;

@@ -114,3 +114,24 @@ def test_fifo_admission_by_memory_and_cancel(pt):
     srv.forget(r1)
     with pytest.raises(pt.Pt2dError):
         srv.status(r1)
+
+
+def test_submit_rejects_what_can_never_run(pt):
+    """A request larger than the whole pool is refused at submission (it would
+    block the FIFO head for ever), and so is one a batch cannot hold."""
+    reqs = _requests(pt)
+    probe = pt.Batch(1 << 24, 3, 8, trace_capacity=0)
+    need = probe.instance_bytes(reqs[5]["phys"], 8, 4, 1)
+    probe.close()
+    srv = pt.Server(need // 2, 3, 8, INTERVAL, EVENTS_PER_STEP)
+    with pytest.raises(pt.Pt2dError) as e:
+        srv.submit(reqs[5]["phys"], reqs[5]["beta"], reqs[5]["P"], 1, reqs[5]["target"], 100)
+    assert "OOM" in str(e.value)
+    small = reqs[0]
+    rid = srv.submit(small["phys"], small["beta"], small["P"], 1, small["target"], 40)
+    _drain(srv, [rid])
+    lk_ptr, lk_col, lk_w, hk, g0 = pt.onehot_penalty(6, [[0, 1, 2], [3, 4, 5]])
+    pen = pt.PhysicalInstance(6, np.zeros(7, np.int32), [], [], lk_ptr, lk_col, lk_w=lk_w, hk=hk, g0=g0)
+    with pytest.raises(pt.Pt2dError):
+        srv.submit(pen, small["beta"], small["P"], 1, 0, 40)
+    srv.close()
