@@ -241,12 +241,17 @@ __device__ __forceinline__ void int8_slab(const BatchArgs &a, const BatchRun &d,
         }
         for (int i = threadIdx.x; i < SW / 4; i += blockDim.x) *word(n, 4 * i) = 0u;
     } else if (SMEM) {
-        const int vec = SW >> 4;
-        const int nvec = (n + 1) * vec;
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-            const int row = i / vec;
-            const int part = i - row * vec;
-            reinterpret_cast<uint4 *>(Ss)[i] = *reinterpret_cast<const uint4 *>(Sg + row * Rp + 16 * part);
+        if (SW >= 16) {
+            const int vec = SW >> 4;
+            const int nvec = (n + 1) * vec;
+            for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+                const int row = i / vec;
+                const int part = i - row * vec;
+                reinterpret_cast<uint4 *>(Ss)[i] = *reinterpret_cast<const uint4 *>(Sg + row * Rp + 16 * part);
+            }
+        } else {  // 8-walker slabs: one 8-byte word per row
+            for (int row = threadIdx.x; row <= n; row += blockDim.x)
+                reinterpret_cast<uint2 *>(Ss)[row] = *reinterpret_cast<const uint2 *>(Sg + row * Rp);
         }
     }
     __syncthreads();
@@ -254,12 +259,17 @@ __device__ __forceinline__ void int8_slab(const BatchArgs &a, const BatchRun &d,
     auto store = [&](int pos, uint32_t w) { *word(pos, lane_off) = w; };
     slab_sweeps<DC, DL>(a, d, rec, cofs, q, fetch, fetch, store, grp, G, lq, sweeps_done, keys);
     if (SMEM) {  // write the slab back (rows 0..n, the zero row included)
-        const int vec = SW >> 4;
-        const int nvec = (n + 1) * vec;
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-            const int row = i / vec;
-            const int part = i - row * vec;
-            *reinterpret_cast<uint4 *>(Sg + row * Rp + 16 * part) = reinterpret_cast<const uint4 *>(Ss)[i];
+        if (SW >= 16) {
+            const int vec = SW >> 4;
+            const int nvec = (n + 1) * vec;
+            for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+                const int row = i / vec;
+                const int part = i - row * vec;
+                *reinterpret_cast<uint4 *>(Sg + row * Rp + 16 * part) = reinterpret_cast<const uint4 *>(Ss)[i];
+            }
+        } else {
+            for (int row = threadIdx.x; row <= n; row += blockDim.x)
+                *reinterpret_cast<uint2 *>(Sg + row * Rp) = reinterpret_cast<const uint2 *>(Ss)[row];
         }
     }
     for (int i = threadIdx.x; i < SW; i += blockDim.x) {

@@ -195,7 +195,7 @@ void drop_graph(pt2d_batch *b) {
 
 // Slab width and storage of a run: int8 spins in shared memory, the whole run
 // when it fits in the shared memory reserved per CTA, else the widest power of
-// two >= 16 that fits; else the same with bit-packed spins (widths >= 8); else
+// two >= 8 that fits; else the same with bit-packed spins (widths >= 8); else
 // int8 spins in global memory at the global-memory slab width.  Then the width
 // is halved while a slab holds more than `cap` spin-walkers (0 = no cap).
 void slab_shape(const pt2d_batch *b, pt2d::BatchRun &d, int64_t cap) {
@@ -203,9 +203,9 @@ void slab_shape(const pt2d_batch *b, pt2d::BatchRun &d, int64_t cap) {
         while (cap > 0 && sw > narrowest && static_cast<int64_t>(d.n) * sw > cap) sw >>= 1;
         return sw;
     };
-    for (int32_t sw = d.Rp; b->int8 && sw >= 16; sw >>= 1)
+    for (int32_t sw = d.Rp; b->int8 && sw >= 8; sw >>= 1)
         if (static_cast<int64_t>(d.n + 1) * sw <= b->smem_state) {
-            d.sw = capped(sw, 16);
+            d.sw = capped(sw, 8);
             d.mode = 1;
             return;
         }

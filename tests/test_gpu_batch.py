@@ -90,12 +90,13 @@ def test_batch_matches_plain_contexts(pt, kernel, threads):
 
 
 def test_batch_slab_storage_by_size(pt):
-    """Runs whose int8 slab of 16 walkers does not fit in shared memory go to
-    bit-packed slabs (128 KB+ instances: widths 8 and 32 walkers), next to int8
-    shared-memory slabs, in one launch; each matches its plain context."""
+    """Runs whose int8 slab of 8 walkers does not fit in shared memory go to
+    bit-packed slabs (widths 8 and 32 walkers), next to int8 shared-memory slabs
+    of 8, 16 and 128 walkers, in one launch; each matches its plain context."""
     probs = [
         _problem(pt, 600, 0.5, 31, ("max_edges", 3), 16, 8, 1),   # n ~ 120k: bits, 8 walkers
         _problem(pt, 300, 0.5, 32, ("max_edges", 3), 16, 8, 1),   # n ~ 30k: bits, 32 walkers
+        _problem(pt, 240, 0.5, 35, ("max_edges", 3), 16, 8, 1),   # n ~ 19k: int8, 8 walkers
         _problem(pt, 150, 0.5, 33, ("max_edges", 3), 16, 8, 2),   # n ~ 7.5k: int8, 16 walkers
         _problem(pt, 40, 0.5, 34, ("max_edges", 3), 4, 8, 1),     # int8, whole run
     ]

@@ -99,6 +99,7 @@ def test_philox_matches_curand(pt, tmp_path):
     rng = np.random.default_rng(2)
     n = 50000
     ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:, 1] &= 0x3FFFFFFF  # cuRAND's offset is 4 x the low 64 counter bits, a 64-bit value
     key = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
     out = np.zeros((n, 4), np.uint32)
     assert L.curand_philox(ctr.ctypes.data, key.ctypes.data, out.ctypes.data, n) == 0
