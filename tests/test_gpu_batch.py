@@ -202,3 +202,34 @@ def test_batch_matches_oracle_on_tiny_config(pt, tiny_config):
                     ("BEST_STATE", "best_state"), ("ACC_P", "acc_P"), ("ACC_B", "acc_B"),
                     ("SUM_F", "sum_f"), ("N_FEASIBLE", "n_feasible")):
         assert np.array_equal(batch.read(bid, getattr(pt, w)), getattr(orc, attr)), w
+
+
+def test_full_size_uneven_batch_sampled_runs(pt):
+    """The 1024-instance uneven workload at full size in the benchmark's launch
+    configuration (default shape, one event of 50 sweeps): the smallest, a
+    middle and the largest instance are checked in full against the oracle."""
+    I, J, interval = 16, 8, 50
+    specs = synth.batch_specs(1024, 1000)
+    probs = []
+    for N, alpha, seed in specs:
+        inst = synth.wishart_planted(N, alpha, seed)
+        probs.append((inst, pt.sparsify(inst.Jq, "max_degree", 4),
+                      synth.beta_ladder(I, 0.1, 5.0, inst.scale), synth.penalty_ladder(J, 0.5, 64.0, 32767),
+                      seed))
+    probe = pt.Batch(1 << 22, 3, 8, trace_capacity=4)
+    need = sum(probe.instance_bytes(p[1], I, J, 1) for p in probs)
+    probe.close()
+    batch = pt.Batch(int(need * 1.02) + (64 << 20), 3, len(probs), trace_capacity=4)
+    ids = [batch.add(p[1], p[2], p[3], 1, p[4], p[0].E_planted) for p in probs]
+    batch.run(1, interval)
+    order = np.argsort([p[1].n for p in probs])
+    for k in (order[0], order[len(order) // 2], order[-1]):
+        inst, phys, beta, P, seed = probs[k]
+        orc = oracle.OracleRun(oracle.OracleInstance(oracle.sparsify(inst.Jq, "max_degree", 4)), beta, P,
+                               [0], seed, trace_cap=4, target=inst.E_planted)
+        orc.run(interval, interval)
+        for w, attr in (("STATES", "spins"), ("WALKER_AT", "walker_at"), ("F", "f"), ("G", "g"),
+                        ("TRACE_F", "trace_f"), ("TRACE_G", "trace_g"), ("BEST_F", "best_f"),
+                        ("ACC_P", "acc_P"), ("ACC_B", "acc_B"), ("SUM_F", "sum_f")):
+            assert np.array_equal(batch.read(ids[k], getattr(pt, w)), getattr(orc, attr)), (k, w)
+    batch.close()
