@@ -558,6 +558,15 @@ def run_batched(args):
         "speedup_batched_over_plain": (plain["seconds"] / t_batched) if plain else None,
         "tts": tts,
     }
+    peaks, peak_src = _peaks()
+    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    alu_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    alu = upd_per_event * E / t_batched * OPS_PER_UPDATE / 1e12
+    line["roofline"] = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tops/s (lane-ops)",
+                        "frac": alu / alu_peak, "traffic": None, "kernel": "k_batch",
+                        "ops_per_update": OPS_PER_UPDATE,
+                        "traffic_source": "profiles/k_batch_256.md (256-instance capture, not scaled)",
+                        "peak_source": f"{sm_count} SMs x 128 lanes x max clock ({peak_src})"}
     print(json.dumps(line))
 
 
