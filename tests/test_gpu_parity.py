@@ -280,6 +280,45 @@ def test_errors_and_empty_runs(pt, tiny_config):
         pt.PT2D(phys, cfg["beta"][::-1].copy(), cfg["P"], 1)  # descending ladder
 
 
+def test_largest_replica_grid(pt, tiny_config):
+    """I x J = 8192 slots (the largest grid a run may have; one more is refused),
+    swaps on both axes, bit-exact with the oracle."""
+    cfg = tiny_config
+    beta = synth.beta_ladder(128, 0.05, 3.0, cfg["inst"].scale)
+    P = synth.penalty_ladder(64, 0.1, 4.0, 32767)
+    ctx, orc = both(pt, cfg["inst"], ("fixed", 2), beta, P, 1, 5, [(24, 2)], trace=16)
+    assert_same(pt, ctx, orc)
+    with pytest.raises(pt.Pt2dError):
+        pt.PT2D(pt.sparsify(cfg["inst"].Jq, "fixed", 2), beta, np.append(P, P[-1]).astype(np.int32), 1)
+
+
+def test_checkpoint_moves_between_sweep_kernels(pt):
+    """The spin layout in device memory is the same for every sweep kernel: a
+    checkpoint taken under one tiling and restored under another continues
+    exactly as an uninterrupted run."""
+    inst = synth.wishart_planted(30, 0.5, 21)
+    beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
+    P = synth.penalty_ladder(3, 0.5, 4.0, 32767)
+    phys = pt.sparsify(inst.Jq, "max_edges", 3)
+    ref = pt.PT2D(phys, beta, P, 3, trace_capacity=32, sweep_kernel="global", walkers_per_cta=16)
+    ref.run(60, 5, 9)
+    order = [("global", 16), ("bits", 8), ("smem", 16), ("bits", 64), ("global", 4), ("smem", 32)]
+    prev = None
+    for kernel, wpc in order:
+        ctx = pt.PT2D(phys, beta, P, 3, trace_capacity=32, sweep_kernel=kernel, walkers_per_cta=wpc)
+        if prev is not None:
+            for what, _ in ARRAYS + [("COUNTERS", None)]:
+                if what in ("F", "G"):
+                    continue
+                ctx.write(getattr(pt, what), prev.read(getattr(pt, what)))
+            prev.close()
+        ctx.run(10, 5, 9)  # six contexts x 10 sweeps = the reference's 60
+        assert ctx.tiling["kernel"] == kernel
+        prev = ctx
+    for what, _ in ARRAYS:
+        assert np.array_equal(prev.read(getattr(pt, what)), ref.read(getattr(pt, what))), what
+
+
 def test_checkpoint_restore_matches_uninterrupted(pt, tiny_config):
     inst = synth.wishart_planted(24, 0.75, 8)
     phys = pt.sparsify(inst.Jq, "max_edges", 3)
