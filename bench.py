@@ -62,10 +62,10 @@ BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
 # DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only while the kernel sources hash to `src`; the summaries are under profiles/.
 PROFILED_TRAFFIC = {
-    ("n200", "k_sweep_smem"): dict(src="514b2e20853ebecb", dram_bytes_per_launch=386_895_872,
+    ("n200", "k_sweep_smem"): dict(src="ceabe32d2d4e2a4a", dram_bytes_per_launch=386_070_016,
                                    profile="profiles/k_sweep_smem_n200.md"),
     # captured at 4 of the 16 runs and scaled by the walkers
-    ("n800", "k_sweep_bits"): dict(src="514b2e20853ebecb", dram_bytes_per_launch=20_444_092_000,
+    ("n800", "k_sweep_bits"): dict(src="ceabe32d2d4e2a4a", dram_bytes_per_launch=19_655_536_000,
                                    profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h")
@@ -281,7 +281,7 @@ def run_gpu(args):
     ops_per_update = OPS_PER_UPDATE
     tiling = ctx.tiling
     kernel = {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
-              "generic": "k_sweep_generic"}[tiling["kernel"]]
+              "generic": "k_sweep_generic", "generic_smem": "k_sweep_generic_smem"}[tiling["kernel"]]
     prof = PROFILED_TRAFFIC.get((args.workload, kernel))
     src_hash = kernel_source_hash()
     traffic = prof["dram_bytes_per_launch"] if prof and prof["src"] == src_hash else None

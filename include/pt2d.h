@@ -125,8 +125,10 @@ typedef struct {
     int32_t device;          /* CUDA device ordinal; -1 = current device            */
     int32_t profile;         /* nonzero: time every kernel launch with CUDA events  */
     int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 int8 slab in
-                                shared memory, 3 bit-packed slab in shared memory
-                                (2, 3: INVALID_ARG if it does not fit)               */
+                                shared memory (also for generic degree layouts and
+                                penalty terms), 3 bit-packed slab in shared memory
+                                (specialised layouts only; 2, 3: INVALID_ARG if it
+                                does not fit)                                        */
     int32_t walkers_per_thread; /* int8 shared-memory kernel: 4 or 8, others: 4;
                                    0 = automatic                                     */
     int32_t swap_mode;       /* PT2D_SWAP_2D (0): Algorithm 1.  PT2D_SWAP_JCOLUMN (1):
@@ -206,7 +208,8 @@ int64_t pt2d_launch_count(const pt2d_ctx *ctx);
 
 /* Sweep tiling the context chose: out[0] = kernel (1 slab in global memory, 2
  * int8 slab in shared memory, 3 bit-packed slab in shared memory, 4 generic
- * degree layout), out[1] = walkers per CTA, out[2] = threads per CTA,
+ * degree layout in global memory, 5 generic degree layout with the int8 slab in
+ * shared memory), out[1] = walkers per CTA, out[2] = threads per CTA,
  * out[3] = walkers per thread.  Host only.  Errors: INVALID_ARG (NULL). */
 int pt2d_tiling(const pt2d_ctx *ctx, int32_t out[4]);
 

@@ -250,9 +250,10 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     const int req_w = opt ? opt->walkers_per_cta : 0;
     if (req_w != 0 && (req_w < 4 || req_w > 128 || (req_w & (req_w - 1)))) return PT2D_ERR_INVALID_ARG;
     // shared-memory slab width: the widest that fits and still gives every SM a
-    // CTA, else the narrowest that fits; 0 = global kernel
+    // CTA, else the narrowest that fits; 0 = global kernel.  Layouts other than
+    // the specialised ones run the generic shared-memory kernel (int8 only).
     int sw = 0;
-    if (mode != 1 && specialised) {
+    if (mode == 0 || mode == 2) {
         if (req_w) {
             if (req_w >= 16 && fits(req_w)) sw = req_w;
         } else {
@@ -298,6 +299,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         ql = sw / 4;
         const int req_t = opt ? opt->walkers_per_thread : 0;
         if (req_t != 0 && req_t != 4 && req_t != 8) return PT2D_ERR_INVALID_ARG;
+        if (req_t == 8 && !specialised) return PT2D_ERR_INVALID_ARG;
         wpt = req_t ? req_t : 4;
         const int lanes = sw / wpt;  // threads per spin row segment
         const int tmax = wpt == 4 ? 1024 : 512;
@@ -615,7 +617,7 @@ int pt2d_tiling(const pt2d_ctx *c, int32_t out[4]) {
     const pt2d::SweepTiling &t = c->pp.tiling;
     const bool specialised =
         !c->pp.penalty && c->pp.DL == 2 && (c->pp.DC == 3 || c->pp.DC == 4 || c->pp.DC == 6);
-    out[0] = t.bits ? 3 : t.smem ? 2 : specialised ? 1 : 4;
+    out[0] = t.bits ? 3 : t.smem ? (specialised ? 2 : 5) : specialised ? 1 : 4;
     out[1] = 4 * t.lanes_per_spin;
     out[2] = t.threads;
     out[3] = t.walkers_per_thread;

@@ -101,6 +101,23 @@ __device__ __forceinline__ Quad load_quad(const Walkers &wk, int64_t col) {
                 bt.w * kNegL2E, pj.x, pj.y, pj.z, pj.w};
 }
 
+// New spin word of a quad from its four local fields H (Eq. 1 energy
+// differences) and Philox block r: the fast decision, with the exact contract
+// inside the uncertainty band.
+__device__ __forceinline__ uint32_t decide_fields(const Quad &q, int a0, int a1, int a2, int a3,
+                                                  const uint4 &r) {
+    float t0 = heatbath_fast(q.c0, a0, r.x), t1 = heatbath_fast(q.c1, a1, r.y);
+    float t2 = heatbath_fast(q.c2, a2, r.z), t3 = heatbath_fast(q.c3, a3, r.w);
+    // one branch for the four band tests; inside it the exact contract decides
+    if (fminf(fminf(fabsf(t0), fabsf(t1)), fminf(fabsf(t2), fabsf(t3))) <= kBand) {
+        if (fabsf(t0) <= kBand) t0 = heatbath_exact(q.b0, a0, r.x) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t1) <= kBand) t1 = heatbath_exact(q.b1, a1, r.y) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t2) <= kBand) t2 = heatbath_exact(q.b2, a2, r.z) > 0 ? -1.0f : 1.0f;
+        if (fabsf(t3) <= kBand) t3 = heatbath_exact(q.b3, a3, r.w) > 0 ? -1.0f : 1.0f;
+    }
+    return pack_signs(t0, t1, t2, t3);
+}
+
 // New spin word of one quad at one position.  `fetch(row)` returns the quad's
 // spin word of a row (shared or global memory).
 template <int DC, int DL>
@@ -123,20 +140,7 @@ __device__ __forceinline__ uint32_t decide4(const Rec<DC, DL> &rc, const Quad &q
         l2 += sbyte<2>(y[l]);
         l3 += sbyte<3>(y[l]);
     }
-    a0 += q.p0 * l0;
-    a1 += q.p1 * l1;
-    a2 += q.p2 * l2;
-    a3 += q.p3 * l3;
-    float t0 = heatbath_fast(q.c0, a0, r.x), t1 = heatbath_fast(q.c1, a1, r.y);
-    float t2 = heatbath_fast(q.c2, a2, r.z), t3 = heatbath_fast(q.c3, a3, r.w);
-    // one branch for the four band tests; inside it the exact contract decides
-    if (fminf(fminf(fabsf(t0), fabsf(t1)), fminf(fabsf(t2), fabsf(t3))) <= kBand) {
-        if (fabsf(t0) <= kBand) t0 = heatbath_exact(q.b0, a0, r.x) > 0 ? -1.0f : 1.0f;
-        if (fabsf(t1) <= kBand) t1 = heatbath_exact(q.b1, a1, r.y) > 0 ? -1.0f : 1.0f;
-        if (fabsf(t2) <= kBand) t2 = heatbath_exact(q.b2, a2, r.z) > 0 ? -1.0f : 1.0f;
-        if (fabsf(t3) <= kBand) t3 = heatbath_exact(q.b3, a3, r.w) > 0 ? -1.0f : 1.0f;
-    }
-    return pack_signs(t0, t1, t2, t3);
+    return decide_fields(q, a0 + q.p0 * l0, a1 + q.p1 * l1, a2 + q.p2 * l2, a3 + q.p3 * l3, r);
 }
 
 template <int DC, int DL, typename Fetch, typename Keys>

@@ -213,8 +213,10 @@ def test_degree_layouts_both_kernels(pt, kernel, wpt):
         assert_same(pt, ctx, orc)
 
 
-def test_generic_degree_kernel_with_fields(pt):
-    """Irregular instance with fields and degrees beyond the specialised kernels."""
+@pytest.mark.parametrize("kernel,wpc", [("auto", 0), ("smem", 16), ("smem", 128), ("global", 0)])
+def test_generic_degree_kernel_with_fields(pt, kernel, wpc):
+    """Irregular instance with fields and degrees beyond the specialised kernels,
+    on the generic kernel with the slab in shared memory and in global memory."""
     rng = np.random.default_rng(9)
     n = 90
     A = np.zeros((n, n), np.int16)
@@ -238,7 +240,9 @@ def test_generic_degree_kernel_with_fields(pt):
                                  np.arange(n + 1))
     beta = np.array([1e-4, 4e-4, 1e-3], np.float32)
     P = np.array([0, 300, 900, 2000], np.int32)
-    ctx, orc = both(pt, None, None, beta, P, 3, 5, [(24, 4)], phys=(phys_p, phys_o), trace=8)
+    ctx, orc = both(pt, None, None, beta, P, 3, 5, [(24, 4)], phys=(phys_p, phys_o), trace=8,
+                    kernel=kernel, wpc=wpc)
+    assert ctx.tiling["kernel"] == ("generic" if kernel == "global" else "generic_smem")
     assert ctx.num_colors == orc.oinst.n_colors
     assert np.array_equal(ctx.read(pt.COLORS), orc.oinst.color)
     assert_same(pt, ctx, orc)
@@ -397,17 +401,18 @@ def _penalty_pair(pt, n, groups, seed, chains=()):
     return phys_p, phys_o
 
 
-@pytest.mark.parametrize("swap_mode", ["2d", "jcolumn"])
-def test_general_penalty_terms_bit_exact(pt, swap_mode):
+@pytest.mark.parametrize("swap_mode,kernel", [("2d", "auto"), ("jcolumn", "auto"), ("2d", "global")])
+def test_general_penalty_terms_bit_exact(pt, swap_mode, kernel):
     """One-hot groups (negative link weights, penalty fields, g0) plus copy links
-    run on the generic kernel, bit-exact with the oracle."""
+    run on the generic kernels (slab in shared or global memory), bit-exact with
+    the oracle."""
     groups = [list(range(k, k + 4)) for k in range(0, 40, 4)] + [[1, 5, 9], [38, 2, 17, 23, 30]]
     phys = _penalty_pair(pt, 44, groups, 7, chains=[(40, 41), (41, 42), (42, 43)])
     beta = np.array([2e-4, 5e-4, 1.2e-3, 3e-3], np.float32)
     P = np.array([50, 200, 600], np.int32)
     ctx, orc = both(pt, None, None, beta, P, 5, 31337, [(30, 3), (12, 3)], phys=phys, trace=32,
-                    target=-2000, swap_mode=swap_mode)
-    assert ctx.tiling["kernel"] == "generic"
+                    target=-2000, swap_mode=swap_mode, kernel=kernel)
+    assert ctx.tiling["kernel"] == ("generic_smem" if kernel == "auto" else "generic")
     assert_same(pt, ctx, orc)
     assert np.all(ctx.read(pt.G) >= 0)
 
@@ -418,6 +423,18 @@ def test_batches_reject_general_penalty_terms(pt):
     with pytest.raises(pt.Pt2dError):
         batch.add(phys, np.array([1e-3], np.float32), np.array([10], np.int32), 1, 1, 0)
     batch.close()
+
+
+def test_three_copies_per_node_generic_smem(pt):
+    """The paper's sparsification for its ground-state runs (three copies per
+    node, ~N/3 couplings per copy) runs on the generic shared-memory kernel."""
+    inst = synth.wishart_planted(40, 0.75, 12)
+    beta = synth.beta_ladder(8, 0.1, 5.0, inst.scale)
+    P = synth.penalty_ladder(4, 0.5, 64.0, 32767)
+    ctx, orc = both(pt, inst, ("fixed", 3), beta, P, 6, 4040, [(40, 5), (10, 5)],
+                    target=inst.E_planted, trace=16)
+    assert ctx.tiling["kernel"] == "generic_smem"
+    assert_same(pt, ctx, orc)
 
 
 # ---- the J-column PT baseline ----------------------------------------------------------
