@@ -1,6 +1,7 @@
 // Host side of the 2D-PT C ABI (include/pt2d.h): validation, greedy colouring,
 // device layout, the Algorithm 1 event loop and the read/write interface.
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <cstdint>
 #include <cstdlib>
@@ -249,19 +250,39 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     };
     const int req_w = opt ? opt->walkers_per_cta : 0;
     if (req_w != 0 && (req_w < 4 || req_w > 128 || (req_w & (req_w - 1)))) return PT2D_ERR_INVALID_ARG;
-    // shared-memory slab width: the widest that fits and still gives every SM a
-    // CTA, else the narrowest that fits; 0 = global kernel.  Layouts other than
-    // the specialised ones run the generic shared-memory kernel (int8 only).
+    // Slab width choice.  Wider slabs share each neighbour record among more
+    // walkers; narrower ones give more CTAs.  A CTA (up to 1024 threads, ~60
+    // registers each, most of shared memory) holds an SM alone, so the grid runs
+    // in waves of `sms` CTAs and a last partial wave leaves SMs idle.  Take the
+    // widest fitting width that fills at least one wave with waves at least 85 %
+    // full, else the one with the fullest waves (the wider on ties); when no
+    // width fills one wave, the narrowest (most CTAs, most spin groups per CTA).
+    auto pick_width = [&](int widest, int narrowest, auto fits_width) -> int {
+        int best = 0, smallest = 0;
+        double best_eff = -1.0;
+        for (int cand = widest; cand >= narrowest; cand /= 2) {
+            if (!fits_width(cand)) continue;
+            smallest = cand;
+            const int64_t ctas = (walkers + cand - 1) / cand;
+            if (ctas < sms) continue;
+            const double waves = static_cast<double>(ctas) / sms;
+            const double eff = waves / std::ceil(waves);
+            if (eff >= 0.85) return cand;
+            if (eff > best_eff) {
+                best_eff = eff;
+                best = cand;
+            }
+        }
+        return best ? best : smallest;
+    };
+    // shared-memory slab width (0 = global kernel).  Layouts other than the
+    // specialised ones run the generic shared-memory kernel (int8 only).
     int sw = 0;
     if (mode == 0 || mode == 2) {
         if (req_w) {
             if (req_w >= 16 && fits(req_w)) sw = req_w;
         } else {
-            for (int cand = 128; cand >= 16; cand /= 2) {
-                if (!fits(cand)) continue;
-                sw = cand;
-                if ((walkers + cand - 1) / cand >= sms) break;
-            }
+            sw = pick_width(128, 16, fits);
         }
     }
     // bit-packed shared-memory slab when the int8 one does not fit (or when forced)
@@ -274,11 +295,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         if (req_w) {
             if (req_w >= 8 && fits_bits(req_w)) bw = req_w;
         } else {
-            for (int cand = 128; cand >= 8; cand /= 2) {
-                if (!fits_bits(cand)) continue;
-                bw = cand;
-                if ((walkers + cand - 1) / cand >= sms) break;
-            }
+            bw = pick_width(128, 8, fits_bits);
         }
         if (mode == 3 && bw == 0) return PT2D_ERR_INVALID_ARG;
     }
