@@ -573,13 +573,15 @@ def run_batched(args):
 def run_compare(args):
     """2D-PT against the J-column PT baseline (the paper's Fig. 3 comparison
     shape) on synthetic planted Wishart instances: N in {20, 30, 40, 50},
-    alpha = 0.75, copy chains of <= 3 original edges per copy (the batched
-    kernel's degree limit; the paper's runs used 3 copies per node),
-    I = 16 x J = 8.  2D-PT uses a linear P
-    ladder; J-column PT runs the same beta ladder in every column at the mean
-    of those penalties, with beta-swaps only, and keeps the best feasible
-    replica of its last row.  Both run as one batch each, `--cmp-events`
-    events of 50 sweeps; reported: the median over instances of the residual
+    alpha = 0.75, I = 16 x J = 8, sparsified either to <= 3 original edges per
+    copy (`--cmp-sparsify max_edges3`: each arm runs as one batch) or to three
+    copies per node, the paper's setting (`fixed3`: ~N/3 couplings per copy,
+    beyond the batched kernel's degree limit, so one context per instance on
+    the generic shared-memory kernel, spread over 16 streams).  2D-PT uses a
+    linear P ladder; J-column PT runs the same beta ladder in every column at
+    the mean of those penalties, with beta-swaps only, and keeps the best
+    feasible replica of its last row.  `--cmp-events` events of 50 sweeps;
+    reported: the median over instances of the residual
     energy per spin of the best feasible state so far, rho = (f - E_gs) / (N s),
     at log-spaced sweep counts, and the sweeps to reach rho <= 0.2 / 0.1 /
     0.05 / 0 (E_gs: the planted energy or anything lower either method found)."""
@@ -597,30 +599,46 @@ def run_compare(args):
     for N in Ns:
         for k in range(per_N):
             inst = synth.wishart_planted(N, 0.75, 5000 + 100 * N + k)
-            phys = pt.sparsify(inst.Jq, "max_edges", 3)
+            rule = ("max_edges", 3) if args.cmp_sparsify == "max_edges3" else ("fixed", 3)
+            phys = pt.sparsify(inst.Jq, *rule)
             probs.append((inst, phys, synth.beta_ladder(I, BETA_MIN, BETA_MAX, inst.scale),
                           synth.penalty_ladder(J, P_MIN, P_MAX, 32767)))
     stream = torch.cuda.Stream()
     out = {}
     traces = {}
     for mode in ("2d", "jcolumn"):
-        b = pt.Batch(1 << 30, 3, len(probs), stream=stream, trace_capacity=E, swap_mode=mode)
-        ids = []
-        for k, (inst, phys, beta, P) in enumerate(probs):
-            Pm = P if mode == "2d" else np.full(J, int(np.rint(P.mean())), np.int32)
-            ids.append(b.add(phys, beta, Pm, 1, 777 + k, inst.E_planted))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.run(E, interval)
-        e1.record(stream)
-        e1.synchronize()
-        secs = e0.elapsed_time(e1) / 1e3
-        tf = np.stack([b.read(i, pt.TRACE_F)[0] for i in ids])
-        tg = np.stack([b.read(i, pt.TRACE_G)[0] for i in ids])
+        ladders = [(P if mode == "2d" else np.full(J, int(np.rint(P.mean())), np.int32))
+                   for _, _, _, P in probs]
+        if args.cmp_sparsify == "max_edges3":
+            b = pt.Batch(1 << 30, 3, len(probs), stream=stream, trace_capacity=E, swap_mode=mode)
+            ids = [b.add(phys, beta, Pm, 1, 777 + k, inst.E_planted)
+                   for k, ((inst, phys, beta, _), Pm) in enumerate(zip(probs, ladders))]
+            t0 = time.perf_counter()
+            b.run(E, interval)
+            b.sync()
+            secs = time.perf_counter() - t0
+            tf = np.stack([b.read(i, pt.TRACE_F)[0] for i in ids])
+            tg = np.stack([b.read(i, pt.TRACE_G)[0] for i in ids])
+            b.close()
+        else:
+            streams = [torch.cuda.Stream() for _ in range(16)]
+            ctxs = []
+            for k, ((inst, phys, beta, _), Pm) in enumerate(zip(probs, ladders)):
+                c = pt.PT2D(phys, beta, Pm, 1, stream=streams[k % 16], trace_capacity=E, swap_mode=mode)
+                c.write(pt.TARGET, np.array([inst.E_planted], np.int64))
+                ctxs.append(c)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k, c in enumerate(ctxs):
+                c.run(E * interval, interval, 777 + k)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            tf = np.stack([c.read(pt.TRACE_F)[0] for c in ctxs])
+            tg = np.stack([c.read(pt.TRACE_G)[0] for c in ctxs])
+            for c in ctxs:
+                c.close()
         traces[mode] = (tf, tg)
         out[mode] = {"seconds": secs, "feasible_record_fraction": float((tg == 0).mean())}
-        b.close()
     # ground-state estimate per instance: the planted energy or anything lower found
     big = np.iinfo(np.int64).max
     E_gs = []
@@ -652,7 +670,8 @@ def run_compare(args):
         "metric": "residual energy per spin vs sweeps, 2D-PT vs J-column PT (same replicas)",
         "value": None, "unit": "rho", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
         "config": {"workload": f"{per_N} planted Wishart instances per N in {list(Ns)}, alpha 0.75, "
-                               f"<=3 edges per copy, I={I} x J={J}, {E} events of {interval} sweeps; "
+                               f"{'<=3 edges per copy' if args.cmp_sparsify == 'max_edges3' else '3 copies per node'}, "
+                               f"I={I} x J={J}, {E} events of {interval} sweeps; "
                                "J-column PT at the mean 2D-PT penalty"},
         "results": out,
     }
@@ -836,6 +855,7 @@ def main():
     ap.add_argument("--fig2-events", type=int, default=8000)
     ap.add_argument("--cmp-events", type=int, default=2000)
     ap.add_argument("--cmp-instances", type=int, default=64)
+    ap.add_argument("--cmp-sparsify", default="max_edges3", choices=["max_edges3", "fixed3"])
     ap.add_argument("--rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--drain", type=float, default=30.0)
