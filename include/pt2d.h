@@ -252,8 +252,11 @@ typedef struct pt2d_batch pt2d_batch;
 
 /* pool_bytes: device bytes for instances (ignored with opt->workspace, whose
  * size then includes the batch's bookkeeping); max_coupling_degree: largest
- * number of coupling neighbours of any spin that will be added (<= 6; links
- * <= 2 per spin); max_runs: most runs alive at once.  opt: stream, workspace,
+ * number of coupling neighbours of any spin that will be added: <= 6 (with at
+ * most 2 links per spin, copy constraints only) uses kernels specialised for
+ * that degree; larger values use a kernel that reads each problem's degrees at
+ * run time and also takes any number of links and general penalty terms
+ * (pt2d_instance lk_w, hk, g0); max_runs: most runs alive at once.  opt: stream, workspace,
  * trace_capacity, and the initial launch shape (pt2d_batch_shape below):
  * threads_per_cta (0 = 1024), sweep_kernel (= storage), walkers_per_cta
  * (= global_width, 0 = 32); balance starts at 2.  device.

@@ -54,7 +54,7 @@ __device__ void run_swap(const BatchArgs &a, const BatchRun &d, int run_index, u
     int8_t *best_state = reinterpret_cast<int8_t *>(pool + d.best_state);
     const int8_t *S = reinterpret_cast<const int8_t *>(pool + d.state);
     const int *recs = reinterpret_cast<const int *>(pool + d.rec);
-    const int pid_at = DC + DL;
+    const int pid_at = DC == 0 ? d.dc + d.dl : DC + DL;
 
     const bool inited = sc[kScInited] != 0;
     const int64_t nev = sc[kScEvents] + 1;
@@ -136,15 +136,42 @@ __device__ __forceinline__ void slab_sweeps(const BatchArgs &a, const BatchRun &
         for (int c = 0; c < d.C; ++c) {
             const int beg = __ldg(cofs + c), end = __ldg(cofs + c + 1);
             for (int pos = beg + grp; pos < end; pos += G) {
-                Rec<DC, DL> rc;
-                rc.load(rec, pos);
-                uint32_t x[DC], y[DL];
+                if constexpr (DC == 0) {  // runtime degrees, optional penalty terms
+                    const int dc = d.dc, dl = d.dl;
+                    const int *rc = reinterpret_cast<const int *>(rec) + static_cast<int64_t>(pos) * d.rec_vec * 4;
+                    const int h2 = __ldg(rc + dc + dl + 1);
+                    int a0 = h2, a1 = h2, a2 = h2, a3 = h2;
+                    const int kk = d.penalty ? __ldg(rc + 2 * dc + 2 * dl + 2) : 0;
+                    int l0 = kk, l1 = kk, l2 = kk, l3 = kk;
+                    for (int k = 0; k < dc; ++k) {
+                        const uint32_t x = fetch(__ldg(rc + k));
+                        const int j = __ldg(rc + dc + dl + 2 + k);
+                        a0 += j * sbyte<0>(x);
+                        a1 += j * sbyte<1>(x);
+                        a2 += j * sbyte<2>(x);
+                        a3 += j * sbyte<3>(x);
+                    }
+                    for (int k = 0; k < dl; ++k) {
+                        const uint32_t y = fetch_link(__ldg(rc + dc + k));
+                        const int w = d.penalty ? __ldg(rc + 2 * dc + dl + 2 + k) : 1;
+                        l0 += w * sbyte<0>(y);
+                        l1 += w * sbyte<1>(y);
+                        l2 += w * sbyte<2>(y);
+                        l3 += w * sbyte<3>(y);
+                    }
+                    const uint4 r = keys(make_uint4(static_cast<uint32_t>(__ldg(rc + dc + dl)), sweep, lq, c3));
+                    store(pos, decide_fields(q, a0 + q.p0 * l0, a1 + q.p1 * l1, a2 + q.p2 * l2, a3 + q.p3 * l3, r));
+                } else {
+                    Rec<DC, DL> rc;
+                    rc.load(rec, pos);
+                    uint32_t x[DC], y[DL];
 #pragma unroll
-                for (int k = 0; k < DC; ++k) x[k] = fetch(rc.nb(k));
+                    for (int k = 0; k < DC; ++k) x[k] = fetch(rc.nb(k));
 #pragma unroll
-                for (int l = 0; l < DL; ++l) y[l] = fetch_link(rc.lk(l));
-                const uint4 r = keys(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3));
-                store(pos, decide4<DC, DL>(rc, q, x, y, r));
+                    for (int l = 0; l < DL; ++l) y[l] = fetch_link(rc.lk(l));
+                    const uint4 r = keys(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3));
+                    store(pos, decide4<DC, DL>(rc, q, x, y, r));
+                }
             }
             __syncthreads();
         }
@@ -160,6 +187,41 @@ __device__ __forceinline__ void slab_energies(const BatchRun &d, const int4 *rec
     long long F0 = 0, F1 = 0, F2 = 0, F3 = 0;
     int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
     for (int pos = grp; pos < n; pos += G) {
+        if constexpr (DC == 0) {
+            const int dc = d.dc, dl = d.dl;
+            const int *rc = reinterpret_cast<const int *>(rec) + static_cast<int64_t>(pos) * d.rec_vec * 4;
+            const uint32_t xs = fetch(pos);
+            const int h4 = 2 * __ldg(rc + dc + dl + 1);
+            int cb[4] = {h4, h4, h4, h4};
+            for (int k = 0; k < dc; ++k) {
+                const uint32_t x = fetch(__ldg(rc + k));
+                const int j2 = __ldg(rc + dc + dl + 2 + k);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) cb[b] += j2 * sbyte_rt(x, b);
+            }
+            F0 += static_cast<long long>(sbyte<0>(xs)) * cb[0];
+            F1 += static_cast<long long>(sbyte<1>(xs)) * cb[1];
+            F2 += static_cast<long long>(sbyte<2>(xs)) * cb[2];
+            F3 += static_cast<long long>(sbyte<3>(xs)) * cb[3];
+            // twice g: weighted links from both ends, twice k of a down spin
+            for (int k = 0; k < dl; ++k) {
+                const int lp = __ldg(rc + dc + k);
+                if (lp == n) continue;  // padding link
+                const uint32_t y = fetch(lp);
+                const int w = d.penalty ? __ldg(rc + 2 * dc + dl + 2 + k) : 1;
+                g0 += w * (sbyte<0>(xs) != sbyte<0>(y));
+                g1 += w * (sbyte<1>(xs) != sbyte<1>(y));
+                g2 += w * (sbyte<2>(xs) != sbyte<2>(y));
+                g3 += w * (sbyte<3>(xs) != sbyte<3>(y));
+            }
+            if (d.penalty) {
+                const int k2 = 2 * __ldg(rc + 2 * dc + 2 * dl + 2);
+                g0 += sbyte<0>(xs) < 0 ? k2 : 0;
+                g1 += sbyte<1>(xs) < 0 ? k2 : 0;
+                g2 += sbyte<2>(xs) < 0 ? k2 : 0;
+                g3 += sbyte<3>(xs) < 0 ? k2 : 0;
+            }
+        } else {
         Rec<DC, DL> rc;
         rc.load(rec, pos);
         const uint32_t xs = fetch(pos);
@@ -187,6 +249,7 @@ __device__ __forceinline__ void slab_energies(const BatchRun &d, const int4 *rec
             g2 += sbyte<2>(xs) != sbyte<2>(y);
             g3 += sbyte<3>(xs) != sbyte<3>(y);
         }
+        }
     }
     unsigned long long *uf = reinterpret_cast<unsigned long long *>(s_F);
     atomicAdd(uf + lane_off + 0, static_cast<unsigned long long>(F0));
@@ -203,8 +266,9 @@ __device__ __forceinline__ void slab_energies(const BatchRun &d, const int4 *rec
 // init stream of the plain kernels).
 template <int DC, int DL>
 __device__ __forceinline__ uint32_t init_word(const BatchRun &d, const int4 *rec, int pos, uint32_t lq) {
+    const int pid_at = DC == 0 ? d.dc + d.dl : DC + DL;
     const uint32_t pid = static_cast<uint32_t>(
-        reinterpret_cast<const int *>(rec)[static_cast<int64_t>(pos) * d.rec_vec * 4 + DC + DL]);
+        reinterpret_cast<const int *>(rec)[static_cast<int64_t>(pos) * d.rec_vec * 4 + pid_at]);
     const uint4 r = philox4x32_10(make_uint4(pid, 0u, lq, (static_cast<uint32_t>(d.run) << 4) | kTagInit),
                                   d.k0, d.k1);
     return pack_signs(r.x < 0x80000000u ? -1.0f : 1.0f, r.y < 0x80000000u ? -1.0f : 1.0f,
@@ -392,7 +456,7 @@ __device__ __forceinline__ void slab_event(const BatchArgs &a, const BatchItem i
         int32_t *g_g = reinterpret_cast<int32_t *>(pool + d.fg + 8 * Rp);
         for (int i = threadIdx.x; i < SW; i += blockDim.x) {
             g_f[col0 + i] = -(s_F[i] / 4);
-            g_g[col0 + i] = s_G[i] / 2;
+            g_g[col0 + i] = s_G[i] / 2 + d.g0;
         }
     }
     // publish this slab; the CTA finishing the run's last slab does its swap event
@@ -439,6 +503,7 @@ size_t batch_small_smem_bytes() {
 cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state) {
     const int smem = smem_state + static_cast<int>(batch_small_smem_bytes());
     if (DL != 2) return cudaErrorInvalidValue;
+    if (DC == 0) return cudaFuncSetAttribute(k_batch<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (DC == 3) return cudaFuncSetAttribute(k_batch<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (DC == 4) return cudaFuncSetAttribute(k_batch<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (DC == 6) return cudaFuncSetAttribute(k_batch<6, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -448,6 +513,7 @@ cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state) {
 cudaError_t launch_batch(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st) {
     const size_t smem = static_cast<size_t>(a.smem_state) + batch_small_smem_bytes();
     if (DL != 2) return cudaErrorInvalidValue;
+    if (DC == 0) return launch_batch_variant<0, 0>(a, grid, threads, smem, st);
     if (DC == 3) return launch_batch_variant<3, 2>(a, grid, threads, smem, st);
     if (DC == 4) return launch_batch_variant<4, 2>(a, grid, threads, smem, st);
     if (DC == 6) return launch_batch_variant<6, 2>(a, grid, threads, smem, st);

@@ -44,6 +44,9 @@ struct BatchRun {
     int32_t mode;        // slab spins: 0 int8 in global memory, 1 int8 in shared memory,
                          // 2 bit-packed in shared memory
     int32_t swap_mode;   // PT2D_SWAP_2D or PT2D_SWAP_JCOLUMN
+    int32_t dc, dl;      // record degrees (used by the runtime-degree kernel)
+    int32_t penalty;     // records carry link weights K and the penalty field k
+    int32_t g0;          // constant term of g
     int32_t pad2;
     int64_t work;        // n * Rp, for ordering
 };
@@ -71,6 +74,8 @@ size_t batch_small_smem_bytes();
 inline int64_t batch_bits_bytes(int32_t n, int32_t sw) {
     return ((static_cast<int64_t>(n + 1) * (sw / 8) + 15) & ~int64_t{15}) + 64;
 }
+// DC = 0 selects the runtime-degree kernel (degrees and penalty terms read
+// from each run's descriptor).
 cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state);
 cudaError_t launch_batch(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
 

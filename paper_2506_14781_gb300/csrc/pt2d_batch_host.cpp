@@ -160,6 +160,7 @@ struct pt2d_batch {
     int32_t n_items = 0;
     int glob_sw = 32;                                 // slab width when spins stay in global memory
     int swap_mode = 0;                                // PT2D_SWAP_2D or PT2D_SWAP_JCOLUMN, all problems
+    bool generic = false;                             // runtime-degree kernel
     int storage = 0;                                  // pt2d_batch_shape::storage
     int balance = 2;                                  // pt2d_batch_shape::balance
     bool int8 = true;                                 // int8 shared-memory slabs allowed
@@ -186,6 +187,12 @@ int fail(pt2d_batch *b, cudaError_t e) {
         cudaError_t _e = (expr);                   \
         if (_e != cudaSuccess) return fail(b, _e); \
     } while (0)
+
+// A runtime-degree batch takes problems whose coupling degree is within the
+// declared cap (records may be padded up to 6 when the layout is small).
+bool degrees_fit(const pt2d_batch *b, const pt2d::Prep &pp) {
+    return pp.DC <= std::max(b->DC, 6);
+}
 
 void drop_graph(pt2d_batch *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -306,13 +313,14 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
     pt2d::BatchArgs a{b->pool, b->d_runs, b->d_items, b->n_runs, b->n_items, b->d_queue, interval,
                       b->smem_state, b->d_status};
     const int grid = std::min(b->grid, b->n_items);
-    BK(b, pt2d::batch_kernel_attributes(b->DC, 2, b->smem_state));
+    const int kdc = b->generic ? 0 : b->DC;
+    BK(b, pt2d::batch_kernel_attributes(kdc, 2, b->smem_state));
     // one launch per event: the counter is cleared, then every slab of every run
     auto enqueue = [&]() -> cudaError_t {
         for (int32_t e = 0; e < events; ++e) {
             cudaError_t x = cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream);
             if (x != cudaSuccess) return x;
-            x = pt2d::launch_batch(a, b->DC, 2, grid, b->threads, b->stream);
+            x = pt2d::launch_batch(a, kdc, 2, grid, b->threads, b->stream);
             if (x != cudaSuccess) return x;
         }
         return cudaSuccess;
@@ -354,7 +362,8 @@ size_t pt2d_batch_instance_bytes(const pt2d_batch *b, const pt2d_instance *inst,
     pt2d_options o;
     pt2d_default_options(&o);
     o.sweep_kernel = 1;
-    if (pt2d::prepare(inst, I, nullptr, J, nullptr, 1, &o, pp, b->DC)) return 0;
+    if (pt2d::prepare(inst, I, nullptr, J, nullptr, 1, &o, pp, b->generic ? 0 : b->DC)) return 0;
+    if (b->generic && !degrees_fit(b, pp)) return 0;
     const int32_t R = I * J;
     return align_up(block_layout(inst->n, pp.C, pp.rec_vec, I, J, R, pow2_at_least(R), runs, b->trace_cap)
                         .total);
@@ -362,7 +371,7 @@ size_t pt2d_batch_instance_bytes(const pt2d_batch *b, const pt2d_instance *inst,
 
 int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_degree,
                       int32_t max_runs, const pt2d_options *opt) {
-    if (!out || pool_bytes == 0 || max_runs < 1 || max_coupling_degree < 0 || max_coupling_degree > 6)
+    if (!out || pool_bytes == 0 || max_runs < 1 || max_coupling_degree < 0 || max_coupling_degree > (1 << 20))
         return PT2D_ERR_INVALID_ARG;
     *out = nullptr;
     pt2d_options dflt;
@@ -383,7 +392,12 @@ int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_
     pt2d_batch *b = new (std::nothrow) pt2d_batch;
     if (!b) return PT2D_ERR_OOM;
     b->device = dev;
-    b->DC = max_coupling_degree <= 3 ? 3 : (max_coupling_degree <= 4 ? 4 : 6);
+    // up to 6 coupling neighbours (and 2 links): the specialised kernels, records
+    // padded to 3, 4 or 6; more: the runtime-degree kernel, any links and
+    // general penalty terms (DC keeps the declared cap, launched as DC = 0)
+    b->generic = max_coupling_degree > 6;
+    b->DC = b->generic ? max_coupling_degree
+                       : (max_coupling_degree <= 3 ? 3 : (max_coupling_degree <= 4 ? 4 : 6));
     b->trace_cap = std::max<int32_t>(opt->trace_capacity, 0);
     b->max_runs = max_runs;
     b->threads = opt->threads_per_cta > 0 ? opt->threads_per_cta : 1024;
@@ -468,8 +482,9 @@ int pt2d_batch_add(pt2d_batch *b, const pt2d_instance *inst, int32_t I, const fl
     o.sweep_kernel = 1;
     Inst in;
     pt2d::Prep pp;
-    int st = pt2d::prepare(inst, I, beta, J, P, 1, &o, pp, b->DC);
+    int st = pt2d::prepare(inst, I, beta, J, P, 1, &o, pp, b->generic ? 0 : b->DC);
     if (st) return st;
+    if (b->generic && !degrees_fit(b, pp)) return PT2D_ERR_INVALID_ARG;
     in.n = pp.n;
     in.I = I;
     in.J = J;
@@ -527,6 +542,10 @@ int pt2d_batch_add(pt2d_batch *b, const pt2d_instance *inst, int32_t I, const fl
         d.run = r;
         d.trace_cap = b->trace_cap;
         d.rec_vec = in.rec_vec;
+        d.dc = pp.DC;
+        d.dl = pp.DL;
+        d.penalty = pp.penalty ? 1 : 0;
+        d.g0 = pp.g0;
         d.work = static_cast<int64_t>(in.n) * in.Rp;
         in.desc.push_back(d);
         scal[static_cast<size_t>(r) * pt2d::kScCount + pt2d::kScTarget] = target ? target[r] : INT64_MIN;

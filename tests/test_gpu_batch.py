@@ -233,3 +233,65 @@ def test_full_size_uneven_batch_sampled_runs(pt):
                         ("ACC_P", "acc_P"), ("ACC_B", "acc_B"), ("SUM_F", "sum_f")):
             assert np.array_equal(batch.read(ids[k], getattr(pt, w)), getattr(orc, attr)), (k, w)
     batch.close()
+
+
+def _penalty_problem(pt, n, groups, seed, I, J):
+    """A one-hot constrained problem (general penalty terms) with random couplings."""
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n), np.int16)
+    for a in range(n):
+        for b in range(a + 1, n):
+            if rng.random() < 0.3:
+                A[a, b] = A[b, a] = rng.integers(-300, 301)
+    cp_ptr = np.concatenate([[0], np.cumsum((A != 0).sum(1))]).astype(np.int32)
+    cp_col = np.concatenate([np.nonzero(A[a])[0] for a in range(n)]).astype(np.int32)
+    cp_J = np.concatenate([A[a][A[a] != 0] for a in range(n)]).astype(np.int16)
+    lk_ptr, lk_col, lk_w, hk, g0 = pt.onehot_penalty(n, groups)
+    phys = pt.PhysicalInstance(n, cp_ptr, cp_col, cp_J, lk_ptr, lk_col, h=rng.integers(-50, 51, n).astype(np.int32),
+                               lk_w=lk_w, hk=hk, g0=g0)
+    beta = np.geomspace(2e-4, 4e-3, I).astype(np.float32)
+    P = np.linspace(40, 400, J).astype(np.int32)
+    return dict(phys=phys, beta=beta, P=P, runs=1, seed=seed, target=-10 ** 6)
+
+
+@pytest.mark.parametrize("kernel", ["auto", "global", "bits"])
+def test_runtime_degree_batch_matches_plain(pt, kernel):
+    """A batch declared with a coupling degree above 6 runs every problem on the
+    runtime-degree kernel: three copies per node (~N/3 couplings per copy),
+    one-hot penalty terms and ordinary <= 3-edge chains together, each equal to
+    its plain context."""
+    probs = [
+        _problem(pt, 30, 0.75, 41, ("fixed", 3), 8, 4, 2),
+        _problem(pt, 45, 0.5, 42, ("fixed", 3), 16, 8, 1),
+        _problem(pt, 60, 0.5, 43, ("max_edges", 3), 8, 8, 1),
+        _penalty_problem(pt, 40, [list(range(k, k + 5)) for k in range(0, 40, 5)], 44, 8, 4),
+        _penalty_problem(pt, 24, [[0, 1, 2], [3, 4, 5], [2, 6, 9, 12]], 45, 4, 4),
+    ]
+    batch = pt.Batch(1 << 28, max_coupling_degree=64, max_runs=16, trace_capacity=16, sweep_kernel=kernel)
+    ids = [batch.add(p["phys"], p["beta"], p["P"], p["runs"], p["seed"], p["target"]) for p in probs]
+    batch.run(3, 5)
+    batch.run(4, 5)
+    for pr, bid in zip(probs, ids):
+        ctx = _plain(pt, pr, 35, 5, 16)
+        _assert_same(pt, batch, bid, ctx)
+        ctx.close()
+    batch.close()
+
+
+def test_runtime_degree_server_takes_penalty_requests(pt):
+    pr = _penalty_problem(pt, 30, [list(range(k, k + 3)) for k in range(0, 30, 3)], 46, 8, 4)
+    srv = pt.Server(1 << 26, 64, 8, 5, 4)
+    rid = srv.submit(pr["phys"], pr["beta"], pr["P"], pr["seed"], pr["target"], 60)
+    for _ in range(100):
+        srv.step()
+        if srv.status(rid)["state"] == "done":
+            break
+    got = srv.status(rid, with_state=True)
+    assert got["state"] == "done" and got["sweeps_done"] == 60
+    ctx = _plain(pt, dict(pr, runs=1), 60, 5, 4)
+    assert ctx.read(pt.BEST_F)[0] == got["best_f"]
+    assert ctx.read(pt.BEST_EVENT)[0] == got["best_event"]
+    if got["best_event"] >= 0:
+        assert np.array_equal(ctx.read(pt.BEST_STATE)[0], got["best_state"])
+    ctx.close()
+    srv.close()
