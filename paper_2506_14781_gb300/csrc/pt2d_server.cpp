@@ -25,9 +25,10 @@ namespace {
 
 struct Request {
     int32_t n = 0, I = 0, J = 0;
-    std::vector<int32_t> cp_ptr, cp_col, lk_ptr, lk_col, h, color;
-    std::vector<int16_t> cp_J;
-    bool has_h = false, has_color = false;
+    std::vector<int32_t> cp_ptr, cp_col, lk_ptr, lk_col, h, color, hk;
+    std::vector<int16_t> cp_J, lk_w;
+    bool has_h = false, has_color = false, has_lk_w = false, has_hk = false;
+    int64_t g0 = 0;
     std::vector<float> beta;
     std::vector<int32_t> P;
     uint64_t seed = 0;
@@ -49,6 +50,9 @@ struct Request {
         v.lk_col = lk_col.data();
         v.h = has_h ? h.data() : nullptr;
         v.color = has_color ? color.data() : nullptr;
+        v.lk_w = has_lk_w ? lk_w.data() : nullptr;
+        v.hk = has_hk ? hk.data() : nullptr;
+        v.g0 = g0;
         return v;
     }
 };
@@ -158,6 +162,15 @@ int pt2d_server_submit(pt2d_server *s, const pt2d_instance *inst, int32_t I, con
         r.color.assign(inst->color, inst->color + n);
         r.has_color = true;
     }
+    if (inst->lk_w) {
+        r.lk_w.assign(inst->lk_w, inst->lk_w + r.lk_ptr[n]);
+        r.has_lk_w = true;
+    }
+    if (inst->hk) {
+        r.hk.assign(inst->hk, inst->hk + n);
+        r.has_hk = true;
+    }
+    r.g0 = inst->g0;
     r.beta.assign(beta, beta + I);
     r.P.assign(P, P + J);
     r.seed = seed;
