@@ -508,6 +508,14 @@ int pt2d_onehot_penalty(int32_t n, int32_t n_groups, const int32_t *grp_ptr, con
                         int32_t *lk_ptr, int32_t *lk_col, int16_t *lk_w, int32_t cap, int32_t *nnz,
                         int32_t *hk, int64_t *g0);
 
+/* ---- test hook ------------------------------------------------------------ */
+/* Host-side fault injection for failure-handling tests: the next `count`
+ * device allocations of context workspaces and batch pools fail as if the
+ * device were out of memory (pt2d_create / pt2d_batch_create return
+ * PT2D_ERR_OOM and leave nothing allocated).  count <= 0 clears it.
+ * Process-wide; returns the count that was pending. */
+int32_t pt2d_debug_fail_allocations(int32_t count);
+
 /* ---- diagnostics: the device arithmetic, element-wise -------------------- */
 /* Each runs the same device functions the sweep and swap kernels use, on
  * `count` elements given in host memory, and copies results back (synchronous,

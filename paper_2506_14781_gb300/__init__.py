@@ -514,6 +514,12 @@ def adaptive_schedule(inst: PhysicalInstance, *, beta0: float, P0: int, max_rows
     return beta[:I.value].copy(), P[:J.value].copy(), int(k.value)
 
 
+def debug_fail_allocations(count: int) -> int:
+    """Test hook: make the next `count` workspace / pool allocations fail as
+    out of memory (pt2d_debug_fail_allocations); returns the pending count."""
+    return int(_lib.lib().pt2d_debug_fail_allocations(int(count)))
+
+
 def _diag(name, arrays, outs, count):
     st = getattr(_lib.lib(), name)(*[_p(a) for a in arrays], *[_p(o) for o in outs], int(count))
     _lib.check(st, name)

@@ -15,6 +15,7 @@
 #include "../../include/pt2d.h"
 #include "pt2d_batch.h"
 #include "pt2d_prep.h"
+#include "pt2d_trace.h"
 
 namespace {
 
@@ -442,7 +443,7 @@ int pt2d_batch_create(pt2d_batch **out, size_t pool_bytes, int32_t max_coupling_
         b->pool = static_cast<uint8_t *>(opt->workspace);
         b->pool_bytes = opt->workspace_bytes;
     } else {
-        if (cudaMalloc(&b->pool, pool_bytes + head) != cudaSuccess) {
+        if (pt2d::device_alloc(reinterpret_cast<void **>(&b->pool), pool_bytes + head) != cudaSuccess) {
             cudaGetLastError();
             pt2d_batch_destroy(b);
             return PT2D_ERR_OOM;
@@ -577,6 +578,7 @@ int pt2d_batch_remove(pt2d_batch *b, int64_t id) {
 }
 
 int pt2d_batch_run(pt2d_batch *b, int32_t events, int32_t swap_interval) {
+    pt2d::TraceRange trace("pt2d_batch_run");
     if (!b || events < 0 || swap_interval < 1) return PT2D_ERR_INVALID_ARG;
     cudaSetDevice(b->device);
     return launch(b, events, swap_interval);
@@ -600,6 +602,7 @@ int pt2d_batch_set_shape(pt2d_batch *b, const pt2d_batch_shape *shape) {
 }
 
 int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, pt2d_batch_shape *chosen) {
+    pt2d::TraceRange trace("pt2d_batch_autotune");
     if (!b || events < 1 || swap_interval < 1) return PT2D_ERR_INVALID_ARG;
     cudaSetDevice(b->device);
     struct Events {

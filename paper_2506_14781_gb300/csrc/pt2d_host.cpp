@@ -1,6 +1,7 @@
 // Host side of the 2D-PT C ABI (include/pt2d.h): validation, greedy colouring,
 // device layout, the Algorithm 1 event loop and the read/write interface.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <cstdint>
@@ -14,6 +15,7 @@
 #include "../../include/pt2d.h"
 #include "pt2d_internal.h"
 #include "pt2d_prep.h"
+#include "pt2d_trace.h"
 
 namespace {
 
@@ -33,6 +35,8 @@ struct Carver {
         return p;
     }
 };
+
+std::atomic<int32_t> g_fail_allocs{0};  // injected allocation failures still to come
 
 // Validates a symmetric CSR (no self loops, no duplicates, equal values both
 // ways; `val` may be NULL for unweighted links) and returns sorted adjacency.
@@ -68,6 +72,14 @@ int check_csr(int32_t n, const int32_t *ptr, const int32_t *col, const int16_t *
 }  // namespace
 
 namespace pt2d {
+
+cudaError_t device_alloc(void **ptr, size_t bytes) {
+    int32_t left = g_fail_allocs.load();
+    while (left > 0) {
+        if (g_fail_allocs.compare_exchange_weak(left, left - 1)) return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
 
 int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, const int32_t *P,
             int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc) {
@@ -487,6 +499,10 @@ void pt2d_default_options(pt2d_options *opt) {
     opt->device = -1;
 }
 
+int32_t pt2d_debug_fail_allocations(int32_t count) {
+    return g_fail_allocs.exchange(count > 0 ? count : 0);
+}
+
 const char *pt2d_strerror(int status) {
     switch (status) {
         case PT2D_OK: return "ok";
@@ -512,6 +528,7 @@ int pt2d_workspace_size(const pt2d_instance *inst, int32_t I, int32_t J, int32_t
 
 int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const float *beta, int32_t J,
                 const int32_t *P, int32_t runs, const pt2d_options *opt) {
+    pt2d::TraceRange trace("pt2d_create");
     if (!out || !beta || !P) return PT2D_ERR_INVALID_ARG;
     *out = nullptr;
     pt2d_options dflt;
@@ -539,7 +556,7 @@ int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const floa
         c->ws = opt->workspace;
         c->ws_bytes = opt->workspace_bytes;
     } else {
-        if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+        if (pt2d::device_alloc(&c->ws, need) != cudaSuccess) {
             cudaGetLastError();
             delete c;
             return PT2D_ERR_OOM;
@@ -643,6 +660,7 @@ int pt2d_tiling(const pt2d_ctx *c, int32_t out[4]) {
 int64_t pt2d_launch_count(const pt2d_ctx *c) { return c ? c->launches : 0; }
 
 int pt2d_run(pt2d_ctx *c, int64_t sweeps, int32_t interval, uint64_t seed) {
+    pt2d::TraceRange trace("pt2d_run");
     if (!c || sweeps < 0 || interval < 1) return PT2D_ERR_INVALID_ARG;
     const int64_t nev = sweeps / interval;
     if (c->adopt_seed) {

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/pt2d.h"
+#include "pt2d_trace.h"
 
 namespace {
 
@@ -185,6 +186,7 @@ int pt2d_server_submit(pt2d_server *s, const pt2d_instance *inst, int32_t I, con
 }
 
 int pt2d_server_step(pt2d_server *s, int32_t *active, int32_t *queued, int32_t *finished) {
+    pt2d::TraceRange trace("pt2d_server_step");
     if (!s) return PT2D_ERR_INVALID_ARG;
     // admit in arrival order while the pool has room
     while (!s->queue.empty() && static_cast<int32_t>(s->by_batch.size()) < s->max_runs) {

@@ -118,3 +118,11 @@ def test_create_fails_loudly_without_gpu(pt):
     phys = pt.sparsify(inst.Jq, "fixed", 2)
     with pytest.raises(pt.Pt2dError):
         pt.PT2D(phys, [1e-5, 2e-5], [100, 200], 1)
+
+
+def test_allocation_failure_hook_counts_without_a_gpu():
+    import paper_2506_14781_gb300 as pt
+
+    assert pt.debug_fail_allocations(3) == 0
+    assert pt.debug_fail_allocations(0) == 3
+    assert pt.debug_fail_allocations(-5) == 0
