@@ -42,7 +42,7 @@ def test_injected_allocation_failures(pt):
     ctx.run(20, 5, 1)
     assert ctx.read(pt.COUNTERS)[1] == 4
     ctx.close()
-    b = pt.Batch(1 << 24, 3, 4)
+    b = pt.Batch(1 << 24, 64, 4)  # two copies of 12 nodes: ~6 couplings per copy
     b.add(phys, beta, P, 1, 1, 0)
     b.run(2, 5)
     b.close()
