@@ -22,11 +22,12 @@
  * Numerical contract (identical on the CPU oracle and the GPU):
  *  - couplings are int16, fields and penalties integers, so f, g, E and the
  *    local field H_a = E(s_a=-1) - E(s_a=+1)
- *        = 2 sum_b J_ab s_b + 2 h_a + P_j sum_{links l of a} s_l
+ *        = 2 sum_b J_ab s_b + 2 h_a + P_j (sum_{links l of a} K_al s_l + k_a)
  *    are exact integers (|H_a| < 2^24 is required);
- *  - g = number of copy links (a,b) with s_a != s_b (copy constraint of the
- *    section "Graph sparsification with copy constraints", normalised so that a
- *    broken link counts 1);
+ *  - g = g0 + sum_{links a<b} K_ab [s_a != s_b] + sum_a k_a [s_a = -1]; for copy
+ *    constraints (K = 1, k = 0, g0 = 0) the number of copy links with
+ *    s_a != s_b, normalised so that a broken link counts 1 (see pt2d_instance);
+ *  - swap_mode selects Algorithm 1 (default) or the J-column PT baseline;
  *  - random words: Philox4x32-10 keyed by the 64-bit seed; counter
  *    (c0, c1, c2, (run << 4) | tag) with
  *      sweep: c0 = spin id, c1 = global sweep index, c2 = walker / 4, word walker % 4
