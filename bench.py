@@ -11,6 +11,8 @@ round of P- or beta-swaps and the bottom-right record.  The int8 spin state
 --workload n800: N = 800 (213,551 physical spins), I = 64 x J = 16, 16 runs
 (3.5 GB of spins), same ladders and interval.
 --workload batched / serving: the uneven batch and the request stream.
+--workload constrained: 3-colouring of a random cubic graph with one-hot
+constraints (general penalty terms, generic kernels), I = 16 x J = 8, 256 runs.
 
 Metric: spin updates per second (physical spins x replicas x sweeps / time).
 
@@ -67,6 +69,8 @@ PROFILED_TRAFFIC = {
     # captured at 4 of the 16 runs and scaled by the walkers
     ("n800", "k_sweep_bits"): dict(src="ceabe32d2d4e2a4a", dram_bytes_per_launch=19_655_536_000,
                                    profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
+    ("constrained", "k_sweep_generic_smem"): dict(src="ceabe32d2d4e2a4a", dram_bytes_per_launch=341_629_184,
+                                                  profile="profiles/k_sweep_generic_smem_colouring.md"),
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h")
 
@@ -735,6 +739,117 @@ def run_fig2(args):
     print(json.dumps(line))
 
 
+def run_constrained(args):
+    """General constraint functions (Eq. 1 with g beyond copy links): 3-colouring
+    of a random cubic graph, V = 2000 vertices (n = 6000 spins, coupling
+    degree 3, two one-hot links per spin), one-hot groups expanded by the
+    library (pt2d_onehot_penalty), I = 16 x J = 8 (the batch's largest grid),
+    256 runs (32,768 replicas, 197 MB of spins, larger than L2), swap
+    interval 50.  The plain context runs it on the generic shared-memory
+    kernel (weighted links, penalty fields, g0); the same runs then go
+    through the runtime-degree batch (identical trajectories).  Reports spin
+    updates/s with the sweep kernel's ALU roofline and how many runs found a
+    proper colouring (g = 0, f = -k W)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # a one-GPU workload
+    import torch
+
+    import paper_2506_14781_gb300 as pt
+    import synth
+
+    V, k, I, J, runs, interval = 2000, 3, 16, 8, args.runs or 256, 50
+    prob = synth.colouring(V, k, 7)
+    lk_ptr, lk_col, lk_w, hk, g0 = pt.onehot_penalty(prob.n, prob.groups)
+    phys = pt.PhysicalInstance(prob.n, prob.cp_ptr, prob.cp_col, prob.cp_J, lk_ptr, lk_col, h=prob.h,
+                               lk_w=lk_w, hk=hk, g0=g0)
+    # f moves by at most 12 per flip; the last column's penalty outweighs that
+    beta = np.geomspace(0.05, 2.0, I).astype(np.float32)
+    P = np.array([1, 2, 3, 5, 8, 12, 17, 24], np.int32)[:J]
+    n, R = prob.n, I * J
+    updates_per_event = n * R * runs * interval
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    ctx = pt.PT2D(phys, beta, P, runs, stream=stream, trace_capacity=args.warmup + args.steps, profile=True)
+    ctx.write(pt.TARGET, np.full(runs, prob.f_proper, np.int64))
+    seed = 2024
+    with torch.cuda.stream(stream):
+        ctx.run(interval * args.warmup, interval, seed)
+    ctx.sync()
+    ms0, l0 = ctx.kernel_time(0)
+    n_launch0 = ctx.launch_count
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        start.record(stream)
+        ctx.run(interval * args.steps, interval, seed)
+        end.record(stream)
+        end.synchronize()
+    elapsed_ms = start.elapsed_time(end)
+    sweep_ms, launches = ctx.kernel_time(0)
+    sweep_ms -= ms0
+    launches -= l0
+    gpu_launches = ctx.launch_count - n_launch0
+    value = updates_per_event * args.steps / (elapsed_ms / 1e3)
+    avg_launch_ms = sweep_ms / max(launches, 1)
+    tiling = ctx.tiling
+    kernel = {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
+              "generic": "k_sweep_generic", "generic_smem": "k_sweep_generic_smem"}[tiling["kernel"]]
+    peaks, peak_src = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    alu = updates_per_event * OPS_PER_UPDATE / (avg_launch_ms / 1e3) / 1e12
+    prof = PROFILED_TRAFFIC.get(("constrained", kernel))
+    src_hash = kernel_source_hash()
+    traffic = prof["dram_bytes_per_launch"] if prof and prof["src"] == src_hash else None
+    best = ctx.read(pt.BEST_F)
+    solved = ctx.read(pt.SOLVED_EVENT)
+    feasible = best < np.iinfo(np.int64).max
+    F_best = prob.same_colour_weight(best[feasible])
+    events_done = args.warmup + args.steps
+    # the same runs through the runtime-degree batch
+    batch = pt.Batch(1 << 31, max_coupling_degree=64, max_runs=runs, stream=stream,
+                     trace_capacity=events_done)
+    bid = batch.add(phys, beta, P, runs, seed, prob.f_proper)
+    batch.run(args.warmup, interval)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    batch.run(args.steps, interval)
+    b1.record(stream)
+    b1.synchronize()
+    batch_ms = b0.elapsed_time(b1)
+    same = bool(np.array_equal(batch.read(bid, pt.BEST_F), best) and
+                np.array_equal(batch.read(bid, pt.F), ctx.read(pt.F)))
+    batch.close()
+    ctx.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8 spins, int32 fields, f32 decisions",
+        "data": "synthetic (seeded random cubic graph, 3-colouring with one-hot constraints)",
+        "config": {"workload": f"3-colouring of a random cubic graph, V={V} ({n} spins, one-hot groups), "
+                               f"I={I} x J={J}, {runs} runs, swap every {interval} sweeps",
+                   "physical_spins": n, "replicas": R * runs, "tiling": tiling,
+                   "l2": f"state {n * R * runs / 1e6:.0f} MB > L2 (129 MB); no flush"},
+        "roofline": {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tops/s (lane-ops)",
+                     "frac": alu / alu_peak, "traffic": traffic, "kernel": kernel, "kernel_src": src_hash,
+                     "traffic_source": prof["profile"] if traffic is not None else
+                     "null: no ncu capture of this kernel source",
+                     "ops_per_update": OPS_PER_UPDATE, "avg_launch_ms": avg_launch_ms, "launches": launches,
+                     "peak_source": f"{sm_count} SMs x 128 lanes x max clock ({peak_src})"},
+        "batched_runtime_degree": {"updates_per_s": updates_per_event * args.steps / (batch_ms / 1e3),
+                                   "identical_results": same},
+        "quality": {"runs_with_proper_colouring": int((solved >= 0).sum()), "runs": runs,
+                    "median_event_solved": float(np.median(solved[solved >= 0])) if (solved >= 0).any() else None,
+                    "runs_feasible": int(feasible.sum()),
+                    "best_same_colour_edges_median": float(np.median(F_best)) if F_best.size else None,
+                    "edges": int(prob.edges.shape[0]), "sweeps_run": events_done * interval},
+        "gpu_launches": int(gpu_launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def run_serving(args):
     """Serving workload: a Poisson stream of constrained Ising requests at
     `--rates` requests per minute for `--duration` seconds each, then up to
@@ -835,7 +950,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=100, help="oracle sample, N=200 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2"])
+    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2", "constrained"])
     ap.add_argument("--fig2-events", type=int, default=8000)
     ap.add_argument("--cmp-events", type=int, default=2000)
     ap.add_argument("--cmp-instances", type=int, default=64)
@@ -864,6 +979,8 @@ def main():
         run_compare(args)
     elif args.workload == "fig2":
         run_fig2(args)
+    elif args.workload == "constrained":
+        run_constrained(args)
     else:
         run_gpu(args)
 

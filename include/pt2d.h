@@ -509,6 +509,28 @@ int pt2d_onehot_penalty(int32_t n, int32_t n_groups, const int32_t *grp_ptr, con
                         int32_t *lk_ptr, int32_t *lk_col, int16_t *lk_w, int32_t cap, int32_t *nnz,
                         int32_t *hk, int64_t *g0);
 
+/* Penalty terms of linear equality constraints (the general g >= 0 of Eq. 1
+ * beyond copy links): for constraints c over spins a with integer
+ * coefficients A_a and right-hand side b_c (binary x_a = [s_a = +1]),
+ *   g = sum_c (sum_{a in c} A_a x_a - b_c)^2,
+ * zero exactly on the feasible states.  Written in the links form of
+ * pt2d_instance with S = sum_{a in c} A_a: each constraint adds (S - b_c)^2 to
+ * g0, A_a (2 b_c - S) to k_a of each member and -A_a A_b to K of each pair of
+ * members (pairs in several constraints add up; pairs that sum to 0 are
+ * dropped).  One-hot groups are A = 1, b = 1 (pt2d_onehot_penalty).  An
+ * inequality sum A_a x_a <= b (b >= 0) takes slack spins z_t with
+ * coefficients 1, 2, 4, ..., 2^(T-1) and b + 1 - 2^T, T = floor(log2(b + 1)),
+ * whose sum takes every value 0..b, and becomes the equality
+ * sum A_a x_a + sum c_t z_t = b over the spins and the slacks.
+ * Constraints: CSR con_ptr[n_cons+1], con_col (spin ids in [0, n), no repeats
+ * within a constraint), coef (int32, parallel to con_col), rhs[n_cons] (int64).
+ * Outputs as pt2d_onehot_penalty.  Errors: INVALID_ARG (bad constraints, NULL
+ * inputs or outputs, cap too small: *nnz still receives the size needed; a
+ * weight K outside int16, a field k outside int32, |b| or g0 above 2^62). */
+int pt2d_equality_penalty(int32_t n, int32_t n_cons, const int32_t *con_ptr, const int32_t *con_col,
+                          const int32_t *coef, const int64_t *rhs, int32_t *lk_ptr, int32_t *lk_col,
+                          int16_t *lk_w, int32_t cap, int32_t *nnz, int32_t *hk, int64_t *g0);
+
 /* ---- test hook ------------------------------------------------------------ */
 /* Host-side fault injection for failure-handling tests: the next `count`
  * device allocations of context workspaces and batch pools fail as if the

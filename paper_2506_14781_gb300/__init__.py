@@ -19,7 +19,7 @@ from ._lib import (ACC_B, ACC_P, BEST_EVENT, BEST_F, BEST_STATE, COLORS, COUNTER
 
 __all__ = [
     "PhysicalInstance", "sparsify", "greedy_color", "PT2D", "Batch", "PoolFull", "Server",
-    "Pt2dError",
+    "Pt2dError", "onehot_penalty", "equality_penalty", "adaptive_schedule",
     "diag_philox",
     "diag_pt_exp", "diag_heatbath", "diag_swap_accept", "STATES", "WALKER_AT", "F", "G",
     "COUNTERS", "TRACE_F", "TRACE_G", "BEST_F", "BEST_EVENT", "BEST_STATE", "SOLVED_EVENT",
@@ -117,6 +117,38 @@ def onehot_penalty(n: int, groups) -> tuple:
     _lib.check(L.pt2d_onehot_penalty(int(n), len(groups), _p(grp_ptr), _p(grp_col), _p(lk_ptr),
                                      _p(lk_col), _p(lk_w), int(lk_col.size), C.byref(nnz), _p(hk),
                                      C.byref(g0)), "pt2d_onehot_penalty")
+    return lk_ptr, lk_col[:nnz.value].copy(), lk_w[:nnz.value].copy(), hk, int(g0.value)
+
+
+def equality_penalty(n: int, constraints) -> tuple:
+    """Penalty terms (lk_ptr, lk_col, lk_w, hk, g0) of linear equality
+    constraints: `constraints` is a list of (spin ids, integer coefficients,
+    right-hand side b), g = sum_c (sum_a A_a [s_a = +1] - b_c)^2
+    (pt2d_equality_penalty)."""
+    con_ptr = np.concatenate([[0], np.cumsum([len(c[0]) for c in constraints])]).astype(np.int32)
+    if constraints:
+        con_col = np.ascontiguousarray(np.concatenate([np.asarray(c[0], np.int32) for c in constraints]),
+                                       dtype=np.int32)
+        coef = np.ascontiguousarray(np.concatenate([np.asarray(c[1], np.int64) for c in constraints]),
+                                    dtype=np.int64)
+        if coef.size and (coef.min() < -2 ** 31 or coef.max() >= 2 ** 31):
+            raise ValueError("equality_penalty: coefficients must fit int32")
+        coef = coef.astype(np.int32)
+    else:
+        con_col = np.zeros(0, np.int32)
+        coef = np.zeros(0, np.int32)
+    rhs = np.array([int(c[2]) for c in constraints], np.int64)
+    L = _lib.lib()
+    lk_ptr = np.zeros(n + 1, np.int32)
+    hk = np.zeros(n, np.int32)
+    nnz = C.c_int32()
+    g0 = C.c_int64()
+    args = (int(n), len(constraints), _p(con_ptr), _p(con_col), _p(coef), _p(rhs), _p(lk_ptr))
+    L.pt2d_equality_penalty(*args, None, None, 0, C.byref(nnz), _p(hk), C.byref(g0))
+    lk_col = np.zeros(max(nnz.value, 1), np.int32)
+    lk_w = np.zeros(max(nnz.value, 1), np.int16)
+    _lib.check(L.pt2d_equality_penalty(*args, _p(lk_col), _p(lk_w), int(lk_col.size), C.byref(nnz), _p(hk),
+                                       C.byref(g0)), "pt2d_equality_penalty")
     return lk_ptr, lk_col[:nnz.value].copy(), lk_w[:nnz.value].copy(), hk, int(g0.value)
 
 

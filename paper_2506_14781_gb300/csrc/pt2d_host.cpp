@@ -916,30 +916,50 @@ int pt2d_greedy_color(const pt2d_instance *inst, int32_t *color, int32_t *n_colo
     return PT2D_OK;
 }
 
-int pt2d_onehot_penalty(int32_t n, int32_t n_groups, const int32_t *grp_ptr, const int32_t *grp_col,
-                        int32_t *lk_ptr, int32_t *lk_col, int16_t *lk_w, int32_t cap, int32_t *nnz,
-                        int32_t *hk, int64_t *g0) {
-    if (n < 1 || n_groups < 0 || !grp_ptr || !lk_ptr || !nnz || !hk || !g0) return PT2D_ERR_INVALID_ARG;
-    if (grp_ptr[0] != 0) return PT2D_ERR_INVALID_ARG;
-    for (int32_t c = 0; c < n_groups; ++c)
-        if (grp_ptr[c + 1] < grp_ptr[c]) return PT2D_ERR_INVALID_ARG;
-    if (grp_ptr[n_groups] > 0 && !grp_col) return PT2D_ERR_INVALID_ARG;
-    // (sum_{a in c} x_a - 1)^2 with x_a = 1 - [s_a = -1]:
-    //   (m - 1)^2 + (2 - m) sum_a [s_a = -1] - sum_{a<b in c} [s_a != s_b]
-    std::vector<std::map<int32_t, int64_t>> K(n);
-    std::vector<int64_t> k(n, 0);
-    int64_t c0 = 0;
-    for (int32_t c = 0; c < n_groups; ++c) {
-        const int32_t b = grp_ptr[c], e = grp_ptr[c + 1], m = e - b;
-        std::vector<int32_t> mem(grp_col + b, grp_col + e);
+namespace {
+
+// Penalty terms of g = sum_c (sum_{a in c} A_a x_a - b_c)^2, x_a = [s_a = +1],
+// in the links form.  With y_a = [s_a = -1] = 1 - x_a and S = sum_a A_a, each
+// constraint equals (sum_a A_a y_a - (S - b))^2; y^2 = y and
+// 2 y_a y_b = y_a + y_b - [s_a != s_b] turn it into
+//   (S - b)^2 + sum_a A_a (2b - S) y_a - sum_{a<b} A_a A_b [s_a != s_b],
+// so g0 += (S - b)^2, k_a += A_a (2b - S), K_ab -= A_a A_b.  coef / rhs NULL
+// mean all ones (one-hot groups).
+int equality_penalty(int32_t n, int32_t n_cons, const int32_t *con_ptr, const int32_t *con_col,
+                     const int32_t *coef, const int64_t *rhs, int32_t *lk_ptr, int32_t *lk_col,
+                     int16_t *lk_w, int32_t cap, int32_t *nnz, int32_t *hk, int64_t *g0) {
+    using i128 = __int128;
+    if (n < 1 || n_cons < 0 || !con_ptr || !lk_ptr || !nnz || !hk || !g0) return PT2D_ERR_INVALID_ARG;
+    if (con_ptr[0] != 0) return PT2D_ERR_INVALID_ARG;
+    for (int32_t c = 0; c < n_cons; ++c)
+        if (con_ptr[c + 1] < con_ptr[c]) return PT2D_ERR_INVALID_ARG;
+    if (con_ptr[n_cons] > 0 && !con_col) return PT2D_ERR_INVALID_ARG;
+    const i128 kLim = static_cast<i128>(1) << 62;
+    std::vector<std::map<int32_t, i128>> K(n);
+    std::vector<i128> k(n, 0);
+    i128 c0 = 0;
+    for (int32_t c = 0; c < n_cons; ++c) {
+        const int32_t beg = con_ptr[c], m = con_ptr[c + 1] - beg;
+        std::vector<std::pair<int32_t, int64_t>> mem(m);
+        for (int32_t i = 0; i < m; ++i) mem[i] = {con_col[beg + i], coef ? coef[beg + i] : 1};
         std::sort(mem.begin(), mem.end());
+        const i128 b = rhs ? rhs[c] : 1;
+        i128 S = 0;
         for (int32_t i = 0; i < m; ++i) {
-            if (mem[i] < 0 || mem[i] >= n || (i > 0 && mem[i] == mem[i - 1])) return PT2D_ERR_INVALID_ARG;
-            k[mem[i]] += 2 - m;
-            for (int32_t j = 0; j < m; ++j)
-                if (j != i) K[mem[i]][mem[j]] -= 1;
+            if (mem[i].first < 0 || mem[i].first >= n || (i > 0 && mem[i].first == mem[i - 1].first))
+                return PT2D_ERR_INVALID_ARG;
+            S += mem[i].second;
         }
-        c0 += static_cast<int64_t>(m - 1) * (m - 1);
+        if (b > kLim || b < -kLim) return PT2D_ERR_INVALID_ARG;
+        for (int32_t i = 0; i < m; ++i) {
+            const i128 A = mem[i].second;
+            k[mem[i].first] += A * (2 * b - S);
+            for (int32_t j = 0; j < m; ++j)
+                if (j != i) K[mem[i].first][mem[j].first] -= A * mem[j].second;
+            if (k[mem[i].first] > kLim || k[mem[i].first] < -kLim) return PT2D_ERR_INVALID_ARG;
+        }
+        c0 += (S - b) * (S - b);
+        if (c0 > kLim) return PT2D_ERR_INVALID_ARG;
     }
     int64_t total = 0;
     for (int32_t a = 0; a < n; ++a)
@@ -962,8 +982,26 @@ int pt2d_onehot_penalty(int32_t n, int32_t n_groups, const int32_t *grp_ptr, con
         if (k[a] < INT32_MIN || k[a] > INT32_MAX) return PT2D_ERR_INVALID_ARG;
         hk[a] = static_cast<int32_t>(k[a]);
     }
-    *g0 = c0;
+    *g0 = static_cast<int64_t>(c0);
     return PT2D_OK;
+}
+
+}  // namespace
+
+int pt2d_equality_penalty(int32_t n, int32_t n_cons, const int32_t *con_ptr, const int32_t *con_col,
+                          const int32_t *coef, const int64_t *rhs, int32_t *lk_ptr, int32_t *lk_col,
+                          int16_t *lk_w, int32_t cap, int32_t *nnz, int32_t *hk, int64_t *g0) {
+    if (n_cons > 0 && con_ptr && con_ptr[n_cons] > 0 && !coef) return PT2D_ERR_INVALID_ARG;
+    if (n_cons > 0 && !rhs) return PT2D_ERR_INVALID_ARG;
+    return equality_penalty(n, n_cons, con_ptr, con_col, coef, rhs, lk_ptr, lk_col, lk_w, cap, nnz, hk, g0);
+}
+
+int pt2d_onehot_penalty(int32_t n, int32_t n_groups, const int32_t *grp_ptr, const int32_t *grp_col,
+                        int32_t *lk_ptr, int32_t *lk_col, int16_t *lk_w, int32_t cap, int32_t *nnz,
+                        int32_t *hk, int64_t *g0) {
+    // (sum_{a in c} x_a - 1)^2: all coefficients 1, right-hand side 1
+    return equality_penalty(n, n_groups, grp_ptr, grp_col, nullptr, nullptr, lk_ptr, lk_col, lk_w, cap, nnz,
+                            hk, g0);
 }
 
 int pt2d_sparsify(int32_t N, const int16_t *Jq, int32_t rule, int32_t param, int32_t *n_out,

@@ -3,7 +3,8 @@
 This package produces the *workloads* only: planted Wishart Ising instances
 (the problem class the paper's ground-state experiments use, Section
 "Ground-state optimization under constraints", citing Hamze et al. 2020),
-temperature / penalty ladders and request-arrival streams.  It holds none of
+one-hot constrained colouring problems, temperature / penalty ladders and
+request-arrival streams.  It holds none of
 the method's arithmetic (no sparsification, colouring, sweeps or swaps), so
 both the CPU oracle and the GPU library can consume the same inputs without
 sharing any method code.
@@ -11,6 +12,7 @@ sharing any method code.
 from .wishart import WishartInstance, wishart_planted
 from .ladders import beta_ladder, penalty_ladder
 from .arrivals import batch_specs, poisson_arrivals, request_specs
+from .constrained import ColoringProblem, colouring, random_cubic_graph, slack_coefficients
 
 __all__ = [
     "WishartInstance",
@@ -20,4 +22,8 @@ __all__ = [
     "poisson_arrivals",
     "request_specs",
     "batch_specs",
+    "ColoringProblem",
+    "colouring",
+    "random_cubic_graph",
+    "slack_coefficients",
 ]

@@ -278,6 +278,42 @@ def test_runtime_degree_batch_matches_plain(pt, kernel):
     batch.close()
 
 
+def _colouring_problem(pt, V, k, seed, capacity, I, J):
+    """k-colouring of a random cubic graph: one-hot groups plus per-colour
+    capacity inequalities through slack spins (library expansion)."""
+    prob = synth.colouring(V, k, seed, w_max=2)
+    n = prob.n
+    cons = [(g, [1] * len(g), 1) for g in prob.groups]
+    sl = synth.slack_coefficients(capacity)
+    for c in range(k):
+        cons.append(([v * k + c for v in range(V)] + list(range(n, n + len(sl))), [1] * V + sl, capacity))
+        n += len(sl)
+    pad = n - prob.n
+    lk_ptr, lk_col, lk_w, hk, g0 = pt.equality_penalty(n, cons)
+    phys = pt.PhysicalInstance(n, np.concatenate([prob.cp_ptr, np.full(pad, prob.cp_ptr[-1], np.int32)]),
+                               prob.cp_col, prob.cp_J, lk_ptr, lk_col,
+                               h=np.concatenate([prob.h, np.zeros(pad, np.int32)]), lk_w=lk_w, hk=hk, g0=g0)
+    beta = np.geomspace(0.02, 1.5, I).astype(np.float32)
+    P = np.linspace(1, 10, J).astype(np.int32)
+    return dict(phys=phys, beta=beta, P=P, runs=1, seed=seed, target=prob.f_proper)
+
+
+@pytest.mark.parametrize("kernel", ["auto", "global"])
+def test_runtime_degree_batch_runs_equality_constraints(pt, kernel):
+    """Colouring problems with one-hot and slack-encoded capacity constraints
+    (link degree ~V/k) in the runtime-degree batch, each equal to its plain
+    context."""
+    probs = [_colouring_problem(pt, 18, 3, 51, 7, 8, 4), _colouring_problem(pt, 30, 4, 52, 9, 4, 4)]
+    batch = pt.Batch(1 << 28, max_coupling_degree=64, max_runs=8, trace_capacity=16, sweep_kernel=kernel)
+    ids = [batch.add(p["phys"], p["beta"], p["P"], p["runs"], p["seed"], p["target"]) for p in probs]
+    batch.run(5, 6)
+    for pr, bid in zip(probs, ids):
+        ctx = _plain(pt, pr, 30, 6, 16)
+        _assert_same(pt, batch, bid, ctx)
+        ctx.close()
+    batch.close()
+
+
 def test_runtime_degree_server_takes_penalty_requests(pt):
     pr = _penalty_problem(pt, 30, [list(range(k, k + 3)) for k in range(0, 30, 3)], 46, 8, 4)
     srv = pt.Server(1 << 26, 64, 8, 5, 4)

@@ -425,6 +425,50 @@ def test_batches_reject_general_penalty_terms(pt):
     batch.close()
 
 
+def _colouring_pair(pt, V, k, seed, capacity=None):
+    """A k-colouring of a random cubic graph with one-hot groups, optionally
+    with "at most `capacity` vertices per colour" inequalities through slack
+    spins; each side expands the constraints with its own routine."""
+    from oracle.penalties import equality
+
+    prob = synth.colouring(V, k, seed, w_max=3)
+    n = prob.n
+    cons = [(g, [1] * len(g), 1) for g in prob.groups]
+    if capacity is not None:
+        sl = synth.slack_coefficients(capacity)
+        for c in range(k):
+            slack = list(range(n, n + len(sl)))
+            n += len(sl)
+            cons.append(([v * k + c for v in range(V)] + slack, [1] * V + sl, capacity))
+    pad = n - prob.n  # slack spins carry no cost
+    cp_ptr = np.concatenate([prob.cp_ptr, np.full(pad, prob.cp_ptr[-1], np.int32)])
+    h = np.concatenate([prob.h, np.zeros(pad, np.int32)])
+    sides = []
+    for expand in (pt.equality_penalty, equality):
+        sides.append(expand(n, cons))
+    (p1, c1, w1, k1, g1), (p2, c2, w2, k2, g2) = sides
+    phys_p = pt.PhysicalInstance(n, cp_ptr, prob.cp_col, prob.cp_J, p1, c1, h=h, lk_w=w1, hk=k1, g0=g1)
+    phys_o = oracle.PhysInstance(n, cp_ptr, prob.cp_col, prob.cp_J, p2, c2, h, n, np.arange(n, dtype=np.int32),
+                                 np.arange(n + 1, dtype=np.int32), lk_w=w2, hk=k2, g0=g2)
+    return prob, (phys_p, phys_o)
+
+
+@pytest.mark.parametrize("capacity,kernel", [(None, "auto"), (None, "global"), (9, "auto"), (9, "global")])
+def test_colouring_with_equality_constraints_bit_exact(pt, capacity, kernel):
+    """Graph colouring with one-hot constraints, and with per-colour capacity
+    inequalities through slack spins (dense constraint rows, weights up to
+    -capacity^2 / 4 between slacks), bit-exact with the oracle on the generic
+    kernels."""
+    prob, phys = _colouring_pair(pt, 24, 3, 5, capacity)
+    beta = np.array([0.02, 0.08, 0.3, 1.0], np.float32)
+    P = np.array([1, 3, 8], np.int32)
+    ctx, orc = both(pt, None, None, beta, P, 5, 2468, [(60, 6), (24, 6)], phys=phys, trace=32,
+                    target=prob.f_proper, kernel=kernel)
+    assert ctx.tiling["kernel"] == ("generic_smem" if kernel == "auto" else "generic")
+    assert_same(pt, ctx, orc)
+    assert np.all(ctx.read(pt.G) >= 0)
+
+
 def test_three_copies_per_node_generic_smem(pt):
     """The paper's sparsification for its ground-state runs (three copies per
     node, ~N/3 couplings per copy) runs on the generic shared-memory kernel."""

@@ -166,3 +166,110 @@ def test_planted_penalty_mistake_fails_stationarity(tmp_path, old, new):
             se = per_run.std(ddof=1) / np.sqrt(8)
             zmax = max(zmax, abs(per_run.mean() - pi @ g) / max(se, 1e-9))
     assert zmax > 8.0, zmax
+
+
+# ---- linear equality constraints (one-hot generalised, slack-encoded inequalities) ----
+def _residual_definition(S, constraints):
+    x = (S > 0).astype(np.int64)
+    g = np.zeros(S.shape[0], np.int64)
+    for ids, coef, b in constraints:
+        g += (x[:, list(ids)] @ np.asarray(coef, np.int64) - int(b)) ** 2
+    return g
+
+
+def _equality_sets():
+    import synth
+
+    rng = np.random.default_rng(17)
+    sets = [
+        (10, [([0, 1, 2, 3], [1, 1, 1, 1], 1)]),                               # one-hot
+        (10, [([0, 1, 2, 3], [2, -1, 3, 1], 2), ([3, 4, 5], [1, 1, 1], 0),    # mixed signs, b = 0
+              ([1, 6, 7, 8, 9], [-2, 1, 4, -3, 1], -1)]),                      # negative rhs
+        (12, [([int(a) for a in rng.choice(12, 6, replace=False)],
+               [int(c) for c in rng.integers(-4, 5, 6)], int(rng.integers(-3, 6))) for _ in range(4)]),
+    ]
+    # inequality 2 x0 + 3 x1 + x2 + 2 x3 <= 4 with slack spins 4.. (coefficients 1, 2, 1)
+    sl = synth.slack_coefficients(4)
+    ids = [0, 1, 2, 3] + list(range(4, 4 + len(sl)))
+    sets.append((4 + len(sl) + 2, [(ids, [2, 3, 1, 2] + sl, 4), ([4 + len(sl), 4 + len(sl) + 1], [1, 1], 1)]))
+    return sets
+
+
+def test_equality_expansion_equals_the_definition_on_every_state():
+    """g of the expanded links form equals sum_c (sum A x - b)^2 on all 2^n
+    states, for one-hot, mixed-sign, negative right-hand-side, overlapping and
+    slack-encoded constraints."""
+    from oracle.penalties import equality
+
+    for n, cons in _equality_sets():
+        lk_ptr, lk_col, lk_w, hk, g0 = equality(n, cons)
+        inst = PhysInstance(n, np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int16),
+                            lk_ptr, lk_col, None, n, np.arange(n, dtype=np.int32),
+                            np.arange(n + 1, dtype=np.int32), lk_w=lk_w, hk=hk, g0=g0)
+        oi = oracle.OracleInstance(inst)
+        S = _all_states(n)
+        g_orc = np.array([oi.constraint_g(s) for s in S])
+        assert np.array_equal(g_orc, _residual_definition(S, cons)), cons
+
+
+def test_equality_with_unit_coefficients_is_the_onehot_expansion():
+    from oracle.penalties import equality
+
+    for groups, n in ((GROUPS, 12), ([[0, 1], [1, 2], [0, 2]], 3), ([], 4)):
+        a = equality(n, [(g, [1] * len(g), 1) for g in groups])
+        b = onehot(n, groups)
+        for x, y in zip(a[:4], b[:4]):
+            assert np.array_equal(x, y)
+        assert a[4] == b[4]
+
+
+def test_slack_coefficients_cover_exactly_zero_to_b():
+    import synth
+
+    for b in range(0, 70):
+        c = synth.slack_coefficients(b)
+        sums = {sum(x * y for x, y in zip(bits, c)) for bits in itertools.product([0, 1], repeat=len(c))}
+        assert sums == set(range(b + 1)), (b, c)
+        assert len(c) == (b + 1).bit_length() - 1 + (0 if (b + 1) & b == 0 else 1)
+
+
+def test_library_equality_expansion_equals_the_oracle():
+    import paper_2506_14781_gb300 as pt
+    from oracle.penalties import equality
+
+    for n, cons in _equality_sets():
+        mine = pt.equality_penalty(n, cons)
+        ref = equality(n, cons)
+        for x, y in zip(mine[:4], ref[:4]):
+            assert np.array_equal(x, y)
+        assert mine[4] == ref[4]
+    # a pair weight outside int16 is refused by both
+    big = [([0, 1], [300, 200], 100)]
+    with pytest.raises(ValueError):
+        equality(2, big)
+    with pytest.raises(pt.Pt2dError):
+        pt.equality_penalty(2, big)
+    # repeated spin inside a constraint
+    with pytest.raises(pt.Pt2dError):
+        pt.equality_penalty(3, [([0, 1, 0], [1, 1, 1], 1)])
+
+
+def test_colouring_problem_cost_is_four_times_the_same_colour_weight():
+    """The colouring input's Ising cost f equals 4 F - k W (F the weight of
+    monochromatic edges) on every feasible state of a small graph, and a
+    proper colouring has f = -k W."""
+    import synth
+
+    prob = synth.colouring(6, 3, 4, w_max=3)
+    deg = np.bincount(prob.edges.ravel(), minlength=prob.V)
+    assert np.all(deg == 3)
+    inst = PhysInstance(prob.n, prob.cp_ptr, prob.cp_col, prob.cp_J, np.zeros(prob.n + 1, np.int32),
+                        np.zeros(0, np.int32), prob.h, prob.n, np.arange(prob.n, dtype=np.int32),
+                        np.arange(prob.n + 1, dtype=np.int32))
+    for col in itertools.product(range(3), repeat=prob.V):
+        s = -np.ones(prob.n, np.int8)
+        s[np.arange(prob.V) * 3 + np.array(col)] = 1
+        f = _f_definition(inst, s[None])[0]
+        F = sum(int(w) for (u, v), w in zip(prob.edges.tolist(), prob.w.tolist()) if col[u] == col[v])
+        assert f == 4 * F - 3 * prob.W
+        assert prob.same_colour_weight(f) == F
