@@ -210,7 +210,8 @@ int64_t pt2d_launch_count(const pt2d_ctx *ctx);
 /* Sweep tiling the context chose: out[0] = kernel (1 slab in global memory, 2
  * int8 slab in shared memory, 3 bit-packed slab in shared memory, 4 generic
  * degree layout in global memory, 5 generic degree layout with the int8 slab in
- * shared memory), out[1] = walkers per CTA, out[2] = threads per CTA,
+ * shared memory, 6 penalty terms with coupling width 3, 4 or 6 and link width
+ * 2 or 3, int8 slab in shared memory), out[1] = walkers per CTA, out[2] = threads per CTA,
  * out[3] = walkers per thread.  Host only.  Errors: INVALID_ARG (NULL). */
 int pt2d_tiling(const pt2d_ctx *ctx, int32_t out[4]);
 

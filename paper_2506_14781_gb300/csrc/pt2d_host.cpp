@@ -14,6 +14,7 @@
 
 #include "../../include/pt2d.h"
 #include "pt2d_internal.h"
+#include "pt2d_penalty.h"
 #include "pt2d_prep.h"
 #include "pt2d_trace.h"
 
@@ -196,6 +197,11 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     } else if (!penalty && dlmax <= 2 && dcmax <= 6) {
         DL = 2;
         DC = dcmax <= 3 ? 3 : (dcmax <= 4 ? 4 : 6);
+    } else if (penalty && force_dc == 0 && dcmax <= 6 && dlmax <= 3) {
+        // padded up to a layout of the penalty-specialised kernel (padding
+        // entries point at the zero row with J = 0, K = 0)
+        DC = dcmax <= 3 ? 3 : (dcmax <= 4 ? 4 : 6);
+        DL = dlmax <= 2 ? 2 : 3;
     } else {
         DC = std::max(dcmax, 1);
         DL = std::max(dlmax, 1);
@@ -356,6 +362,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.tiling.smem = sw != 0;
     pp.tiling.bits = bw != 0;
     pp.tiling.walkers_per_thread = wpt;
+    pp.pen_kernel = penalty && sw != 0 && wpt == 4 && pt2d::penalty_kernel_degrees(DC, DL);
     // neighbour references become byte offsets into the shared-memory slab
     const int scale = sw ? sw : (bw ? bw / 8 : 1);
     if (scale > 1) {
@@ -651,7 +658,7 @@ int pt2d_tiling(const pt2d_ctx *c, int32_t out[4]) {
     const pt2d::SweepTiling &t = c->pp.tiling;
     const bool specialised =
         !c->pp.penalty && c->pp.DL == 2 && (c->pp.DC == 3 || c->pp.DC == 4 || c->pp.DC == 6);
-    out[0] = t.bits ? 3 : t.smem ? (specialised ? 2 : 5) : specialised ? 1 : 4;
+    out[0] = t.bits ? 3 : t.smem ? (specialised ? 2 : (c->pp.pen_kernel ? 6 : 5)) : specialised ? 1 : 4;
     out[1] = 4 * t.lanes_per_spin;
     out[2] = t.threads;
     out[3] = t.walkers_per_thread;
@@ -688,8 +695,13 @@ int pt2d_run(pt2d_ctx *c, int64_t sweeps, int32_t interval, uint64_t seed) {
             ev[1] = take_events(c);
             CK(c, cudaEventRecord(ev[0].first, s));
         }
-        CK(c, pt2d::launch_sweeps(c->L, c->wk, c->pp.tiling, c->pp.Rp / 4, seed,
-                                  static_cast<uint32_t>(c->sweeps_done), interval, s));
+        if (c->pp.pen_kernel) {
+            CK(c, pt2d::launch_penalty_sweeps(c->L, c->wk, c->pp.tiling, c->pp.Rp / 4, seed,
+                                              static_cast<uint32_t>(c->sweeps_done), interval, s));
+        } else {
+            CK(c, pt2d::launch_sweeps(c->L, c->wk, c->pp.tiling, c->pp.Rp / 4, seed,
+                                      static_cast<uint32_t>(c->sweeps_done), interval, s));
+        }
         if (c->profile) {
             CK(c, cudaEventRecord(ev[0].second, s));
             CK(c, cudaEventRecord(ev[1].first, s));

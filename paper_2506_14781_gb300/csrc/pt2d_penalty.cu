@@ -1,0 +1,216 @@
+// Shared-memory sweep kernel for instances with general penalty terms (Eq. 1
+// with a constraint function g beyond copy links: weighted links K, penalty
+// fields k, constant g0) and small degrees.
+//
+//  k_sweep_penalty_smem<DC, DL>  the sweep block of one event of Algorithm 1
+//      with the CTA's int8 replica slab in shared memory, as k_sweep_smem,
+//      reading the penalty record layout [nb x DC, lk x DL, pid, 2h,
+//      2J x DC, K x DL, k] with compile-time offsets (16-byte loads, unrolled
+//      neighbour loops), then f and g of the final sweep.
+//
+// The heat-bath field of spin a is H_a = 2 sum_b J_ab s_b + 2h_a +
+// P (sum_l K_al s_l + k_a); padding neighbours and links point at the slab's
+// zero row (and carry J = 0 / K = 0), so they add nothing.  The arithmetic
+// (Philox counters, decision sequence, exact integer fields) is the same as in
+// the runtime-degree kernels, so results are bit-identical to them.
+#include <cstdint>
+
+#include "pt2d_device.cuh"
+#include "pt2d_internal.h"
+#include "pt2d_penalty.h"
+#include "pt2d_sweep.cuh"
+
+namespace pt2d {
+namespace {
+
+template <int DC, int DL>
+struct PenRec {
+    static constexpr int kInts = 2 * DC + 2 * DL + 3;
+    static constexpr int kVec = (kInts + 3) / 4;
+    int v[kVec * 4];
+    __device__ __forceinline__ void load(const int4 *base, int pos) {
+        const int4 *p = base + static_cast<int64_t>(pos) * kVec;
+#pragma unroll
+        for (int i = 0; i < kVec; ++i) reinterpret_cast<int4 *>(v)[i] = __ldg(p + i);
+    }
+    __device__ __forceinline__ int nb(int k) const { return v[k]; }
+    __device__ __forceinline__ int lk(int l) const { return v[DC + l]; }
+    __device__ __forceinline__ int pid() const { return v[DC + DL]; }
+    __device__ __forceinline__ int h2() const { return v[DC + DL + 1]; }
+    __device__ __forceinline__ int j2(int k) const { return v[DC + DL + 2 + k]; }
+    __device__ __forceinline__ int w(int l) const { return v[2 * DC + DL + 2 + l]; }
+    __device__ __forceinline__ int kk() const { return v[2 * DC + 2 * DL + 2]; }
+};
+
+// Neighbour references in the records are byte offsets row * SW into the slab.
+template <int DC, int DL>
+__global__ void __launch_bounds__(1024, 1) k_sweep_penalty_smem(Layout L, Walkers wk, int sw_shift,
+                                                                int32_t quads_per_run, RoundKeys rk,
+                                                                uint32_t sweep0, int32_t nsweeps) {
+    extern __shared__ __align__(16) int8_t smp[];
+    const int SW = 1 << sw_shift;
+    const int QL = SW >> 2;
+    const int lane = threadIdx.x & (QL - 1);
+    const int grp = threadIdx.x >> (sw_shift - 2);
+    const int G = blockDim.x >> (sw_shift - 2);
+    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * SW;
+    const int64_t quad = col0 / 4 + lane;
+    const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
+    const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
+    const uint32_t c3 = (run << 4) | kTagSweep;
+    const int lane_off = 4 * lane;
+    const Quad q = load_quad(wk, col0 + lane_off);
+    const KeysConst keys{rk};
+    const int vec_per_row = SW >> 4;
+    const int64_t nvec = static_cast<int64_t>(L.n + 1) * vec_per_row;
+    for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
+        const int64_t row = i / vec_per_row;
+        const int part = static_cast<int>(i - row * vec_per_row);
+        reinterpret_cast<uint4 *>(smp)[i] =
+            *reinterpret_cast<const uint4 *>(L.S + row * L.Wc + col0 + 16 * part);
+    }
+    __syncthreads();
+    auto word = [&](int off) -> uint32_t { return *reinterpret_cast<const uint32_t *>(smp + off + lane_off); };
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
+        for (int c = 0; c < L.C; ++c) {
+            const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                PenRec<DC, DL> rc;
+                rc.load(L.rec, pos);
+                uint32_t x[DC], y[DL];
+#pragma unroll
+                for (int k = 0; k < DC; ++k) x[k] = word(rc.nb(k));
+#pragma unroll
+                for (int l = 0; l < DL; ++l) y[l] = word(rc.lk(l));
+                const uint4 r = keys(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3));
+                int a0 = rc.h2(), a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const int j = rc.j2(k);
+                    a0 += j * sbyte<0>(x[k]);
+                    a1 += j * sbyte<1>(x[k]);
+                    a2 += j * sbyte<2>(x[k]);
+                    a3 += j * sbyte<3>(x[k]);
+                }
+                int l0 = rc.kk(), l1 = l0, l2 = l0, l3 = l0;
+#pragma unroll
+                for (int l = 0; l < DL; ++l) {
+                    const int w = rc.w(l);
+                    l0 += w * sbyte<0>(y[l]);
+                    l1 += w * sbyte<1>(y[l]);
+                    l2 += w * sbyte<2>(y[l]);
+                    l3 += w * sbyte<3>(y[l]);
+                }
+                *reinterpret_cast<uint32_t *>(smp + (pos << sw_shift) + lane_off) =
+                    decide_fields(q, a0 + q.p0 * l0, a1 + q.p1 * l1, a2 + q.p2 * l2, a3 + q.p3 * l3, r);
+            }
+            __syncthreads();
+        }
+    }
+    const int64_t nvec_out = static_cast<int64_t>(L.n) * vec_per_row;
+    for (int64_t i = threadIdx.x; i < nvec_out; i += blockDim.x) {
+        const int64_t row = i / vec_per_row;
+        const int part = static_cast<int>(i - row * vec_per_row);
+        *reinterpret_cast<uint4 *>(L.S + row * L.Wc + col0 + 16 * part) = reinterpret_cast<const uint4 *>(smp)[i];
+    }
+    // f and g of the final sweep: F = sum_a s_a (sum_b 2J s_b + 2 * 2h_a) = -4 f;
+    // twice g: each link from both ends (weight K), twice k of a down spin
+    __shared__ long long s_F[kMaxSlab];
+    __shared__ int s_g[kMaxSlab];
+    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+        s_F[i] = 0;
+        s_g[i] = 0;
+    }
+    __syncthreads();
+    long long F0 = 0, F1 = 0, F2 = 0, F3 = 0;
+    int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+    for (int pos = grp; pos < L.n; pos += G) {
+        PenRec<DC, DL> rc;
+        rc.load(L.rec, pos);
+        const uint32_t xs = word(pos << sw_shift);
+        const int h4 = 2 * rc.h2();
+        int c0 = h4, c1 = h4, c2 = h4, c3x = h4;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) {
+            const uint32_t x = word(rc.nb(k));
+            const int j = rc.j2(k);
+            c0 += j * sbyte<0>(x);
+            c1 += j * sbyte<1>(x);
+            c2 += j * sbyte<2>(x);
+            c3x += j * sbyte<3>(x);
+        }
+        F0 += static_cast<long long>(sbyte<0>(xs)) * c0;
+        F1 += static_cast<long long>(sbyte<1>(xs)) * c1;
+        F2 += static_cast<long long>(sbyte<2>(xs)) * c2;
+        F3 += static_cast<long long>(sbyte<3>(xs)) * c3x;
+#pragma unroll
+        for (int l = 0; l < DL; ++l) {
+            if (rc.lk(l) == L.pad_ref) continue;
+            const uint32_t y = word(rc.lk(l));
+            const int w = rc.w(l);
+            g0 += w * (sbyte<0>(xs) != sbyte<0>(y));
+            g1 += w * (sbyte<1>(xs) != sbyte<1>(y));
+            g2 += w * (sbyte<2>(xs) != sbyte<2>(y));
+            g3 += w * (sbyte<3>(xs) != sbyte<3>(y));
+        }
+        const int k2 = 2 * rc.kk();
+        g0 += sbyte<0>(xs) < 0 ? k2 : 0;
+        g1 += sbyte<1>(xs) < 0 ? k2 : 0;
+        g2 += sbyte<2>(xs) < 0 ? k2 : 0;
+        g3 += sbyte<3>(xs) < 0 ? k2 : 0;
+    }
+    unsigned long long *sF = reinterpret_cast<unsigned long long *>(s_F);
+    atomicAdd(sF + lane_off + 0, static_cast<unsigned long long>(F0));
+    atomicAdd(sF + lane_off + 1, static_cast<unsigned long long>(F1));
+    atomicAdd(sF + lane_off + 2, static_cast<unsigned long long>(F2));
+    atomicAdd(sF + lane_off + 3, static_cast<unsigned long long>(F3));
+    atomicAdd(&s_g[lane_off + 0], g0);
+    atomicAdd(&s_g[lane_off + 1], g1);
+    atomicAdd(&s_g[lane_off + 2], g2);
+    atomicAdd(&s_g[lane_off + 3], g3);
+    __syncthreads();
+    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+        wk.f[col0 + i] = -(s_F[i] / 4);
+        wk.g[col0 + i] = s_g[i] / 2 + L.g0;
+    }
+}
+
+template <int DC, int DL>
+cudaError_t launch_variant(const Layout &L, const Walkers &wk, const SweepTiling &tl, int32_t qpr,
+                           const RoundKeys &rk, uint32_t sweep0, int32_t nsweeps, cudaStream_t st) {
+    int shift = 0;
+    while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
+    const size_t smem = smem_sweep_bytes(L.n, 1 << shift);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_penalty_smem<DC, DL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
+    k_sweep_penalty_smem<DC, DL><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool penalty_kernel_degrees(int DC, int DL) {
+    return (DC == 3 || DC == 4 || DC == 6) && (DL == 2 || DL == 3);
+}
+
+cudaError_t launch_penalty_sweeps(const Layout &L, const Walkers &wk, const SweepTiling &tl,
+                                  int32_t quads_per_run, uint64_t seed, uint32_t sweep0, int32_t nsweeps,
+                                  cudaStream_t st) {
+    if (!L.penalty || !tl.smem || tl.walkers_per_thread != 4 || tl.lanes_per_spin < 4) return cudaErrorInvalidValue;
+    const RoundKeys rk = round_keys(seed);
+    const int k = L.DC * 8 + L.DL;
+    switch (k) {
+        case 3 * 8 + 2: return launch_variant<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        case 3 * 8 + 3: return launch_variant<3, 3>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        case 4 * 8 + 2: return launch_variant<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        case 4 * 8 + 3: return launch_variant<4, 3>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        case 6 * 8 + 2: return launch_variant<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        case 6 * 8 + 3: return launch_variant<6, 3>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pt2d

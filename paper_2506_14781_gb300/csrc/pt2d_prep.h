@@ -17,6 +17,7 @@ struct Prep {
     pt2d::SweepTiling tiling{};
     int32_t rec_vec = 0, pad_ref = 0;
     bool penalty = false;  // link weights other than 1 or penalty fields: generic records
+    bool pen_kernel = false;  // penalty records swept by the degree-specialised shared-memory kernel
     int32_t g0 = 0;        // constant term of g
     std::vector<int32_t> color, pid, pos_of, cofs, rec;
 };

@@ -464,7 +464,63 @@ def test_colouring_with_equality_constraints_bit_exact(pt, capacity, kernel):
     P = np.array([1, 3, 8], np.int32)
     ctx, orc = both(pt, None, None, beta, P, 5, 2468, [(60, 6), (24, 6)], phys=phys, trace=32,
                     target=prob.f_proper, kernel=kernel)
-    assert ctx.tiling["kernel"] == ("generic_smem" if kernel == "auto" else "generic")
+    expect = "generic" if kernel == "global" else ("penalty_smem" if capacity is None else "generic_smem")
+    assert ctx.tiling["kernel"] == expect
+    assert_same(pt, ctx, orc)
+    assert np.all(ctx.read(pt.G) >= 0)
+
+
+def _graph_colouring_pair(pt, V, k, max_deg, seed):
+    """One-hot k-colouring of a random graph with degrees <= max_deg and edge
+    weights 1..3; each side expands the one-hot groups with its own routine."""
+    from oracle.penalties import onehot
+
+    rng = np.random.default_rng(seed)
+    deg = np.zeros(V, np.int64)
+    edges = set()
+    for _ in range(V * max_deg * 4):
+        u, v = (int(x) for x in rng.integers(V, size=2))
+        e = (min(u, v), max(u, v))
+        if u == v or deg[u] >= max_deg or deg[v] >= max_deg or e in edges:
+            continue
+        edges.add(e)
+        deg[u] += 1
+        deg[v] += 1
+    n = V * k
+    rows = [dict() for _ in range(n)]
+    h = np.zeros(n, np.int32)
+    for u, v in sorted(edges):
+        w = int(rng.integers(1, 4))
+        for c in range(k):
+            a, b = u * k + c, v * k + c
+            rows[a][b] = rows[b][a] = -w
+            h[a] -= w
+            h[b] -= w
+    cp_ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    cp_col = np.array([b for r in rows for b in sorted(r)], np.int32)
+    cp_J = np.array([r[b] for r in rows for b in sorted(r)], np.int16)
+    groups = [list(range(v * k, v * k + k)) for v in range(V)]
+    p1, c1, w1, k1, g1 = pt.onehot_penalty(n, groups)
+    p2, c2, w2, k2, g2 = onehot(n, groups)
+    phys_p = pt.PhysicalInstance(n, cp_ptr, cp_col, cp_J, p1, c1, h=h, lk_w=w1, hk=k1, g0=g1)
+    phys_o = oracle.PhysInstance(n, cp_ptr, cp_col, cp_J, p2, c2, h, n, np.arange(n, dtype=np.int32),
+                                 np.arange(n + 1, dtype=np.int32), lk_w=w2, hk=k2, g0=g2)
+    return phys_p, phys_o, int(deg.max())
+
+
+@pytest.mark.parametrize("k,max_deg,wpc", [(3, 3, 0), (4, 3, 16), (3, 4, 0), (4, 4, 32), (3, 6, 0), (4, 5, 64)])
+def test_penalty_specialised_kernel_bit_exact(pt, k, max_deg, wpc):
+    """Instances with penalty terms and coupling degree <= 6, link degree <= 3
+    run on the degree-specialised shared-memory kernel (records padded to
+    coupling width 3, 4 or 6 and link width 2 or 3), bit-exact with the
+    oracle, over several slab widths and a ragged last tile."""
+    phys_p, phys_o, dmax = _graph_colouring_pair(pt, 40, k, max_deg, 100 + 10 * k + max_deg)
+    assert dmax == max_deg
+    beta = np.array([0.03, 0.1, 0.4, 1.2, 3.0], np.float32)
+    P = np.array([1, 2, 4, 9], np.int32)
+    ctx, orc = both(pt, None, None, beta, P, 7, 97531, [(48, 4), (20, 4)], phys=(phys_p, phys_o), trace=24,
+                    target=-10 ** 6, wpc=wpc)
+    assert ctx.tiling["kernel"] == "penalty_smem"
     assert_same(pt, ctx, orc)
     assert np.all(ctx.read(pt.G) >= 0)
 
