@@ -64,12 +64,12 @@ BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
 # DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only while the kernel sources hash to `src`; the summaries are under profiles/.
 PROFILED_TRAFFIC = {
-    ("n200", "k_sweep_smem"): dict(src="ceabe32d2d4e2a4a", dram_bytes_per_launch=386_070_016,
+    ("n200", "k_sweep_smem"): dict(src="bd5e83aa7856705b", dram_bytes_per_launch=387_603_712,
                                    profile="profiles/k_sweep_smem_n200.md"),
     # captured at 4 of the 16 runs and scaled by the walkers
-    ("n800", "k_sweep_bits"): dict(src="ceabe32d2d4e2a4a", dram_bytes_per_launch=19_655_536_000,
+    ("n800", "k_sweep_bits"): dict(src="bd5e83aa7856705b", dram_bytes_per_launch=18_844_223_488,
                                    profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
-    ("constrained", "k_sweep_penalty_smem"): dict(src="0b046b3daf429894", dram_bytes_per_launch=341_854_208,
+    ("constrained", "k_sweep_penalty_smem"): dict(src="20ec3f524dc8ee88", dram_bytes_per_launch=341_336_832,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h")

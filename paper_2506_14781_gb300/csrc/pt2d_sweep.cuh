@@ -10,30 +10,15 @@
 
 namespace pt2d {
 
-// Philox key sources for update4: round keys from the kernel's parameter space
-// (one seed per launch), or a base key advanced per round (a seed per run).
+// Philox key source of the sweep loops: the ten round keys, held as kernel
+// parameters (one seed per launch) or in per-thread registers (the batch, a
+// seed per run).
 struct KeysConst {
     RoundKeys rk;
     __device__ __forceinline__ uint4 operator()(uint4 x) const { return philox4x32_10(x, rk); }
 };
-struct KeysBase {
-    uint32_t k0, k1;
-    __device__ __forceinline__ uint4 operator()(uint4 x) const { return philox4x32_10(x, k0, k1); }
-};
-// Round keys staged in shared memory, two rounds per 16-byte word:
-// k[r] = (k0 of round 2r, k1 of round 2r, k0 of round 2r+1, k1 of round 2r+1).
-struct KeysShared {
-    const uint4 *k;
-    __device__ __forceinline__ uint4 operator()(uint4 x) const {
-#pragma unroll
-        for (int r = 0; r < 5; ++r) {
-            const uint4 kk = k[r];
-            x = philox_round(x, kk.x, kk.y);
-            x = philox_round(x, kk.z, kk.w);
-        }
-        return x;
-    }
-};
+// A run's round keys staged in shared memory, two rounds per 16-byte word:
+// dst[r] = (k0 of round 2r, k1 of round 2r, k0 of round 2r+1, k1 of round 2r+1).
 __device__ __forceinline__ void stage_round_keys(uint4 *dst, uint32_t k0, uint32_t k1) {
     if (threadIdx.x < 5) {
         const uint32_t r = 2 * threadIdx.x;
