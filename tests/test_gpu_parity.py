@@ -616,3 +616,32 @@ def test_n800_full_size_sampled_walkers(pt):
                                           np.arange(64 * 16), seed, run_id, 1, 1)
         assert np.array_equal(at_gpu[run_id], at)
         assert np.array_equal(acc_gpu[run_id], accP)
+
+
+def test_colouring_full_size_sampled_runs(pt):
+    """The constrained workload at full size: 3-colouring of a random cubic
+    graph, V=2000 (6000 spins, one-hot groups), I=16 x J=8, 256 runs, on the
+    degree-specialised penalty kernel in the automatic launch configuration the
+    benchmark uses; three runs checked in full by the oracle after two events."""
+    from oracle.penalties import onehot
+
+    prob = synth.colouring(2000, 3, 7)
+    p1, c1, w1, k1, g1 = pt.onehot_penalty(prob.n, prob.groups)
+    p2, c2, w2, k2, g2 = onehot(prob.n, prob.groups)
+    phys_p = pt.PhysicalInstance(prob.n, prob.cp_ptr, prob.cp_col, prob.cp_J, p1, c1, h=prob.h, lk_w=w1,
+                                 hk=k1, g0=g1)
+    phys_o = oracle.PhysInstance(prob.n, prob.cp_ptr, prob.cp_col, prob.cp_J, p2, c2, prob.h, prob.n,
+                                 np.arange(prob.n, dtype=np.int32), np.arange(prob.n + 1, dtype=np.int32),
+                                 lk_w=w2, hk=k2, g0=g2)
+    beta = np.geomspace(0.05, 2.0, 16).astype(np.float32)
+    P = np.array([1, 2, 3, 5, 8, 12, 17, 24], np.int32)
+    seed = 2024
+    ctx = pt.PT2D(phys_p, beta, P, 256, trace_capacity=8)
+    assert ctx.tiling["kernel"] == "penalty_smem" and ctx.tiling["walkers_per_cta"] == 32
+    ctx.write(pt.TARGET, np.full(256, prob.f_proper))
+    ctx.run(20, 10, seed)
+    oinst = oracle.OracleInstance(phys_o)
+    for run_id in (0, 137, 255):
+        orc = oracle.OracleRun(oinst, beta, P, [run_id], seed, trace_cap=8, target=prob.f_proper)
+        orc.run(20, 10)
+        assert_same(pt, ctx, orc, runs_sel=[run_id])
