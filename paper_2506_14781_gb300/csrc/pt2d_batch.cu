@@ -20,6 +20,7 @@
 #include "pt2d_device.cuh"
 #include "pt2d_internal.h"
 #include "pt2d_sweep.cuh"
+#include "pt2d_wide.cuh"
 
 namespace pt2d {
 namespace {
@@ -158,31 +159,26 @@ __device__ __forceinline__ void slab_sweeps(const BatchArgs &a, const BatchRun &
         for (int c = 0; c < d.C; ++c) {
             const int beg = __ldg(cofs + c), end = __ldg(cofs + c + 1);
             for (int pos = beg + grp; pos < end; pos += G) {
-                if constexpr (DC == 0) {  // runtime degrees, optional penalty terms
+                if constexpr (DC == 0) {  // runtime degrees on wide records, optional penalty terms
                     const int dc = d.dc, dl = d.dl;
+                    const int jo = wide_jpack_offset(dc, dl), ko = jo + dc / 2;
                     const int *rc = reinterpret_cast<const int *>(rec) + static_cast<int64_t>(pos) * d.rec_vec * 4;
+                    int j0, j1, j2, j3;  // sum_k J_k s_k per walker
+                    wide_coupling_sums<true>(rc, dc, jo, fetch, j0, j1, j2, j3);
                     const int h2 = __ldg(rc + dc + dl + 1);
-                    int a0 = h2, a1 = h2, a2 = h2, a3 = h2;
-                    const int kk = d.penalty ? __ldg(rc + 2 * dc + 2 * dl + 2) : 0;
+                    const int kk = d.penalty ? __ldg(rc + ko + dl) : 0;
                     int l0 = kk, l1 = kk, l2 = kk, l3 = kk;
-                    for (int k = 0; k < dc; ++k) {
-                        const uint32_t x = fetch(__ldg(rc + k));
-                        const int j = __ldg(rc + dc + dl + 2 + k);
-                        a0 += j * sbyte<0>(x);
-                        a1 += j * sbyte<1>(x);
-                        a2 += j * sbyte<2>(x);
-                        a3 += j * sbyte<3>(x);
-                    }
                     for (int k = 0; k < dl; ++k) {
                         const uint32_t y = fetch_link(__ldg(rc + dc + k));
-                        const int w = d.penalty ? __ldg(rc + 2 * dc + dl + 2 + k) : 1;
+                        const int w = d.penalty ? __ldg(rc + ko + k) : 1;
                         l0 += w * sbyte<0>(y);
                         l1 += w * sbyte<1>(y);
                         l2 += w * sbyte<2>(y);
                         l3 += w * sbyte<3>(y);
                     }
                     const uint4 r = keys(make_uint4(static_cast<uint32_t>(__ldg(rc + dc + dl)), sweep, lq, c3));
-                    store(pos, decide_fields(q, a0 + q.p0 * l0, a1 + q.p1 * l1, a2 + q.p2 * l2, a3 + q.p3 * l3, r));
+                    store(pos, decide_fields(q, h2 + 2 * j0 + q.p0 * l0, h2 + 2 * j1 + q.p1 * l1,
+                                             h2 + 2 * j2 + q.p2 * l2, h2 + 2 * j3 + q.p3 * l3, r));
                 } else {
                     Rec<DC, DL> rc;
                     rc.load(rec, pos);
@@ -211,33 +207,29 @@ __device__ __forceinline__ void slab_energies(const BatchRun &d, const int4 *rec
     for (int pos = grp; pos < n; pos += G) {
         if constexpr (DC == 0) {
             const int dc = d.dc, dl = d.dl;
+            const int jo = wide_jpack_offset(dc, dl), ko = jo + dc / 2;
             const int *rc = reinterpret_cast<const int *>(rec) + static_cast<int64_t>(pos) * d.rec_vec * 4;
             const uint32_t xs = fetch(pos);
+            int j0, j1, j2, j3;
+            wide_coupling_sums<true>(rc, dc, jo, fetch, j0, j1, j2, j3);
             const int h4 = 2 * __ldg(rc + dc + dl + 1);
-            int cb[4] = {h4, h4, h4, h4};
-            for (int k = 0; k < dc; ++k) {
-                const uint32_t x = fetch(__ldg(rc + k));
-                const int j2 = __ldg(rc + dc + dl + 2 + k);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) cb[b] += j2 * sbyte_rt(x, b);
-            }
-            F0 += static_cast<long long>(sbyte<0>(xs)) * cb[0];
-            F1 += static_cast<long long>(sbyte<1>(xs)) * cb[1];
-            F2 += static_cast<long long>(sbyte<2>(xs)) * cb[2];
-            F3 += static_cast<long long>(sbyte<3>(xs)) * cb[3];
+            F0 += static_cast<long long>(sbyte<0>(xs)) * (h4 + 2 * j0);
+            F1 += static_cast<long long>(sbyte<1>(xs)) * (h4 + 2 * j1);
+            F2 += static_cast<long long>(sbyte<2>(xs)) * (h4 + 2 * j2);
+            F3 += static_cast<long long>(sbyte<3>(xs)) * (h4 + 2 * j3);
             // twice g: weighted links from both ends, twice k of a down spin
             for (int k = 0; k < dl; ++k) {
                 const int lp = __ldg(rc + dc + k);
                 if (lp == n) continue;  // padding link
                 const uint32_t y = fetch(lp);
-                const int w = d.penalty ? __ldg(rc + 2 * dc + dl + 2 + k) : 1;
+                const int w = d.penalty ? __ldg(rc + ko + k) : 1;
                 g0 += w * (sbyte<0>(xs) != sbyte<0>(y));
                 g1 += w * (sbyte<1>(xs) != sbyte<1>(y));
                 g2 += w * (sbyte<2>(xs) != sbyte<2>(y));
                 g3 += w * (sbyte<3>(xs) != sbyte<3>(y));
             }
             if (d.penalty) {
-                const int k2 = 2 * __ldg(rc + 2 * dc + 2 * dl + 2);
+                const int k2 = 2 * __ldg(rc + ko + dl);
                 g0 += sbyte<0>(xs) < 0 ? k2 : 0;
                 g1 += sbyte<1>(xs) < 0 ? k2 : 0;
                 g2 += sbyte<2>(xs) < 0 ? k2 : 0;

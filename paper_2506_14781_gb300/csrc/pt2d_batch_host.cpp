@@ -190,9 +190,9 @@ int fail(pt2d_batch *b, cudaError_t e) {
     } while (0)
 
 // A runtime-degree batch takes problems whose coupling degree is within the
-// declared cap (records may be padded up to 6 when the layout is small).
+// declared cap (its wide records pad the degree up to a multiple of 4).
 bool degrees_fit(const pt2d_batch *b, const pt2d::Prep &pp) {
-    return pp.DC <= std::max(b->DC, 6);
+    return pp.dcmax <= std::max(b->DC, 6);
 }
 
 void drop_graph(pt2d_batch *b) {
@@ -363,7 +363,7 @@ size_t pt2d_batch_instance_bytes(const pt2d_batch *b, const pt2d_instance *inst,
     pt2d_options o;
     pt2d_default_options(&o);
     o.sweep_kernel = 1;
-    if (pt2d::prepare(inst, I, nullptr, J, nullptr, 1, &o, pp, b->generic ? 0 : b->DC)) return 0;
+    if (pt2d::prepare(inst, I, nullptr, J, nullptr, 1, &o, pp, b->generic ? -1 : b->DC)) return 0;
     if (b->generic && !degrees_fit(b, pp)) return 0;
     const int32_t R = I * J;
     return align_up(block_layout(inst->n, pp.C, pp.rec_vec, I, J, R, pow2_at_least(R), runs, b->trace_cap)
@@ -483,7 +483,7 @@ int pt2d_batch_add(pt2d_batch *b, const pt2d_instance *inst, int32_t I, const fl
     o.sweep_kernel = 1;
     Inst in;
     pt2d::Prep pp;
-    int st = pt2d::prepare(inst, I, beta, J, P, 1, &o, pp, b->generic ? 0 : b->DC);
+    int st = pt2d::prepare(inst, I, beta, J, P, 1, &o, pp, b->generic ? -1 : b->DC);
     if (st) return st;
     if (b->generic && !degrees_fit(b, pp)) return PT2D_ERR_INVALID_ARG;
     in.n = pp.n;

@@ -13,10 +13,12 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pt2d.h"
+#include "pt2d_generic.h"
 #include "pt2d_internal.h"
 #include "pt2d_penalty.h"
 #include "pt2d_prep.h"
 #include "pt2d_trace.h"
+#include "pt2d_wide.cuh"
 
 namespace {
 
@@ -189,47 +191,22 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         dcmax = std::max<int32_t>(dcmax, static_cast<int32_t>(cadj[a].size()));
         dlmax = std::max<int32_t>(dlmax, static_cast<int32_t>(ladj[a].size()));
     }
-    int32_t DC, DL;
+    // Record layout.  Without penalty terms and with coupling degree <= 6 and
+    // two copy links: the specialised layouts (coupling width 3, 4 or 6), or the
+    // width a batch forces.  Otherwise decided after the tiling: the
+    // penalty-specialised layout when that kernel will sweep the instance, else
+    // the wide layout of the runtime-degree kernels (force_dc < 0 asks for it).
+    int32_t DC = 0, DL = 0;
+    const bool spec_layout = force_dc > 0 || (force_dc == 0 && !penalty && dlmax <= 2 && dcmax <= 6);
     if (force_dc > 0) {
         if (dlmax > 2 || dcmax > force_dc) return PT2D_ERR_INVALID_ARG;
         DC = force_dc;
         DL = 2;
-    } else if (!penalty && dlmax <= 2 && dcmax <= 6) {
+    } else if (spec_layout) {
         DL = 2;
         DC = dcmax <= 3 ? 3 : (dcmax <= 4 ? 4 : 6);
-    } else if (penalty && force_dc == 0 && dcmax <= 6 && dlmax <= 3) {
-        // padded up to a layout of the penalty-specialised kernel (padding
-        // entries point at the zero row with J = 0, K = 0)
-        DC = dcmax <= 3 ? 3 : (dcmax <= 4 ? 4 : 6);
-        DL = dlmax <= 2 ? 2 : 3;
-    } else {
-        DC = std::max(dcmax, 1);
-        DL = std::max(dlmax, 1);
     }
-    // packed records: [nb x DC, lk x DL, pid, 2h, 2J x DC], then with penalty terms
-    // [K x DL, k], padded to whole int4s
-    const int32_t rec_ints = 2 * DC + DL + 2 + (penalty ? DL + 1 : 0);
-    const int32_t rec_vec = (rec_ints + 3) / 4;
-    const size_t ri = static_cast<size_t>(rec_vec) * 4;
-    pp.rec_vec = rec_vec;
-    pp.rec.assign(static_cast<size_t>(n) * ri, 0);
-    for (int32_t p = 0; p < n; ++p) {
-        const int32_t a = pp.pid[p];
-        int32_t *r = pp.rec.data() + static_cast<size_t>(p) * ri;
-        for (int32_t k = 0; k < DC; ++k) r[k] = n;
-        for (int32_t k = 0; k < DL; ++k) r[DC + k] = n;
-        for (size_t k = 0; k < cadj[a].size(); ++k) {
-            r[k] = pp.pos_of[cadj[a][k].first];
-            r[DC + DL + 2 + k] = 2 * cadj[a][k].second;
-        }
-        for (size_t k = 0; k < ladj[a].size(); ++k) r[DC + k] = pp.pos_of[ladj[a][k].first];
-        r[DC + DL] = a;
-        r[DC + DL + 1] = inst->h ? 2 * inst->h[a] : 0;
-        if (penalty) {
-            for (size_t k = 0; k < ladj[a].size(); ++k) r[2 * DC + DL + 2 + k] = ladj[a][k].second;
-            r[2 * DC + 2 * DL + 2] = inst->hk ? inst->hk[a] : 0;
-        }
-    }
+    pp.dcmax = dcmax;
     pp.n = n;
     pp.I = I;
     pp.J = J;
@@ -237,8 +214,6 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.Rp = (pp.R + 3) / 4 * 4;
     pp.runs = runs;
     pp.C = C;
-    pp.DC = DC;
-    pp.DL = DL;
     pp.trace_cap = opt ? std::max<int32_t>(opt->trace_capacity, 0) : 1024;
     // Sweep tiling.  The shared-memory kernel holds a CTA's whole slab,
     // (n + 1) x SW bytes, for the swap interval; it needs one of the specialised
@@ -362,7 +337,57 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.tiling.smem = sw != 0;
     pp.tiling.bits = bw != 0;
     pp.tiling.walkers_per_thread = wpt;
-    pp.pen_kernel = penalty && sw != 0 && wpt == 4 && pt2d::penalty_kernel_degrees(DC, DL);
+    pp.pen_kernel = !spec_layout && force_dc == 0 && penalty && sw != 0 && wpt == 4 && dcmax <= 6 && dlmax <= 3;
+    if (pp.pen_kernel) {
+        // padded up to a layout of the penalty-specialised kernel (padding
+        // entries point at the zero row with J = 0, K = 0)
+        DC = dcmax <= 3 ? 3 : (dcmax <= 4 ? 4 : 6);
+        DL = dlmax <= 2 ? 2 : 3;
+        if (!pt2d::penalty_kernel_degrees(DC, DL)) return PT2D_ERR_INVALID_ARG;
+    } else if (!spec_layout) {
+        DC = std::max<int32_t>(4, (dcmax + 3) / 4 * 4);
+        DL = dlmax;
+    }
+    pp.wide = !spec_layout && !pp.pen_kernel;
+    pp.DC = DC;
+    pp.DL = DL;
+    // packed records (the spin id at DC + DL in every layout), padded to whole int4s:
+    //  specialised / penalty-specialised: [nb x DC, lk x DL, pid, 2h, 2J x DC] and,
+    //  with penalty terms, [K x DL, k];  wide: see pt2d_wide.cuh
+    const int32_t jo = pt2d::wide_jpack_offset(DC, DL);
+    const int32_t rec_ints = pp.wide ? pt2d::wide_record_ints(DC, DL, penalty)
+                                     : 2 * DC + DL + 2 + (penalty ? DL + 1 : 0);
+    const int32_t rec_vec = (rec_ints + 3) / 4;
+    const size_t ri = static_cast<size_t>(rec_vec) * 4;
+    pp.rec_vec = rec_vec;
+    pp.rec.assign(static_cast<size_t>(n) * ri, 0);
+    for (int32_t p = 0; p < n; ++p) {
+        const int32_t a = pp.pid[p];
+        int32_t *r = pp.rec.data() + static_cast<size_t>(p) * ri;
+        for (int32_t k = 0; k < DC; ++k) r[k] = n;
+        for (int32_t k = 0; k < DL; ++k) r[DC + k] = n;
+        for (size_t k = 0; k < cadj[a].size(); ++k) {
+            r[k] = pp.pos_of[cadj[a][k].first];
+            const int32_t Jk = cadj[a][k].second;
+            if (pp.wide) {  // J = 256 hi + lo, byte k % 4 of group k / 4
+                const uint32_t lo = static_cast<uint32_t>(Jk) & 0xFFu;
+                const uint32_t hi = static_cast<uint32_t>(Jk >> 8) & 0xFFu;
+                uint32_t *g = reinterpret_cast<uint32_t *>(r + jo + 2 * (k / 4));
+                g[0] |= lo << (8 * (k % 4));
+                g[1] |= hi << (8 * (k % 4));
+            } else {
+                r[DC + DL + 2 + k] = 2 * Jk;
+            }
+        }
+        for (size_t k = 0; k < ladj[a].size(); ++k) r[DC + k] = pp.pos_of[ladj[a][k].first];
+        r[DC + DL] = a;
+        r[DC + DL + 1] = inst->h ? 2 * inst->h[a] : 0;
+        if (penalty) {
+            const int32_t ko = pp.wide ? jo + DC / 2 : 2 * DC + DL + 2;
+            for (size_t k = 0; k < ladj[a].size(); ++k) r[ko + k] = ladj[a][k].second;
+            r[ko + DL] = inst->hk ? inst->hk[a] : 0;
+        }
+    }
     // neighbour references become byte offsets into the shared-memory slab
     const int scale = sw ? sw : (bw ? bw / 8 : 1);
     if (scale > 1) {
@@ -656,9 +681,7 @@ int pt2d_num_colors(const pt2d_ctx *c) { return c ? c->pp.C : 0; }
 int pt2d_tiling(const pt2d_ctx *c, int32_t out[4]) {
     if (!c || !out) return PT2D_ERR_INVALID_ARG;
     const pt2d::SweepTiling &t = c->pp.tiling;
-    const bool specialised =
-        !c->pp.penalty && c->pp.DL == 2 && (c->pp.DC == 3 || c->pp.DC == 4 || c->pp.DC == 6);
-    out[0] = t.bits ? 3 : t.smem ? (specialised ? 2 : (c->pp.pen_kernel ? 6 : 5)) : specialised ? 1 : 4;
+    out[0] = t.bits ? 3 : t.smem ? (c->pp.pen_kernel ? 6 : (c->pp.wide ? 5 : 2)) : (c->pp.wide ? 4 : 1);
     out[1] = 4 * t.lanes_per_spin;
     out[2] = t.threads;
     out[3] = t.walkers_per_thread;
@@ -697,6 +720,9 @@ int pt2d_run(pt2d_ctx *c, int64_t sweeps, int32_t interval, uint64_t seed) {
         }
         if (c->pp.pen_kernel) {
             CK(c, pt2d::launch_penalty_sweeps(c->L, c->wk, c->pp.tiling, c->pp.Rp / 4, seed,
+                                              static_cast<uint32_t>(c->sweeps_done), interval, s));
+        } else if (c->pp.wide) {
+            CK(c, pt2d::launch_generic_sweeps(c->L, c->wk, c->pp.tiling, c->pp.Rp / 4, seed,
                                               static_cast<uint32_t>(c->sweeps_done), interval, s));
         } else {
             CK(c, pt2d::launch_sweeps(c->L, c->wk, c->pp.tiling, c->pp.Rp / 4, seed,

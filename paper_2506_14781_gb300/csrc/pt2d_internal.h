@@ -17,9 +17,12 @@ namespace pt2d {
 //    the total rounded up to the sweep tile.
 //  * One packed record per position, rec_vec int4s: [nb_0..nb_{DC-1} (coupling
 //    neighbours, padding -> zero row), lk_0..lk_{DL-1} (link neighbours, padding
-//    -> zero row), spin id, 2h, 2J_0..2J_{DC-1}, zero padding].  Neighbour
-//    references are row indices for the global-memory kernels and byte offsets
-//    row * SW into the slab for the shared-memory kernel.
+//    -> zero row), spin id, 2h, 2J_0..2J_{DC-1}, zero padding], with link
+//    weights K and the penalty field k after 2J when penalty is set; records of
+//    the runtime-degree kernels use the wide layout of pt2d_wide.cuh (the spin
+//    id is at DC + DL in every layout).  Neighbour references are row indices
+//    for the global-memory kernels and byte offsets row * SW into the slab for
+//    the shared-memory kernels.
 struct Layout {
     int8_t *S;
     int64_t Wc;
@@ -31,7 +34,7 @@ struct Layout {
     int32_t pad_ref;      // neighbour reference of the zero row (n, or n * SW when scaled)
     const int4 *rec;      // [n][rec_vec]
     const int32_t *cofs;  // [C + 1] colour class offsets (positions)
-    int32_t penalty;      // generic records carry link weights K and the penalty field k
+    int32_t penalty;      // records carry link weights K and the penalty field k
     int32_t g0;           // constant term of g
 };
 

@@ -19,6 +19,10 @@
 // row segment (4*QL bytes); the CTA's QL-lane groups take different spins of the
 // current colour class.  Per spin the neighbour list is one packed record
 // (positions, spin id, 2h, 2J) read with 16-byte loads.
+//
+// These kernels take the specialised record layouts (coupling width 3, 4 or 6,
+// two copy links).  Runtime degrees are swept by pt2d_generic.cu, instances
+// with small degrees and general penalty terms by pt2d_penalty.cu.
 #include <cstdint>
 
 #include "pt2d_device.cuh"
@@ -286,239 +290,6 @@ __global__ void __launch_bounds__(256) k_sweep_global(Layout L, Walkers wk, int 
                         static_cast<int64_t>(blockIdx.x) * QL * 4);
 }
 
-// Generic degrees (any DC, DL read from the layout), global memory.
-__global__ void __launch_bounds__(256) k_sweep_generic(Layout L, Walkers wk, int ql_shift,
-                                                       int32_t quads_per_run, RoundKeys rk,
-                                                       uint32_t sweep0, int32_t nsweeps) {
-    const int QL = 1 << ql_shift;
-    const int lane_q = threadIdx.x & (QL - 1);
-    const int grp = threadIdx.x >> ql_shift;
-    const int G = blockDim.x >> ql_shift;
-    const int64_t quad = static_cast<int64_t>(blockIdx.x) * QL + lane_q;
-    const int64_t col = quad * 4;
-    const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
-    const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
-    const uint32_t c3 = (run << 4) | kTagSweep;
-    const Quad q = load_quad(wk, col);
-    const int DC = L.DC, DL = L.DL;
-    const int rec_ints = L.rec_vec * 4;
-    const int *recs = reinterpret_cast<const int *>(L.rec);
-    int8_t *__restrict__ S = L.S;
-    const int64_t Wc = L.Wc;
-    auto word = [&](int row) -> uint32_t {
-        return *reinterpret_cast<const uint32_t *>(S + static_cast<int64_t>(row) * Wc + col);
-    };
-    const float bq[4] = {q.b0, q.b1, q.b2, q.b3};
-    const float cq[4] = {q.c0, q.c1, q.c2, q.c3};
-    const int pq[4] = {q.p0, q.p1, q.p2, q.p3};
-    for (int t = 0; t < nsweeps; ++t) {
-        const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
-        for (int c = 0; c < L.C; ++c) {
-            const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
-            for (int pos = beg + grp; pos < end; pos += G) {
-                const int *rc = recs + static_cast<int64_t>(pos) * rec_ints;
-                const int h2 = __ldg(rc + DC + DL + 1);
-                int a[4] = {h2, h2, h2, h2};
-                // penalty part: sum_l K_l s_l + k (K = 1, k = 0 for copy links)
-                const int kk = L.penalty ? __ldg(rc + 2 * DC + 2 * DL + 2) : 0;
-                int l[4] = {kk, kk, kk, kk};
-                for (int k = 0; k < DC; ++k) {
-                    const uint32_t x = word(__ldg(rc + k));
-                    const int j = __ldg(rc + DC + DL + 2 + k);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) a[b] += j * sbyte_rt(x, b);
-                }
-                for (int k = 0; k < DL; ++k) {
-                    const uint32_t y = word(__ldg(rc + DC + k));
-                    const int w = L.penalty ? __ldg(rc + 2 * DC + DL + 2 + k) : 1;
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) l[b] += w * sbyte_rt(y, b);
-                }
-                const uint4 r = philox4x32_10(
-                    make_uint4(static_cast<uint32_t>(__ldg(rc + DC + DL)), sweep, lq, c3), rk);
-                const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
-                float tv[4];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) tv[b] = heatbath_t(bq[b], cq[b], a[b] + pq[b] * l[b], rr[b]);
-                *reinterpret_cast<uint32_t *>(S + static_cast<int64_t>(pos) * Wc + col) =
-                    pack_signs(tv[0], tv[1], tv[2], tv[3]);
-            }
-            __syncthreads();
-        }
-    }
-    // epilogue
-    __shared__ long long s_F[kMaxSlab];
-    __shared__ int s_g[kMaxSlab];
-    for (int i = threadIdx.x; i < 4 * QL; i += blockDim.x) {
-        s_F[i] = 0;
-        s_g[i] = 0;
-    }
-    __syncthreads();
-    long long F[4] = {0, 0, 0, 0};
-    int g[4] = {0, 0, 0, 0};
-    for (int pos = grp; pos < L.n; pos += G) {
-        const int *rc = recs + static_cast<int64_t>(pos) * rec_ints;
-        const uint32_t xs = word(pos);
-        const int h4 = 2 * __ldg(rc + DC + DL + 1);
-        int cc[4] = {h4, h4, h4, h4};
-        for (int k = 0; k < DC; ++k) {
-            const uint32_t x = word(__ldg(rc + k));
-            const int j = __ldg(rc + DC + DL + 2 + k);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) cc[b] += j * sbyte_rt(x, b);
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) F[b] += static_cast<long long>(sbyte_rt(xs, b)) * cc[b];
-        // twice g: each link from both ends (weight K), twice k of a down spin
-        for (int k = 0; k < DL; ++k) {
-            const int lp = __ldg(rc + DC + k);
-            if (lp == L.pad_ref) continue;
-            const uint32_t y = word(lp);
-            const int w = L.penalty ? __ldg(rc + 2 * DC + DL + 2 + k) : 1;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) g[b] += w * (sbyte_rt(xs, b) != sbyte_rt(y, b));
-        }
-        if (L.penalty) {
-            const int k2 = 2 * __ldg(rc + 2 * DC + 2 * DL + 2);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) g[b] += sbyte_rt(xs, b) < 0 ? k2 : 0;
-        }
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&s_F[lane_q * 4 + b]),
-                  static_cast<unsigned long long>(F[b]));
-        atomicAdd(&s_g[lane_q * 4 + b], g[b]);
-    }
-    __syncthreads();
-    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * QL * 4;
-    for (int i = threadIdx.x; i < 4 * QL; i += blockDim.x) {
-        wk.f[col0 + i] = -(s_F[i] / 4);
-        wk.g[col0 + i] = s_g[i] / 2 + L.g0;
-    }
-}
-
-// Generic degrees (any DC, DL read from the layout, general penalty terms) with
-// the CTA's int8 slab in shared memory for the whole swap interval, as in
-// k_sweep_smem; neighbour references are byte offsets row * SW.
-__global__ void __launch_bounds__(1024, 1) k_sweep_generic_smem(Layout L, Walkers wk, int sw_shift,
-                                                                int32_t quads_per_run, RoundKeys rk,
-                                                                uint32_t sweep0, int32_t nsweeps) {
-    extern __shared__ __align__(16) int8_t smg[];
-    const int SW = 1 << sw_shift;
-    const int QL = SW >> 2;
-    const int lane = threadIdx.x & (QL - 1);
-    const int grp = threadIdx.x / QL;
-    const int G = blockDim.x / QL;
-    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * SW;
-    const int64_t quad = col0 / 4 + lane;
-    const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
-    const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
-    const uint32_t c3 = (run << 4) | kTagSweep;
-    const int lane_off = 4 * lane;
-    const Quad q = load_quad(wk, col0 + lane_off);
-    const int DC = L.DC, DL = L.DL;
-    const int rec_ints = L.rec_vec * 4;
-    const int *recs = reinterpret_cast<const int *>(L.rec);
-    const int vec_per_row = SW >> 4;
-    const int64_t nvec = static_cast<int64_t>(L.n + 1) * vec_per_row;
-    for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
-        const int64_t row = i / vec_per_row;
-        const int part = static_cast<int>(i - row * vec_per_row);
-        reinterpret_cast<uint4 *>(smg)[i] =
-            *reinterpret_cast<const uint4 *>(L.S + row * L.Wc + col0 + 16 * part);
-    }
-    __syncthreads();
-    auto word = [&](int off) -> uint32_t { return *reinterpret_cast<const uint32_t *>(smg + off + lane_off); };
-    for (int t = 0; t < nsweeps; ++t) {
-        const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
-        for (int c = 0; c < L.C; ++c) {
-            const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
-            for (int pos = beg + grp; pos < end; pos += G) {
-                const int *rc = recs + static_cast<int64_t>(pos) * rec_ints;
-                const int h2 = __ldg(rc + DC + DL + 1);
-                int a0 = h2, a1 = h2, a2 = h2, a3 = h2;
-                const int kk = L.penalty ? __ldg(rc + 2 * DC + 2 * DL + 2) : 0;
-                int l0 = kk, l1 = kk, l2 = kk, l3 = kk;
-                for (int k = 0; k < DC; ++k) {
-                    const uint32_t x = word(__ldg(rc + k));
-                    const int j = __ldg(rc + DC + DL + 2 + k);
-                    a0 += j * sbyte<0>(x);
-                    a1 += j * sbyte<1>(x);
-                    a2 += j * sbyte<2>(x);
-                    a3 += j * sbyte<3>(x);
-                }
-                for (int k = 0; k < DL; ++k) {
-                    const uint32_t y = word(__ldg(rc + DC + k));
-                    const int w = L.penalty ? __ldg(rc + 2 * DC + DL + 2 + k) : 1;
-                    l0 += w * sbyte<0>(y);
-                    l1 += w * sbyte<1>(y);
-                    l2 += w * sbyte<2>(y);
-                    l3 += w * sbyte<3>(y);
-                }
-                const uint4 r = philox4x32_10(
-                    make_uint4(static_cast<uint32_t>(__ldg(rc + DC + DL)), sweep, lq, c3), rk);
-                *reinterpret_cast<uint32_t *>(smg + (pos << sw_shift) + lane_off) =
-                    decide_fields(q, a0 + q.p0 * l0, a1 + q.p1 * l1, a2 + q.p2 * l2, a3 + q.p3 * l3, r);
-            }
-            __syncthreads();
-        }
-    }
-    const int64_t nvec_out = static_cast<int64_t>(L.n) * vec_per_row;
-    for (int64_t i = threadIdx.x; i < nvec_out; i += blockDim.x) {
-        const int64_t row = i / vec_per_row;
-        const int part = static_cast<int>(i - row * vec_per_row);
-        *reinterpret_cast<uint4 *>(L.S + row * L.Wc + col0 + 16 * part) = reinterpret_cast<const uint4 *>(smg)[i];
-    }
-    // f and g of the final sweep (twice g: links from both ends, twice k of down spins)
-    __shared__ long long s_F[kMaxSlab];
-    __shared__ int s_g[kMaxSlab];
-    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
-        s_F[i] = 0;
-        s_g[i] = 0;
-    }
-    __syncthreads();
-    long long F[4] = {0, 0, 0, 0};
-    int g[4] = {0, 0, 0, 0};
-    for (int pos = grp; pos < L.n; pos += G) {
-        const int *rc = recs + static_cast<int64_t>(pos) * rec_ints;
-        const uint32_t xs = word(pos << sw_shift);
-        const int h4 = 2 * __ldg(rc + DC + DL + 1);
-        int cc[4] = {h4, h4, h4, h4};
-        for (int k = 0; k < DC; ++k) {
-            const uint32_t x = word(__ldg(rc + k));
-            const int j = __ldg(rc + DC + DL + 2 + k);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) cc[b] += j * sbyte_rt(x, b);
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) F[b] += static_cast<long long>(sbyte_rt(xs, b)) * cc[b];
-        for (int k = 0; k < DL; ++k) {
-            const int lp = __ldg(rc + DC + k);
-            if (lp == L.pad_ref) continue;
-            const uint32_t y = word(lp);
-            const int w = L.penalty ? __ldg(rc + 2 * DC + DL + 2 + k) : 1;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) g[b] += w * (sbyte_rt(xs, b) != sbyte_rt(y, b));
-        }
-        if (L.penalty) {
-            const int k2 = 2 * __ldg(rc + 2 * DC + 2 * DL + 2);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) g[b] += sbyte_rt(xs, b) < 0 ? k2 : 0;
-        }
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&s_F[lane_off + b]), static_cast<unsigned long long>(F[b]));
-        atomicAdd(&s_g[lane_off + b], g[b]);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
-        wk.f[col0 + i] = -(s_F[i] / 4);
-        wk.g[col0 + i] = s_g[i] / 2 + L.g0;
-    }
-}
-
 __global__ void k_init_spins(Layout L, int32_t quads_per_run, uint32_t k0, uint32_t k1) {
     const int64_t quads = L.Wc / 4;
     const int64_t total = static_cast<int64_t>(L.n) * quads;
@@ -717,6 +488,7 @@ cudaError_t launch_init(const Layout &L, const RunState &rs, const Walkers &wk, 
 cudaError_t launch_sweeps(const Layout &L, const Walkers &wk, const SweepTiling &tl,
                           int32_t quads_per_run, uint64_t seed, uint32_t sweep0, int32_t nsweeps,
                           cudaStream_t st) {
+    if (L.penalty) return cudaErrorInvalidValue;  // specialised records only
     const RoundKeys rk = round_keys(seed);
     if (tl.bits) {
         if (L.DC == 3 && L.DL == 2) return launch_bits_variant<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
@@ -725,30 +497,15 @@ cudaError_t launch_sweeps(const Layout &L, const Walkers &wk, const SweepTiling 
         return cudaErrorInvalidValue;
     }
     if (tl.smem) {
-        if (!L.penalty && L.DC == 3 && L.DL == 2) return launch_smem<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
-        if (!L.penalty && L.DC == 4 && L.DL == 2) return launch_smem<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
-        if (!L.penalty && L.DC == 6 && L.DL == 2) return launch_smem<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
-        int shift = 0;
-        while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
-        const size_t smem = smem_sweep_bytes(L.n, 1 << shift);
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_generic_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
-        k_sweep_generic_smem<<<blocks, tl.threads, smem, st>>>(L, wk, shift, quads_per_run, rk, sweep0, nsweeps);
-        return cudaGetLastError();
+        if (L.DC == 3 && L.DL == 2) return launch_smem<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        if (L.DC == 4 && L.DL == 2) return launch_smem<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        if (L.DC == 6 && L.DL == 2) return launch_smem<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+        return cudaErrorInvalidValue;
     }
-    if (!L.penalty && L.DC == 3 && L.DL == 2)
-        return launch_global_variant<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
-    if (!L.penalty && L.DC == 4 && L.DL == 2)
-        return launch_global_variant<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
-    if (!L.penalty && L.DC == 6 && L.DL == 2)
-        return launch_global_variant<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
-    int shift = 0;
-    while ((1 << shift) < tl.lanes_per_spin) ++shift;
-    const unsigned blocks = static_cast<unsigned>(L.Wc / (4LL * tl.lanes_per_spin));
-    k_sweep_generic<<<blocks, tl.threads, 0, st>>>(L, wk, shift, quads_per_run, rk, sweep0, nsweeps);
-    return cudaGetLastError();
+    if (L.DC == 3 && L.DL == 2) return launch_global_variant<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+    if (L.DC == 4 && L.DL == 2) return launch_global_variant<4, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+    if (L.DC == 6 && L.DL == 2) return launch_global_variant<6, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_swap_event(const Layout &L, const RunState &rs, const Walkers &wk,

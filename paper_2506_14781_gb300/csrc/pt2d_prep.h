@@ -18,13 +18,16 @@ struct Prep {
     int32_t rec_vec = 0, pad_ref = 0;
     bool penalty = false;  // link weights other than 1 or penalty fields: generic records
     bool pen_kernel = false;  // penalty records swept by the degree-specialised shared-memory kernel
+    bool wide = false;        // wide records (pt2d_wide.cuh) for the runtime-degree kernels
+    int32_t dcmax = 0;        // largest coupling degree before padding
     int32_t g0 = 0;        // constant term of g
     std::vector<int32_t> color, pid, pos_of, cofs, rec;
 };
 
 // Validates the instance and ladders (beta / P may be NULL for size queries),
 // colours it, orders spins by colour and packs the neighbour records; with
-// force_dc > 0 the records use that coupling width (links 2) or the call fails.
+// force_dc > 0 the records use that coupling width (links 2) or the call fails;
+// with force_dc < 0 they use the wide layout of the runtime-degree kernels.
 // Also chooses the plain-context sweep tiling from `opt` and `runs`.
 int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, const int32_t *P,
             int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc = 0);
