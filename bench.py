@@ -64,12 +64,12 @@ BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
 # DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only while the kernel sources hash to `src`; the summaries are under profiles/.
 PROFILED_TRAFFIC = {
-    ("n200", "k_sweep_smem"): dict(src="bd5e83aa7856705b", dram_bytes_per_launch=387_603_712,
+    ("n200", "k_sweep_smem"): dict(src="971882812ba8f7ec", dram_bytes_per_launch=386_739_712,
                                    profile="profiles/k_sweep_smem_n200.md"),
     # captured at 4 of the 16 runs and scaled by the walkers
-    ("n800", "k_sweep_bits"): dict(src="bd5e83aa7856705b", dram_bytes_per_launch=18_844_223_488,
+    ("n800", "k_sweep_bits"): dict(src="971882812ba8f7ec", dram_bytes_per_launch=19_173_867_520,
                                    profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
-    ("constrained", "k_sweep_penalty_smem"): dict(src="20ec3f524dc8ee88", dram_bytes_per_launch=341_336_832,
+    ("constrained", "k_sweep_penalty_smem"): dict(src="1116f5aad9bb58c3", dram_bytes_per_launch=341_334_784,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h")
