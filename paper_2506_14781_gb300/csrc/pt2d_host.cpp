@@ -215,9 +215,10 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.runs = runs;
     pp.C = C;
     pp.trace_cap = opt ? std::max<int32_t>(opt->trace_capacity, 0) : 1024;
-    // Sweep tiling.  The shared-memory kernel holds a CTA's whole slab,
-    // (n + 1) x SW bytes, for the swap interval; it needs one of the specialised
-    // degree layouts.  Otherwise the slab stays in global memory.
+    // Sweep tiling.  The shared-memory kernels hold a CTA's whole slab,
+    // (n + 1) x SW bytes (int8) or (n + 1) x SW / 8 bytes (bit-packed, the
+    // specialised layouts only), for the swap interval; otherwise the slab
+    // stays in global memory.
     int sms = 152, smem_max = 232448;
     {
         int dev = 0;
@@ -268,8 +269,8 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         }
         return best ? best : smallest;
     };
-    // shared-memory slab width (0 = global kernel).  Layouts other than the
-    // specialised ones run the generic shared-memory kernel (int8 only).
+    // int8 shared-memory slab width (0 = global kernel): the specialised, the
+    // penalty-specialised or the runtime-degree shared-memory kernel.
     int sw = 0;
     if (mode == 0 || mode == 2) {
         if (req_w) {

@@ -16,7 +16,7 @@ struct Prep {
     int32_t trace_cap = 0;
     pt2d::SweepTiling tiling{};
     int32_t rec_vec = 0, pad_ref = 0;
-    bool penalty = false;  // link weights other than 1 or penalty fields: generic records
+    bool penalty = false;  // link weights other than 1 or penalty fields (records carry K and k)
     bool pen_kernel = false;  // penalty records swept by the degree-specialised shared-memory kernel
     bool wide = false;        // wide records (pt2d_wide.cuh) for the runtime-degree kernels
     int32_t dcmax = 0;        // largest coupling degree before padding
