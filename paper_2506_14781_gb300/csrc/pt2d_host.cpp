@@ -628,7 +628,6 @@ int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const floa
     };
     cudaError_t e = cudaMemsetAsync(c->ws, 0, need - 256, s);
     if (e != cudaSuccess) return fail(e);
-    const int64_t n = pp.n;
     struct Up {
         void *d;
         const void *h;
