@@ -581,7 +581,7 @@ def run_batched(args):
 
 def run_compare(args):
     """2D-PT against the J-column PT baseline (the paper's Fig. 3 comparison
-    shape) on synthetic planted Wishart instances: N in {20, 30, 40, 50},
+    shape) on synthetic planted Wishart instances: N in `--cmp-ns` (20, 30, 40, 50),
     alpha = 0.75, I = 16 x J = 8, sparsified either to <= 3 original edges per
     copy (`--cmp-sparsify max_edges3`) or to three copies per node, the paper's
     setting (`fixed3`: ~N/3 couplings per copy, on the batch's runtime-degree
@@ -602,7 +602,7 @@ def run_compare(args):
 
     I, J, interval, E = 16, 8, 50, args.cmp_events
     per_N = args.cmp_instances
-    Ns = (20, 30, 40, 50)
+    Ns = tuple(args.cmp_ns)
     probs = []
     for N in Ns:
         for k in range(per_N):
@@ -617,7 +617,8 @@ def run_compare(args):
     for mode in ("2d", "jcolumn"):
         ladders = [(P if mode == "2d" else np.full(J, int(np.rint(P.mean())), np.int32))
                    for _, _, _, P in probs]
-        degree = 3 if args.cmp_sparsify == "max_edges3" else 64
+        degree = 3 if args.cmp_sparsify == "max_edges3" else max(
+            64, max(int(np.diff(phys.cp_ptr).max()) for _, phys, _, _ in probs))
         b = pt.Batch(1 << 30, degree, len(probs), stream=stream, trace_capacity=E, swap_mode=mode)
         ids = [b.add(phys, beta, Pm, 1, 777 + k, inst.E_planted)
                for k, ((inst, phys, beta, _), Pm) in enumerate(zip(probs, ladders))]
@@ -960,6 +961,7 @@ def main():
     ap.add_argument("--cmp-events", type=int, default=2000)
     ap.add_argument("--cmp-instances", type=int, default=64)
     ap.add_argument("--cmp-sparsify", default="max_edges3", choices=["max_edges3", "fixed3"])
+    ap.add_argument("--cmp-ns", type=int, nargs="+", default=[20, 30, 40, 50])
     ap.add_argument("--rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--drain", type=float, default=30.0)
