@@ -13,6 +13,7 @@ round of P- or beta-swaps and the bottom-right record.  The int8 spin state
 --workload batched / serving: the uneven batch and the request stream.
 --workload constrained: 3-colouring of a random cubic graph with one-hot
 constraints (general penalty terms), I = 16 x J = 8, 256 runs.
+--workload membw: L2 and HBM read ceilings from the library's read probe.
 
 Metric: spin updates per second (physical spins x replicas x sweeps / time).
 
@@ -856,6 +857,40 @@ def run_constrained(args):
     print(json.dumps(line))
 
 
+def run_membw(args):
+    """Read ceilings of L2 and HBM from the library's read probe
+    (pt2d_diag_read_bandwidth): 16-byte loads cached in L2 only, 8 CTAs of 256
+    threads per SM, over buffers of 24, 48 and 96 MB (L2-resident after a
+    warm-up pass; L2 is 129 MB) and of 8 GB (HBM).  GB/s = bytes x passes /
+    time, best of three timings; the ceilings against which the L2 and HBM
+    traffic of the sweep kernels (from ncu) is judged."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # a one-GPU workload
+    import torch
+
+    import paper_2506_14781_gb300 as pt
+
+    out = torch.zeros(4, dtype=torch.int32, device="cuda")
+    res = {}
+    for mb, passes in ((24, 2000), (48, 1000), (96, 500), (8192, 6)):
+        buf = torch.ones(mb << 20, dtype=torch.uint8, device="cuda")
+        pt.diag_read_bandwidth(buf, 2, out)  # warm-up: bring an L2-sized buffer into L2
+        best = min(pt.diag_read_bandwidth(buf, passes, out) for _ in range(3))
+        res[mb] = (mb << 20) * passes / (best / 1e3) / 1e9
+        del buf
+    peaks, src = _peaks()
+    line = {
+        "metric": "read bandwidth ceilings: L2-resident buffers and HBM (project read probe)",
+        "value": max(res[m] for m in (24, 48, 96)), "unit": "GB/s", "n_gpus": 1, "higher_is_better": True,
+        "data": "device buffers of ones",
+        "config": {"workload": "pt2d_diag_read_bandwidth over 24, 48, 96 MB and 8 GB, best of 3"},
+        "l2_read_gbs": {f"{m} MB": res[m] for m in (24, 48, 96)},
+        "hbm_read_gbs": res[8192],
+        "hbm_copy_gbs_measured": peaks.get("hbm_gbs"), "peaks_source": src,
+    }
+    print(json.dumps(line))
+
+
 def run_serving(args):
     """Serving workload: a Poisson stream of constrained Ising requests at
     `--rates` requests per minute for `--duration` seconds each, then up to
@@ -956,7 +991,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=100, help="oracle sample, N=200 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2", "constrained"])
+    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2", "constrained", "membw"])
     ap.add_argument("--fig2-events", type=int, default=8000)
     ap.add_argument("--cmp-events", type=int, default=2000)
     ap.add_argument("--cmp-instances", type=int, default=64)
@@ -988,6 +1023,8 @@ def main():
         run_fig2(args)
     elif args.workload == "constrained":
         run_constrained(args)
+    elif args.workload == "membw":
+        run_membw(args)
     else:
         run_gpu(args)
 

@@ -551,6 +551,16 @@ int pt2d_diag_heatbath(const float *beta, const int32_t *H, const uint32_t *r, i
                        int64_t count);
 int pt2d_diag_swap_accept(const float *x, const uint32_t *r, int8_t *accept, int64_t count);
 
+/* Read-bandwidth probe: `iters` passes of 16-byte loads (cached in L2 only)
+ * over `bytes` of device memory at device_buf (16-byte aligned, bytes a
+ * multiple of 16), on the legacy default stream; *ms receives the time of all
+ * passes from CUDA events.  device_out: 4 bytes of device memory the probe may
+ * write (it keeps the loads alive; the value is meaningless).  A buffer well
+ * below the L2 size measures the L2 read ceiling after a warm-up call, one well
+ * above it the HBM read ceiling.  Errors: INVALID_ARG, UNSUPPORTED (no
+ * device), CUDA. */
+int pt2d_diag_read_bandwidth(const void *device_buf, size_t bytes, int32_t iters, void *device_out, float *ms);
+
 #ifdef __cplusplus
 }
 #endif

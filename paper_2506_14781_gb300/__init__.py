@@ -21,7 +21,7 @@ __all__ = [
     "PhysicalInstance", "sparsify", "greedy_color", "PT2D", "Batch", "PoolFull", "Server",
     "Pt2dError", "onehot_penalty", "equality_penalty", "adaptive_schedule",
     "diag_philox",
-    "diag_pt_exp", "diag_heatbath", "diag_swap_accept", "STATES", "WALKER_AT", "F", "G",
+    "diag_pt_exp", "diag_heatbath", "diag_swap_accept", "diag_read_bandwidth", "STATES", "WALKER_AT", "F", "G",
     "COUNTERS", "TRACE_F", "TRACE_G", "BEST_F", "BEST_EVENT", "BEST_STATE", "SOLVED_EVENT",
     "ACC_P", "ACC_B", "SUM_F", "SUM_G", "N_FEASIBLE", "COLORS", "TARGET",
 ]
@@ -587,3 +587,16 @@ def diag_swap_accept(x, r) -> np.ndarray:
     out = np.empty(x.size, np.int8)
     _diag("pt2d_diag_swap_accept", [x, r], [out], x.size)
     return out
+
+
+def diag_read_bandwidth(buf, iters: int, out) -> float:
+    """Milliseconds for `iters` read passes over a device buffer (any object
+    with a CUDA data pointer and byte size, e.g. a torch tensor), L2-cached
+    16-byte loads (pt2d_diag_read_bandwidth); `out` is a device buffer of at
+    least 4 bytes the probe may write."""
+    ms = C.c_float()
+    ptr = C.c_void_p(int(buf.data_ptr()))
+    nbytes = int(buf.numel() * buf.element_size())
+    _lib.check(_lib.lib().pt2d_diag_read_bandwidth(ptr, nbytes, int(iters), C.c_void_p(int(out.data_ptr())),
+                                                   C.byref(ms)), "pt2d_diag_read_bandwidth")
+    return float(ms.value)

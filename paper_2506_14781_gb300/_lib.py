@@ -38,7 +38,7 @@ EXPORTS = [
     "pt2d_batch_launch_count", "pt2d_batch_cuda_error", "pt2d_batch_destroy", "pt2d_batch_poll",
     "pt2d_server_create", "pt2d_server_submit", "pt2d_server_step", "pt2d_server_status",
     "pt2d_server_cancel", "pt2d_server_forget", "pt2d_server_free_bytes", "pt2d_server_destroy",
-    "pt2d_adaptive_schedule", "pt2d_onehot_penalty", "pt2d_equality_penalty",
+    "pt2d_adaptive_schedule", "pt2d_onehot_penalty", "pt2d_equality_penalty", "pt2d_diag_read_bandwidth",
     "pt2d_debug_fail_allocations",
 ]
 
@@ -180,6 +180,7 @@ def lib():
                                           C.POINTER(C.c_int64)]
         L.pt2d_equality_penalty.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, C.POINTER(i32), vp,
                                             C.POINTER(C.c_int64)]
+        L.pt2d_diag_read_bandwidth.argtypes = [vp, sz, i32, vp, C.POINTER(C.c_float)]
         L.pt2d_adaptive_schedule.argtypes = [C.POINTER(Instance), C.POINTER(ScheduleParams), vp,
                                              C.POINTER(C.c_float), C.POINTER(i32), C.POINTER(i32),
                                              C.POINTER(i32), C.POINTER(C.c_int64)]

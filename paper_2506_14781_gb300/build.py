@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
 SOURCES = ["pt2d_kernels.cu", "pt2d_host.cpp", "pt2d_noalloc.cu", "pt2d_batch.cu", "pt2d_batch_host.cpp",
-           "pt2d_server.cpp", "pt2d_schedule.cpp", "pt2d_penalty.cu", "pt2d_generic.cu"]
+           "pt2d_server.cpp", "pt2d_schedule.cpp", "pt2d_penalty.cu", "pt2d_generic.cu", "pt2d_probe.cu"]
 
 
 def _nvcc() -> str:
