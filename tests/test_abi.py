@@ -126,3 +126,14 @@ def test_allocation_failure_hook_counts_without_a_gpu():
     assert pt.debug_fail_allocations(3) == 0
     assert pt.debug_fail_allocations(0) == 3
     assert pt.debug_fail_allocations(-5) == 0
+
+
+def test_read_probe_rejects_bad_arguments_without_a_gpu(pt):
+    L = pt._lib.lib()
+    ms = C.c_float()
+    buf = C.c_void_p(4096)  # never dereferenced: every call below fails its argument check
+    assert L.pt2d_diag_read_bandwidth(None, 1024, 1, buf, C.byref(ms)) == -1
+    assert L.pt2d_diag_read_bandwidth(buf, 1000, 1, buf, C.byref(ms)) == -1  # not a multiple of 16
+    assert L.pt2d_diag_read_bandwidth(buf, 1024, 0, buf, C.byref(ms)) == -1
+    assert L.pt2d_diag_read_bandwidth(C.c_void_p(4100), 1024, 1, buf, C.byref(ms)) == -1  # unaligned
+    assert L.pt2d_diag_read_bandwidth(buf, 1024, 1, None, C.byref(ms)) == -1

@@ -61,3 +61,21 @@ def test_refused_inputs_leave_the_context_usable(pt):
     ctx.run(10, 5, 7)
     assert ctx.read(pt.COUNTERS)[1] == 4
     ctx.close()
+
+
+@pytest.mark.gpu
+def test_read_probe_times_l2_and_rejects_bad_calls():
+    """The read-bandwidth probe returns a positive time for an L2-sized buffer
+    and a larger one for more passes; misaligned or unsized calls are refused."""
+    import torch
+
+    import paper_2506_14781_gb300 as pt
+
+    buf = torch.ones(8 << 20, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(4, dtype=torch.int32, device="cuda")
+    pt.diag_read_bandwidth(buf, 2, out)
+    t1 = pt.diag_read_bandwidth(buf, 10, out)
+    t2 = pt.diag_read_bandwidth(buf, 200, out)
+    assert 0 < t1 < t2
+    with pytest.raises(pt.Pt2dError):
+        pt.diag_read_bandwidth(buf[1:17], 1, out)  # not 16-byte aligned
