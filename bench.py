@@ -927,6 +927,9 @@ def run_serving(args):
         t0 = time.perf_counter()
         nxt = 0
         steps = 0
+        pool_bytes = args.pool_gb << 30
+        free0 = srv.free_bytes()
+        peak_used, peak_active = 0, 0
         while True:
             now = time.perf_counter() - t0
             while nxt < arrivals.size and arrivals[nxt] <= now:
@@ -937,6 +940,8 @@ def run_serving(args):
                 break
             active, queued, _ = srv.step()
             steps += 1
+            peak_active = max(peak_active, active)
+            peak_used = max(peak_used, free0 - srv.free_bytes())
             if active == 0 and queued == 0:
                 if nxt >= arrivals.size:
                     break
@@ -968,6 +973,8 @@ def run_serving(args):
             "solves_per_s": solved / wall, "completed_per_s": done / wall,
             "spin_updates_per_s_completed": updates / wall,
             "median_best_residual_per_spin": pct(rho, 50),
+            "resident_peak": int(peak_active), "memory_admitted_peak_bytes": int(peak_used),
+            "pool_bytes": int(pool_bytes),
         })
     line = {
         "metric": "serving p50/p99 latency and solves/sec", "value": results[0]["solves_per_s"],
