@@ -928,7 +928,7 @@ def run_serving(args):
         nxt = 0
         steps = 0
         pool_bytes = args.pool_gb << 30
-        free0 = srv.free_bytes()
+        free0 = srv.free_bytes
         peak_used, peak_active = 0, 0
         while True:
             now = time.perf_counter() - t0
@@ -941,7 +941,7 @@ def run_serving(args):
             active, queued, _ = srv.step()
             steps += 1
             peak_active = max(peak_active, active)
-            peak_used = max(peak_used, free0 - srv.free_bytes())
+            peak_used = max(peak_used, free0 - srv.free_bytes)
             if active == 0 and queued == 0:
                 if nxt >= arrivals.size:
                     break
