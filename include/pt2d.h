@@ -128,8 +128,8 @@ typedef struct {
     int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 int8 slab in
                                 shared memory (also for generic degree layouts and
                                 penalty terms), 3 bit-packed slab in shared memory
-                                (specialised layouts only; 2, 3: INVALID_ARG if it
-                                does not fit)                                        */
+                                (specialised layouts only, else INVALID_ARG; 2, 3:
+                                INVALID_ARG if it does not fit)                      */
     int32_t walkers_per_thread; /* int8 shared-memory kernel: 4 or 8, others: 4;
                                    0 = automatic                                     */
     int32_t swap_mode;       /* PT2D_SWAP_2D (0): Algorithm 1.  PT2D_SWAP_JCOLUMN (1):

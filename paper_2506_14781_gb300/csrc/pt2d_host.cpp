@@ -238,6 +238,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     if (opt && opt->swap_mode != PT2D_SWAP_2D && opt->swap_mode != PT2D_SWAP_JCOLUMN)
         return PT2D_ERR_INVALID_ARG;
     const bool specialised = !penalty && DL == 2 && (DC == 3 || DC == 4 || DC == 6);
+    if (mode == 3 && !specialised) return PT2D_ERR_INVALID_ARG;  // bit-packed slabs: specialised layouts only
     const int64_t walkers = static_cast<int64_t>(runs) * pp.Rp;
     auto fits = [&](int sw) {
         return pt2d::smem_sweep_bytes(n, sw) + pt2d::kSweepStaticSmem <= static_cast<size_t>(smem_max);

@@ -59,12 +59,18 @@ def test_sparsifier_and_colouring_match_oracle(pt, rule, param, N, alpha, seed):
     assert na == nb and np.array_equal(ca, cb)
 
 
-def _status_of_workspace(pt, inst, I=2, J=2, runs=1):
+def _status_of_workspace(pt, inst, I=2, J=2, runs=1, sweep_kernel=None):
     from paper_2506_14781_gb300 import _lib
 
     cs = inst.c_struct()
     need = C.c_size_t()
-    st = _lib.lib().pt2d_workspace_size(C.byref(cs), I, J, runs, None, C.byref(need))
+    opt = None
+    if sweep_kernel is not None:
+        o = _lib.Options()
+        _lib.lib().pt2d_default_options(C.byref(o))
+        o.sweep_kernel = sweep_kernel
+        opt = C.byref(o)
+    st = _lib.lib().pt2d_workspace_size(C.byref(cs), I, J, runs, opt, C.byref(need))
     return st, need.value
 
 
@@ -96,6 +102,11 @@ def test_validation_rejects_malformed_instances(pt):
     # sizes
     assert _status_of_workspace(pt, good, I=0)[0] == -1
     assert _status_of_workspace(pt, good, runs=0)[0] == -1
+    # bit-packed slabs exist for the specialised layouts only
+    assert _status_of_workspace(pt, good, sweep_kernel=3)[0] == 0
+    wide = pt.sparsify(synth.wishart_planted(30, 0.5, 2).Jq, "fixed", 2)  # ~15 couplings per copy
+    assert _status_of_workspace(pt, wide, sweep_kernel=3)[0] == -1
+    assert _status_of_workspace(pt, wide, sweep_kernel=2)[0] == 0
 
 
 def test_strerror_and_defaults(pt):
