@@ -645,3 +645,36 @@ def test_colouring_full_size_sampled_runs(pt):
         orc = oracle.OracleRun(oinst, beta, P, [run_id], seed, trace_cap=8, target=prob.f_proper)
         orc.run(20, 10)
         assert_same(pt, ctx, orc, runs_sel=[run_id])
+
+
+@pytest.mark.parametrize("kernel", ["auto", "global"])
+def test_wide_records_without_links(pt, kernel):
+    """An instance with no copy links at all (a plain Ising model, g = 0) and
+    coupling degree up to 9: wide records with link width 0 on the
+    runtime-degree kernels, bit-exact with the oracle."""
+    rng = np.random.default_rng(31)
+    n = 70
+    A = np.zeros((n, n), np.int16)
+    deg = np.zeros(n, int)
+    for _ in range(n * 20):
+        a, b = (int(x) for x in rng.integers(n, size=2))
+        if a != b and A[a, b] == 0 and deg[a] < 9 and deg[b] < 9:
+            A[a, b] = A[b, a] = int(rng.integers(-32767, 32768)) or 1
+            deg[a] += 1
+            deg[b] += 1
+    cp_ptr = np.concatenate([[0], np.cumsum((A != 0).sum(1))]).astype(np.int32)
+    cp_col = np.concatenate([np.nonzero(A[a])[0] for a in range(n)]).astype(np.int32)
+    cp_J = np.concatenate([A[a][A[a] != 0] for a in range(n)]).astype(np.int16)
+    lk_ptr = np.zeros(n + 1, np.int32)
+    lk_col = np.zeros(0, np.int32)
+    h = rng.integers(-500, 501, n).astype(np.int32)
+    phys_p = pt.PhysicalInstance(n, cp_ptr, cp_col, cp_J, lk_ptr, lk_col, h=h)
+    phys_o = oracle.PhysInstance(n, cp_ptr, cp_col, cp_J, lk_ptr, lk_col, h, n, np.arange(n, dtype=np.int32),
+                                 np.arange(n + 1, dtype=np.int32))
+    beta = np.geomspace(1e-5, 3e-4, 6).astype(np.float32)
+    P = np.array([1, 5], np.int32)
+    ctx, orc = both(pt, None, None, beta, P, 4, 4711, [(30, 5), (15, 5)], phys=(phys_p, phys_o), trace=16,
+                    kernel=kernel)
+    assert ctx.tiling["kernel"] == ("generic_smem" if kernel == "auto" else "generic")
+    assert_same(pt, ctx, orc)
+    assert np.all(ctx.read(pt.G) == 0)
