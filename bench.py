@@ -75,7 +75,7 @@ PROFILED_TRAFFIC = {
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h")
 # kernels defined outside pt2d_kernels.cu hash their own file as well
-KERNEL_EXTRA_SOURCES = {"k_sweep_penalty_smem": ("pt2d_penalty.cu",)}
+KERNEL_EXTRA_SOURCES = {"k_sweep_penalty_smem": ("pt2d_penalty.cu",), "k_sweep_penalty_bits": ("pt2d_penalty.cu",)}
 
 
 def kernel_source_hash(kernel=None):
@@ -291,7 +291,7 @@ def run_gpu(args):
     tiling = ctx.tiling
     kernel = {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
               "generic": "k_sweep_generic", "generic_smem": "k_sweep_generic_smem",
-              "penalty_smem": "k_sweep_penalty_smem"}[tiling["kernel"]]
+              "penalty_smem": "k_sweep_penalty_smem", "penalty_bits": "k_sweep_penalty_bits"}[tiling["kernel"]]
     prof = PROFILED_TRAFFIC.get((args.workload, kernel))
     src_hash = kernel_source_hash(kernel)
     traffic = prof["dram_bytes_per_launch"] if prof and prof["src"] == src_hash else None
@@ -746,14 +746,15 @@ def run_fig2(args):
 
 def run_constrained(args):
     """General constraint functions (Eq. 1 with g beyond copy links): 3-colouring
-    of a random cubic graph, V = 2000 vertices (n = 6000 spins, coupling
+    of a random cubic graph, V = 2000 vertices (`--col-vertices`; n = 6000 spins, coupling
     degree 3, two one-hot links per spin), one-hot groups expanded by the
     library (pt2d_onehot_penalty), I = 16 x J = 8 (the batch's largest grid),
     256 runs (32,768 replicas, 197 MB of spins, larger than L2), swap
     interval 50.  The plain context runs it on the degree-specialised
-    penalty kernel (int8 slab in shared memory; weighted links, penalty
-    fields, g0); the same runs then go through the runtime-degree batch
-    (identical trajectories).  Reports spin
+    penalty kernel (int8 slab in shared memory, or bit-packed when the int8
+    slab does not fit, e.g. --col-vertices 40000 --runs 64; weighted links,
+    penalty fields, g0); the same runs then go through the runtime-degree
+    batch (identical trajectories).  Reports spin
     updates/s with the sweep kernel's ALU roofline and how many runs found a
     proper colouring (g = 0, f = -k W)."""
     if int(os.environ.get("RANK", "0")) != 0:
@@ -763,7 +764,7 @@ def run_constrained(args):
     import paper_2506_14781_gb300 as pt
     import synth
 
-    V, k, I, J, runs, interval = 2000, 3, 16, 8, args.runs or 256, 50
+    V, k, I, J, runs, interval = args.col_vertices, 3, 16, 8, args.runs or 256, 50
     prob = synth.colouring(V, k, 7)
     lk_ptr, lk_col, lk_w, hk, g0 = pt.onehot_penalty(prob.n, prob.groups)
     phys = pt.PhysicalInstance(prob.n, prob.cp_ptr, prob.cp_col, prob.cp_J, lk_ptr, lk_col, h=prob.h,
@@ -800,7 +801,7 @@ def run_constrained(args):
     tiling = ctx.tiling
     kernel = {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
               "generic": "k_sweep_generic", "generic_smem": "k_sweep_generic_smem",
-              "penalty_smem": "k_sweep_penalty_smem"}[tiling["kernel"]]
+              "penalty_smem": "k_sweep_penalty_smem", "penalty_bits": "k_sweep_penalty_bits"}[tiling["kernel"]]
     peaks, peak_src = _peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -814,7 +815,7 @@ def run_constrained(args):
     F_best = prob.same_colour_weight(best[feasible])
     events_done = args.warmup + args.steps
     # the same runs through the runtime-degree batch
-    batch = pt.Batch(1 << 31, max_coupling_degree=64, max_runs=runs, stream=stream,
+    batch = pt.Batch(max(1 << 31, 3 * n * R * runs), max_coupling_degree=64, max_runs=runs, stream=stream,
                      trace_capacity=events_done)
     bid = batch.add(phys, beta, P, runs, seed, prob.f_proper)
     batch.run(args.warmup, interval)
@@ -1004,6 +1005,7 @@ def main():
     ap.add_argument("--cmp-instances", type=int, default=64)
     ap.add_argument("--cmp-sparsify", default="max_edges3", choices=["max_edges3", "fixed3"])
     ap.add_argument("--cmp-ns", type=int, nargs="+", default=[20, 30, 40, 50])
+    ap.add_argument("--col-vertices", type=int, default=2000, help="constrained: vertices of the cubic graph")
     ap.add_argument("--rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--drain", type=float, default=30.0)

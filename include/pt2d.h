@@ -128,8 +128,9 @@ typedef struct {
     int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 int8 slab in
                                 shared memory (also for generic degree layouts and
                                 penalty terms), 3 bit-packed slab in shared memory
-                                (specialised layouts only, else INVALID_ARG; 2, 3:
-                                INVALID_ARG if it does not fit)                      */
+                                (specialised layouts and penalty terms with coupling
+                                degree <= 6 and link degree <= 3 only, else
+                                INVALID_ARG; 2, 3: INVALID_ARG if it does not fit)   */
     int32_t walkers_per_thread; /* int8 shared-memory kernel: 4 or 8, others: 4;
                                    0 = automatic                                     */
     int32_t swap_mode;       /* PT2D_SWAP_2D (0): Algorithm 1.  PT2D_SWAP_JCOLUMN (1):
@@ -211,7 +212,8 @@ int64_t pt2d_launch_count(const pt2d_ctx *ctx);
  * int8 slab in shared memory, 3 bit-packed slab in shared memory, 4 generic
  * degree layout in global memory, 5 generic degree layout with the int8 slab in
  * shared memory, 6 penalty terms with coupling width 3, 4 or 6 and link width
- * 2 or 3, int8 slab in shared memory), out[1] = walkers per CTA, out[2] = threads per CTA,
+ * 2 or 3, int8 slab in shared memory, 7 the same with a bit-packed slab),
+ * out[1] = walkers per CTA, out[2] = threads per CTA,
  * out[3] = walkers per thread.  Host only.  Errors: INVALID_ARG (NULL). */
 int pt2d_tiling(const pt2d_ctx *ctx, int32_t out[4]);
 

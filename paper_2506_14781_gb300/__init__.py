@@ -285,7 +285,8 @@ class PT2D:
         walkers per thread."""
         out = (C.c_int32 * 4)()
         _lib.check(_lib.lib().pt2d_tiling(self._ctx, out), "pt2d_tiling", self._ctx)
-        kernel = {1: "global", 2: "smem", 3: "bits", 4: "generic", 5: "generic_smem", 6: "penalty_smem"}[out[0]]
+        kernel = {1: "global", 2: "smem", 3: "bits", 4: "generic", 5: "generic_smem", 6: "penalty_smem",
+                  7: "penalty_bits"}[out[0]]
         return dict(kernel=kernel, walkers_per_cta=out[1], threads_per_cta=out[2],
                     walkers_per_thread=out[3])
 

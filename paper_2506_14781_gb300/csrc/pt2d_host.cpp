@@ -238,7 +238,10 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     if (opt && opt->swap_mode != PT2D_SWAP_2D && opt->swap_mode != PT2D_SWAP_JCOLUMN)
         return PT2D_ERR_INVALID_ARG;
     const bool specialised = !penalty && DL == 2 && (DC == 3 || DC == 4 || DC == 6);
-    if (mode == 3 && !specialised) return PT2D_ERR_INVALID_ARG;  // bit-packed slabs: specialised layouts only
+    // penalty terms with small degrees: the penalty-specialised kernels (int8 or bit-packed slab)
+    const bool pen_ok = !spec_layout && force_dc == 0 && penalty && dcmax <= 6 && dlmax <= 3;
+    // bit-packed slabs: specialised and penalty-specialised layouts only
+    if (mode == 3 && !specialised && !pen_ok) return PT2D_ERR_INVALID_ARG;
     const int64_t walkers = static_cast<int64_t>(runs) * pp.Rp;
     auto fits = [&](int sw) {
         return pt2d::smem_sweep_bytes(n, sw) + pt2d::kSweepStaticSmem <= static_cast<size_t>(smem_max);
@@ -285,7 +288,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     auto fits_bits = [&](int cand) {
         return pt2d::bits_sweep_bytes(n, cand) + pt2d::kSweepStaticSmem <= static_cast<size_t>(smem_max);
     };
-    if (specialised && (mode == 3 || (mode == 0 && sw == 0))) {
+    if ((specialised || pen_ok) && (mode == 3 || (mode == 0 && sw == 0))) {
         sw = 0;
         if (req_w) {
             if (req_w >= 8 && fits_bits(req_w)) bw = req_w;
@@ -339,7 +342,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.tiling.smem = sw != 0;
     pp.tiling.bits = bw != 0;
     pp.tiling.walkers_per_thread = wpt;
-    pp.pen_kernel = !spec_layout && force_dc == 0 && penalty && sw != 0 && wpt == 4 && dcmax <= 6 && dlmax <= 3;
+    pp.pen_kernel = pen_ok && (sw != 0 || bw != 0) && wpt == 4;
     if (pp.pen_kernel) {
         // padded up to a layout of the penalty-specialised kernel (padding
         // entries point at the zero row with J = 0, K = 0)
@@ -682,7 +685,8 @@ int pt2d_num_colors(const pt2d_ctx *c) { return c ? c->pp.C : 0; }
 int pt2d_tiling(const pt2d_ctx *c, int32_t out[4]) {
     if (!c || !out) return PT2D_ERR_INVALID_ARG;
     const pt2d::SweepTiling &t = c->pp.tiling;
-    out[0] = t.bits ? 3 : t.smem ? (c->pp.pen_kernel ? 6 : (c->pp.wide ? 5 : 2)) : (c->pp.wide ? 4 : 1);
+    out[0] = t.bits ? (c->pp.pen_kernel ? 7 : 3)
+                    : t.smem ? (c->pp.pen_kernel ? 6 : (c->pp.wide ? 5 : 2)) : (c->pp.wide ? 4 : 1);
     out[1] = 4 * t.lanes_per_spin;
     out[2] = t.threads;
     out[3] = t.walkers_per_thread;

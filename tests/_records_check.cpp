@@ -148,6 +148,7 @@ int main() {
         {3, 2, true, 0, 0, 1},   {5, 3, true, 0, 0, 1},   {6, 2, true, 0, 2, 1},   {9, 2, false, 0, 0, 2},
         {3, 4, false, 0, 0, 2},  {13, 3, true, 0, 0, 2},  {3, 2, true, 0, 1, 2},   {3, 2, false, -1, 1, 2},
         {21, 5, true, -1, 1, 2}, {1, 1, false, -1, 1, 2}, {7, 0, false, 0, 2, 2},
+        {3, 2, true, 0, 3, 1},   {6, 3, true, 0, 3, 1},   {3, 2, false, 0, 3, 0},
     };
     for (const Case &c : cs) {
         for (int rep = 0; rep < 3; ++rep) {

@@ -508,19 +508,22 @@ def _graph_colouring_pair(pt, V, k, max_deg, seed):
     return phys_p, phys_o, int(deg.max())
 
 
-@pytest.mark.parametrize("k,max_deg,wpc", [(3, 3, 0), (4, 3, 16), (3, 4, 0), (4, 4, 32), (3, 6, 0), (4, 5, 64)])
-def test_penalty_specialised_kernel_bit_exact(pt, k, max_deg, wpc):
+@pytest.mark.parametrize("k,max_deg,wpc,kernel", [
+    (3, 3, 0, "auto"), (4, 3, 16, "auto"), (3, 4, 0, "auto"), (4, 4, 32, "auto"), (3, 6, 0, "auto"),
+    (4, 5, 64, "auto"), (3, 3, 8, "bits"), (4, 3, 16, "bits"), (3, 4, 64, "bits"), (4, 5, 128, "bits")])
+def test_penalty_specialised_kernel_bit_exact(pt, k, max_deg, wpc, kernel):
     """Instances with penalty terms and coupling degree <= 6, link degree <= 3
-    run on the degree-specialised shared-memory kernel (records padded to
-    coupling width 3, 4 or 6 and link width 2 or 3), bit-exact with the
-    oracle, over several slab widths and a ragged last tile."""
+    run on the degree-specialised kernels (records padded to coupling width 3,
+    4 or 6 and link width 2 or 3), with the slab as int8 or bit-packed in
+    shared memory, bit-exact with the oracle, over several slab widths and a
+    ragged last tile."""
     phys_p, phys_o, dmax = _graph_colouring_pair(pt, 40, k, max_deg, 100 + 10 * k + max_deg)
     assert dmax == max_deg
     beta = np.array([0.03, 0.1, 0.4, 1.2, 3.0], np.float32)
     P = np.array([1, 2, 4, 9], np.int32)
     ctx, orc = both(pt, None, None, beta, P, 7, 97531, [(48, 4), (20, 4)], phys=(phys_p, phys_o), trace=24,
-                    target=-10 ** 6, wpc=wpc)
-    assert ctx.tiling["kernel"] == "penalty_smem"
+                    target=-10 ** 6, wpc=wpc, kernel=kernel)
+    assert ctx.tiling["kernel"] == ("penalty_bits" if kernel == "bits" else "penalty_smem")
     assert_same(pt, ctx, orc)
     assert np.all(ctx.read(pt.G) >= 0)
 
