@@ -72,6 +72,9 @@ PROFILED_TRAFFIC = {
                                    profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
     ("constrained", "k_sweep_penalty_smem"): dict(src="1116f5aad9bb58c3", dram_bytes_per_launch=341_334_784,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
+    # V = 40000 colouring: captured at 16 of the 64 runs and scaled by the walkers
+    ("constrained", "k_sweep_penalty_bits"): dict(src="514f809c272428c6", dram_bytes_per_launch=3_795_927_040,
+                                                  profile="profiles/k_sweep_penalty_bits_colouring40k.md (16 runs x 4)"),
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h")
 # kernels defined outside pt2d_kernels.cu hash their own file as well
