@@ -70,7 +70,7 @@ PROFILED_TRAFFIC = {
     # captured at 4 of the 16 runs and scaled by the walkers
     ("n800", "k_sweep_bits"): dict(src="971882812ba8f7ec", dram_bytes_per_launch=19_173_867_520,
                                    profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
-    ("constrained", "k_sweep_penalty_smem"): dict(src="1116f5aad9bb58c3", dram_bytes_per_launch=341_334_784,
+    ("constrained", "k_sweep_penalty_smem"): dict(src="514f809c272428c6", dram_bytes_per_launch=341_006_592,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
     # V = 40000 colouring: captured at 16 of the 64 runs and scaled by the walkers
     ("constrained", "k_sweep_penalty_bits"): dict(src="514f809c272428c6", dram_bytes_per_launch=3_795_927_040,
