@@ -76,7 +76,7 @@ PROFILED_TRAFFIC = {
     ("constrained", "k_sweep_penalty_bits"): dict(src="514f809c272428c6", dram_bytes_per_launch=3_795_927_040,
                                                   profile="profiles/k_sweep_penalty_bits_colouring40k.md (16 runs x 4)"),
 }
-KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h")
+KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h", "pt2d_wide.cuh")
 # kernels defined outside pt2d_kernels.cu hash their own file as well
 KERNEL_EXTRA_SOURCES = {"k_sweep_penalty_smem": ("pt2d_penalty.cu",), "k_sweep_penalty_bits": ("pt2d_penalty.cu",)}
 

@@ -387,6 +387,15 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         for (size_t k = 0; k < ladj[a].size(); ++k) r[DC + k] = pp.pos_of[ladj[a][k].first];
         r[DC + DL] = a;
         r[DC + DL + 1] = inst->h ? 2 * inst->h[a] : 0;
+        if (spec_layout && DC == 3 && DL == 2) {  // packed J bytes for the dp4a field sums
+            uint32_t lo = 0, hi = 0;
+            for (size_t k = 0; k < cadj[a].size(); ++k) {
+                lo |= (static_cast<uint32_t>(cadj[a][k].second) & 0xFFu) << (8 * k);
+                hi |= (static_cast<uint32_t>(cadj[a][k].second >> 8) & 0xFFu) << (8 * k);
+            }
+            r[10] = static_cast<int32_t>(lo);
+            r[11] = static_cast<int32_t>(hi);
+        }
         if (penalty) {
             const int32_t ko = pp.wide ? jo + DC / 2 : 2 * DC + DL + 2;
             for (size_t k = 0; k < ladj[a].size(); ++k) r[ko + k] = ladj[a][k].second;

@@ -7,6 +7,7 @@
 
 #include "pt2d_device.cuh"
 #include "pt2d_internal.h"
+#include "pt2d_wide.cuh"
 
 namespace pt2d {
 
@@ -54,7 +55,10 @@ __device__ __forceinline__ uint32_t pack_signs(float t0, float t1, float t2, flo
 constexpr int kMaxSlab = 128;  // walkers per CTA
 
 // Packed neighbour record of one position: [nb_0..nb_{DC-1}, lk_0..lk_{DL-1},
-// pid, 2h, 2J_0..2J_{DC-1}] padded to whole int4s.
+// pid, 2h, 2J_0..2J_{DC-1}] padded to whole int4s.  With DC = 3 and DL = 2
+// the two padding ints hold J_0..J_2 as packed low and high bytes (byte k =
+// J_k & 0xff, resp. J_k >> 8; byte 3 zero) for the byte dot products of
+// decide4.
 template <int DC, int DL>
 struct Rec {
     static constexpr int kInts = 2 * DC + DL + 2;
@@ -108,6 +112,27 @@ __device__ __forceinline__ uint32_t decide_fields(const Quad &q, int a0, int a1,
 template <int DC, int DL>
 __device__ __forceinline__ uint32_t decide4(const Rec<DC, DL> &rc, const Quad &q, const uint32_t *x,
                                             const uint32_t *y, const uint4 &r) {
+    if constexpr (DC == 3 && DL == 2) {
+        // Byte-transpose (x0, x1, x2, y0) into one word per walker; then the
+        // coupling sum is two dp4a against the packed J bytes (sum J s =
+        // sum lo s + 256 sum hi s, exact) and the link sum one dp4a picking
+        // byte 3 plus the second link: the same integers as the loop below,
+        // with sign extraction moved from the ALU to the FMA pipe (~5 %).
+        uint32_t w0, w1, w2, w3;
+        transpose4(x[0], x[1], x[2], y[0], w0, w1, w2, w3);
+        const uint32_t lo = static_cast<uint32_t>(rc.v[10]), hi = static_cast<uint32_t>(rc.v[11]);
+        const int h2 = rc.h2();
+        const int a0 = h2 + 2 * dp4a_su(w0, lo, 256 * dp4a_ss(w0, hi, 0));
+        const int a1 = h2 + 2 * dp4a_su(w1, lo, 256 * dp4a_ss(w1, hi, 0));
+        const int a2 = h2 + 2 * dp4a_su(w2, lo, 256 * dp4a_ss(w2, hi, 0));
+        const int a3 = h2 + 2 * dp4a_su(w3, lo, 256 * dp4a_ss(w3, hi, 0));
+        const uint32_t e3 = 0x01000000u;  // picks the first link's spin from a transposed word
+        const int l0 = dp4a_ss(w0, e3, sbyte<0>(y[1]));
+        const int l1 = dp4a_ss(w1, e3, sbyte<1>(y[1]));
+        const int l2 = dp4a_ss(w2, e3, sbyte<2>(y[1]));
+        const int l3 = dp4a_ss(w3, e3, sbyte<3>(y[1]));
+        return decide_fields(q, a0 + q.p0 * l0, a1 + q.p1 * l1, a2 + q.p2 * l2, a3 + q.p3 * l3, r);
+    }
     int a0 = rc.h2(), a1 = a0, a2 = a0, a3 = a0;
 #pragma unroll
     for (int k = 0; k < DC; ++k) {

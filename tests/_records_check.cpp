@@ -4,8 +4,9 @@
 // For random instances it decodes every record with the documented layouts
 // (specialised, penalty-specialised, wide) and compares the result with the
 // instance it came from: the spin id, 2h, every coupling (neighbour and J,
-// padding entries pointing at the zero row with J = 0), every copy link, and
-// with penalty terms the link weights K and the field k.  Prints "ok" or the
+// padding entries pointing at the zero row with J = 0; for coupling width 3 also
+// the packed J bytes), every copy link, and with penalty terms the link
+// weights K and the field k.  Prints "ok" or the
 // first mismatch and exits non-zero.
 #include <algorithm>
 #include <cstdint>
@@ -100,6 +101,13 @@ int check(const Inst &in, const pt2d::Prep &pp, bool penalty) {
             } else {
                 if (r[DC + DL + 2 + k] % 2) return fail("2J parity", p, k);
                 J = r[DC + DL + 2 + k] / 2;
+                if (!pp.pen_kernel && DC == 3 && DL == 2) {  // packed bytes in the two spare ints
+                    const uint32_t lo = static_cast<uint32_t>(r[10]) >> (8 * k) & 0xFFu;
+                    const uint32_t hi = static_cast<uint32_t>(r[11]) >> (8 * k) & 0xFFu;
+                    if (256 * static_cast<int8_t>(hi) + static_cast<int>(lo) != J) return fail("packed J bytes", p, k);
+                    if ((static_cast<uint32_t>(r[10]) | static_cast<uint32_t>(r[11])) >> 24)
+                        return fail("packed J byte 3", p, k);
+                }
             }
             if (row == n) {
                 if (J != 0) return fail("padding coupling with J != 0", p, k);
