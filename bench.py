@@ -65,15 +65,15 @@ BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
 # DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only while the kernel sources hash to `src`; the summaries are under profiles/.
 PROFILED_TRAFFIC = {
-    ("n200", "k_sweep_smem"): dict(src="971882812ba8f7ec", dram_bytes_per_launch=386_739_712,
+    ("n200", "k_sweep_smem"): dict(src="adee74855b0e7033", dram_bytes_per_launch=386_782_976,
                                    profile="profiles/k_sweep_smem_n200.md"),
     # captured at 4 of the 16 runs and scaled by the walkers
-    ("n800", "k_sweep_bits"): dict(src="971882812ba8f7ec", dram_bytes_per_launch=19_173_867_520,
+    ("n800", "k_sweep_bits"): dict(src="adee74855b0e7033", dram_bytes_per_launch=18_430_910_464,
                                    profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
-    ("constrained", "k_sweep_penalty_smem"): dict(src="514f809c272428c6", dram_bytes_per_launch=341_006_592,
+    ("constrained", "k_sweep_penalty_smem"): dict(src="704df347ebd1e10c", dram_bytes_per_launch=341_058_304,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
     # V = 40000 colouring: captured at 16 of the 64 runs and scaled by the walkers
-    ("constrained", "k_sweep_penalty_bits"): dict(src="514f809c272428c6", dram_bytes_per_launch=3_795_927_040,
+    ("constrained", "k_sweep_penalty_bits"): dict(src="704df347ebd1e10c", dram_bytes_per_launch=3_800_154_112,
                                                   profile="profiles/k_sweep_penalty_bits_colouring40k.md (16 runs x 4)"),
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h", "pt2d_wide.cuh")
