@@ -14,6 +14,7 @@ round of P- or beta-swaps and the bottom-right record.  The int8 spin state
 --workload constrained: 3-colouring of a random cubic graph with one-hot
 constraints (general penalty terms), I = 16 x J = 8, 256 runs.
 --workload membw: L2 and HBM read ceilings from the library's read probe.
+--workload threecopy: the runtime-degree kernels on three copies per node.
 
 Metric: spin updates per second (physical spins x replicas x sweeps / time).
 
@@ -861,6 +862,49 @@ def run_constrained(args):
     print(json.dumps(line))
 
 
+def run_threecopy(args):
+    """The runtime-degree kernels on the paper's sparsification for its
+    ground-state runs: planted Wishart instances with alpha = 0.75 and N = 50
+    and 100 (`--threecopy-ns`), three copies per node (about N/3
+    couplings per copy), I = 20 x J = 20 ladders, 64 runs, swap interval 50;
+    each on the shared-memory kernel (automatic tiling) and on the
+    global-memory one.  Reports spin updates/s per kernel (3 warm-up events,
+    then 10 timed events, CUDA-event time of the sweep launches)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # a one-GPU workload
+    import torch  # noqa: F401  (CUDA context for the library)
+
+    import paper_2506_14781_gb300 as pt
+    import synth
+
+    Ns = args.threecopy_ns
+    rows = []
+    for N in Ns:
+        inst = synth.wishart_planted(N, 0.75, 3)
+        phys = pt.sparsify(inst.Jq, "fixed", 3)
+        beta = synth.beta_ladder(20, BETA_MIN, BETA_MAX, inst.scale)
+        P = synth.penalty_ladder(20, P_MIN, P_MAX, 32767)
+        for kernel in ("auto", "global"):
+            ctx = pt.PT2D(phys, beta, P, 64, profile=True, trace_capacity=8, sweep_kernel=kernel)
+            ctx.run(150, 50, 100)
+            ctx.sync()
+            ms0, n0 = ctx.kernel_time(0)
+            ctx.run(500, 50, 100)
+            ms1, n1 = ctx.kernel_time(0)
+            per = (ms1 - ms0) / (n1 - n0)
+            rows.append({"N": N, "spins": phys.n, "max_couplings_per_copy": int(np.diff(phys.cp_ptr).max()),
+                         "tiling": ctx.tiling, "ms_per_launch": per,
+                         "updates_per_s": phys.n * 400 * 64 * 50 / (per / 1e3)})
+            ctx.close()
+    line = {"metric": "spin updates/sec, runtime-degree kernels on three copies per node",
+            "value": rows[0]["updates_per_s"], "unit": "spin-updates/s", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic (seeded planted Wishart instances)",
+            "config": {"workload": f"alpha 0.75, N in {list(Ns)}, three copies per node, I=20 x J=20, 64 runs, "
+                                   f"swap every 50 sweeps"},
+            "kernels": rows}
+    print(json.dumps(line))
+
+
 def run_membw(args):
     """Read ceilings of L2 and HBM from the library's read probe
     (pt2d_diag_read_bandwidth): 16-byte loads cached in L2 only, 8 CTAs of 256
@@ -1002,13 +1046,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=100, help="oracle sample, N=200 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2", "constrained", "membw"])
+    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2", "constrained", "membw", "threecopy"])
     ap.add_argument("--fig2-events", type=int, default=8000)
     ap.add_argument("--cmp-events", type=int, default=2000)
     ap.add_argument("--cmp-instances", type=int, default=64)
     ap.add_argument("--cmp-sparsify", default="max_edges3", choices=["max_edges3", "fixed3"])
     ap.add_argument("--cmp-ns", type=int, nargs="+", default=[20, 30, 40, 50])
     ap.add_argument("--col-vertices", type=int, default=2000, help="constrained: vertices of the cubic graph")
+    ap.add_argument("--threecopy-ns", type=int, nargs="+", default=[50, 100])
     ap.add_argument("--rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--drain", type=float, default=30.0)
@@ -1037,6 +1082,8 @@ def main():
         run_constrained(args)
     elif args.workload == "membw":
         run_membw(args)
+    elif args.workload == "threecopy":
+        run_threecopy(args)
     else:
         run_gpu(args)
 
