@@ -273,3 +273,34 @@ def test_colouring_problem_cost_is_four_times_the_same_colour_weight():
         F = sum(int(w) for (u, v), w in zip(prob.edges.tolist(), prob.w.tolist()) if col[u] == col[v])
         assert f == 4 * F - 3 * prob.W
         assert prob.same_colour_weight(f) == F
+
+
+def test_local_field_with_weighted_equality_constraints():
+    """With general integer coefficients (link weights other than -1, fields of
+    both signs) the oracle's heat-bath field is still E(s_a = -1) - E(s_a = +1)
+    for E = f + P g, g the squared residuals."""
+    from oracle.penalties import equality
+
+    for n, cons in _equality_sets():
+        lk_ptr, lk_col, lk_w, hk, g0 = equality(n, cons)
+        rng = np.random.default_rng(n)
+        A = np.zeros((n, n), np.int16)
+        for a in range(n):
+            for b in range(a + 1, n):
+                if rng.random() < 0.3:
+                    A[a, b] = A[b, a] = rng.integers(-9, 10)
+        cp_ptr = np.concatenate([[0], np.cumsum((A != 0).sum(1))]).astype(np.int32)
+        cp_col = np.concatenate([np.nonzero(A[a])[0] for a in range(n)]).astype(np.int32)
+        cp_J = np.concatenate([A[a][A[a] != 0] for a in range(n)]).astype(np.int16)
+        h = rng.integers(-4, 5, n).astype(np.int32)
+        inst = PhysInstance(n, cp_ptr, cp_col, cp_J, lk_ptr, lk_col, h, n, np.arange(n, dtype=np.int32),
+                            np.arange(n + 1, dtype=np.int32), lk_w=lk_w, hk=hk, g0=g0)
+        oi = oracle.OracleInstance(inst)
+        for _ in range(100):
+            s = rng.choice(np.array([-1, 1], np.int8), n)
+            a = int(rng.integers(n))
+            P = int(rng.integers(0, 30))
+            up, down = s.copy(), s.copy()
+            up[a], down[a] = 1, -1
+            E = lambda t: _f_definition(inst, t[None])[0] + P * _residual_definition(t[None], cons)[0]
+            assert oi.local_field(s, a, P) == E(down) - E(up)
