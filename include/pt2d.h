@@ -16,8 +16,11 @@
  *    caller keeps ownership of every buffer it passes;
  *  - device work is queued on the context's stream; pt2d_read/pt2d_write and
  *    pt2d_sync synchronise that stream;
- *  - no global state: one context per thread at a time (contexts are
- *    independent and may live on different streams).
+ *  - no global state, with one documented exception: pt2d_run_noalloc
+ *    carves its buffers from one file-scope device array that every call of
+ *    that entry point shares (see its comment).  Otherwise one context per
+ *    thread at a time (contexts are independent and may live on different
+ *    streams).
  *
  * Numerical contract (identical on the CPU oracle and the GPU):
  *  - couplings are int16, fields and penalties integers, so f, g, E and the
@@ -454,8 +457,13 @@ int pt2d_adaptive_schedule(const pt2d_instance *inst, const pt2d_schedule_params
  * every device buffer carved from a file-scope device array of
  * PT2D_NOALLOC_SCRATCH_BYTES bytes that the library holds on each GPU it is
  * used on until the process exits.  It calls no cudaMalloc or cudaFree.
- *  - The first call on a device looks up that array's device address (with
- *    the device current); make that first call before any stream capture.
+ *  - Every call checks that the current device is an sm_103 GPU
+ *    (PT2D_ERR_UNSUPPORTED otherwise) and then looks up the array's device
+ *    address on that device.  The look-up is repeated on every call, so the
+ *    address stays right after cudaDeviceReset or under another context of
+ *    the same device; the first call on a device (and the first after a
+ *    reset) also loads the library's device code there, so make it before any
+ *    stream capture.
  *  - All calls share the array and it keeps the previous call's contents; each
  *    call clears the part it uses before starting.  Calls whose GPU work
  *    overlaps (several streams or host threads at once) race on the array and

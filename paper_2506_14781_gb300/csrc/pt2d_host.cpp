@@ -84,6 +84,17 @@ cudaError_t device_alloc(void **ptr, size_t bytes) {
     return cudaMalloc(ptr, bytes);
 }
 
+int check_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PT2D_ERR_UNSUPPORTED;
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess)
+        return PT2D_ERR_UNSUPPORTED;
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return PT2D_ERR_UNSUPPORTED;
+    return PT2D_OK;
+}
+
 int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, const int32_t *P,
             int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc) {
     if (!inst || inst->n < 1 || I < 1 || J < 1 || runs < 1) return PT2D_ERR_INVALID_ARG;
@@ -523,17 +534,6 @@ int cuda_fail(pt2d_ctx *c, cudaError_t e) {
         if (_e != cudaSuccess) return cuda_fail(ctx, _e); \
     } while (0)
 
-int check_device() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PT2D_ERR_UNSUPPORTED;
-    int major = 0, minor = 0;
-    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess)
-        return PT2D_ERR_UNSUPPORTED;
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    if (major != 10 || minor != 3) return PT2D_ERR_UNSUPPORTED;
-    return PT2D_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -581,7 +581,7 @@ int pt2d_create(pt2d_ctx **out, const pt2d_instance *inst, int32_t I, const floa
     pt2d_default_options(&dflt);
     if (!opt) opt = &dflt;
     if (opt->device >= 0 && cudaSetDevice(opt->device) != cudaSuccess) return PT2D_ERR_UNSUPPORTED;
-    int st = check_device();
+    int st = pt2d::check_device();
     if (st) return st;
     pt2d_ctx *c = new (std::nothrow) pt2d_ctx;
     if (!c) return PT2D_ERR_OOM;
@@ -1165,26 +1165,26 @@ int pt2d_sparsify(int32_t N, const int16_t *Jq, int32_t rule, int32_t param, int
 // ---- diagnostics ------------------------------------------------------------------
 int pt2d_diag_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t count) {
     if (count < 0 || (count > 0 && (!ctr || !key || !out))) return PT2D_ERR_INVALID_ARG;
-    if (int st = check_device()) return st;
+    if (int st = pt2d::check_device()) return st;
     return pt2d::diag_philox(ctr, key, out, count) == cudaSuccess ? PT2D_OK : PT2D_ERR_CUDA;
 }
 
 int pt2d_diag_pt_exp(const float *x, float *y, int64_t count) {
     if (count < 0 || (count > 0 && (!x || !y))) return PT2D_ERR_INVALID_ARG;
-    if (int st = check_device()) return st;
+    if (int st = pt2d::check_device()) return st;
     return pt2d::diag_pt_exp(x, y, count) == cudaSuccess ? PT2D_OK : PT2D_ERR_CUDA;
 }
 
 int pt2d_diag_heatbath(const float *beta, const int32_t *H, const uint32_t *r, int8_t *spin,
                        int64_t count) {
     if (count < 0 || (count > 0 && (!beta || !H || !r || !spin))) return PT2D_ERR_INVALID_ARG;
-    if (int st = check_device()) return st;
+    if (int st = pt2d::check_device()) return st;
     return pt2d::diag_heatbath(beta, H, r, spin, count) == cudaSuccess ? PT2D_OK : PT2D_ERR_CUDA;
 }
 
 int pt2d_diag_swap_accept(const float *x, const uint32_t *r, int8_t *accept, int64_t count) {
     if (count < 0 || (count > 0 && (!x || !r || !accept))) return PT2D_ERR_INVALID_ARG;
-    if (int st = check_device()) return st;
+    if (int st = pt2d::check_device()) return st;
     return pt2d::diag_swap_accept(x, r, accept, count) == cudaSuccess ? PT2D_OK : PT2D_ERR_CUDA;
 }
 

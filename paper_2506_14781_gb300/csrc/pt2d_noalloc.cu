@@ -8,39 +8,29 @@
 // two calls whose GPU work overlaps (other streams, other host threads) race on
 // it.
 #include <cstdint>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
 #include "../../include/pt2d.h"
+#include "pt2d_trace.h"
 
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PT2D_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-
 // Device address of the scratch array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// array's name is only a host-side stand-in, so its address is looked up with
+// the device current.  The look-up is repeated on every call rather than
+// cached: after cudaDeviceReset, or under another context of the same device,
+// the library's device code is loaded again at another address, and a cached
+// pointer would then point at freed memory.
 int scratch_address(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
-        return PT2D_ERR_UNSUPPORTED;
+        return PT2D_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return PT2D_ERR_CUDA;
-        }
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return PT2D_OK;
 }
 
@@ -59,6 +49,8 @@ extern "C" int pt2d_run_noalloc(const pt2d_instance *inst, int32_t I, const floa
     int st = pt2d_workspace_size(inst, I, J, runs, &opt, &need);
     if (st) return st;
     if (need > PT2D_NOALLOC_SCRATCH_BYTES) return PT2D_ERR_INVALID_ARG;
+    st = pt2d::check_device();  // before the look-up, which fails on other devices
+    if (st) return st;
     void *scratch = nullptr;
     st = scratch_address(&scratch);
     if (st) return st;

@@ -21,4 +21,7 @@ struct TraceRange {
 // if out of memory while a test has asked for injected allocation failures.
 cudaError_t device_alloc(void **ptr, size_t bytes);
 
+// PT2D_OK when the current device is an sm_103 GPU, else PT2D_ERR_UNSUPPORTED.
+int check_device();
+
 }  // namespace pt2d

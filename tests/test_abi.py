@@ -148,3 +148,21 @@ def test_read_probe_rejects_bad_arguments_without_a_gpu(pt):
     assert L.pt2d_diag_read_bandwidth(buf, 1024, 0, buf, C.byref(ms)) == -1
     assert L.pt2d_diag_read_bandwidth(C.c_void_p(4100), 1024, 1, buf, C.byref(ms)) == -1  # unaligned
     assert L.pt2d_diag_read_bandwidth(buf, 1024, 1, None, C.byref(ms)) == -1
+
+
+def test_noalloc_reports_unsupported_without_a_gpu(pt):
+    """pt2d_run_noalloc checks the device before it looks up its scratch array,
+    so without an sm_103 GPU it returns PT2D_ERR_UNSUPPORTED, as pt2d_create does."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    inst = synth.wishart_planted(10, 0.5, 1)
+    phys = pt.sparsify(inst.Jq, "fixed", 2)
+    beta = np.array([1e-5, 2e-5], np.float32)
+    P = np.array([100, 200], np.int32)
+    cs = phys.c_struct()
+    st = pt._lib.lib().pt2d_run_noalloc(C.byref(cs), 2, beta.ctypes.data_as(C.c_void_p), 2,
+                                        P.ctypes.data_as(C.c_void_p), 1, 10, 5, 1, None, None, None,
+                                        None, None)
+    assert st == -6

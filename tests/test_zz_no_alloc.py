@@ -68,12 +68,28 @@ def test_noalloc_matches_context_api_twice(pt):
     inst2 = synth.wishart_planted(10, 0.5, 1)
     cases.append((pt.sparsify(inst2.Jq, "fixed", 2), synth.beta_ladder(4, 0.1, 2.0, inst2.scale),
                   synth.penalty_ladder(4, 0.5, 4.0, 32767), 2, 200, 1, 7))
-    for phys, beta, P, runs, sweeps, interval, seed in cases:  # two calls in a row
-        st, got = _noalloc(pt, phys, beta, P, runs, sweeps, interval, seed)
-        assert st == 0, pt._lib.lib().pt2d_strerror(st)
-        ref = _reference(pt, phys, beta, P, runs, sweeps, interval, seed)
-        for k in ref:
-            assert np.array_equal(got[k], ref[k]), k
+    import torch
+
+    refs = [_reference(pt, *case) for case in cases]
+    # Any device allocation inside the entry point would now fail as out of
+    # memory: the library's allocation hook refuses the next 2^30 of them.
+    pt.debug_fail_allocations(1 << 30)
+    try:
+        for case, ref in zip(cases, refs):  # two calls in a row
+            st, got = _noalloc(pt, *case)
+            assert st == 0, pt._lib.lib().pt2d_strerror(st)
+            for k in ref:
+                assert np.array_equal(got[k], ref[k]), k
+        # a third call, repeating the first problem (its kernels are loaded by
+        # now): free device memory is the same before and after it
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        st, got = _noalloc(pt, *cases[0])
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert st == 0 and all(np.array_equal(got[k], refs[0][k]) for k in got)
+    finally:
+        pt.debug_fail_allocations(0)
 
 
 def test_noalloc_rejects_problems_beyond_scratch(pt):
