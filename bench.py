@@ -303,21 +303,24 @@ def run_gpu(args):
     alu_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
     alu_achieved = updates_per_launch * ops_per_update / (avg_launch_ms / 1e3) / 1e12
     clocks = clk.summary()
-    # time to target: bottom-right feasible at residual rho or at the planted energy
-    best = ctx.read(pt.BEST_F)
-    sec_per_sweep = elapsed_ms / 1e3 / (args.steps * interval)
-    feasible = best < np.iinfo(np.int64).max
-    rho = (best[feasible] - inst.E_planted) / (inst.N * inst.scale)
-    per = residual_tts(ctx.read(pt.TRACE_F), ctx.read(pt.TRACE_G), args.warmup + args.steps,
-                       inst.E_planted, inst.N, inst.scale, interval)
-    tts = {
-        "targets": tts_summary(per, sec_per_sweep),
-        "seconds_per_sweep_all_runs": sec_per_sweep,
-        "median_best_feasible_residual_per_spin": float(np.median(rho)) if rho.size else None,
-        "sweeps_run": int((args.warmup + args.steps) * interval),
-    }
     e2e = run_e2e(pt, phys, wl, args) if rank == 0 else None
     cpu = cpu_baseline(wl, args) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    # The metric's second half, measured outside the timed region on one GPU
+    # (under torchrun the line carries the update rate only): (a) time to
+    # target of these runs, continued; (b) the uneven batch, batched vs one
+    # context per instance; (c) time to the planted ground state, batched vs
+    # plain, on small instances where it is reached.
+    legs = args.legs == "all" and world == 1 and args.workload == "n200"
+    if legs:
+        tts = leg_tts(pt, ctx, inst, wl, seed, args.warmup + args.steps, args.tts_sweeps, stream, dev)
+    else:
+        per = residual_tts(ctx.read(pt.TRACE_F), ctx.read(pt.TRACE_G), args.warmup + args.steps,
+                           inst.E_planted, inst.N, inst.scale, interval)
+        tts = {"targets": tts_summary(per, elapsed_ms / 1e3 / (args.steps * interval)),
+               "sweeps_run": int((args.warmup + args.steps) * interval), "note": PROXY_NOTE}
+    ctx.close()
+    batched = leg_batched(pt, args, stream, dev) if legs else None
+    ground = leg_ground_state(pt, args, stream, dev) if legs else None
     line = {
         "metric": METRIC,
         "value": value,
@@ -353,11 +356,12 @@ def run_gpu(args):
         "gpu_launches": int(gpu_launches),
         "clocks": clocks,
         "tts": tts,
+        "batched": batched,
+        "ground_state": ground,
         "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -461,121 +465,264 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _cuda_events():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _timed(stream, fn):
+    """CUDA-event seconds of the work `fn` queues on `stream`."""
+    e0, e1 = _cuda_events()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+PROXY_NOTE = ("rho<=x targets (bottom-right replica feasible with residual energy per spin "
+              "(f - E_planted)/(N s) <= x) are proxies for the planted ground state; 'planted' is the "
+              "target the metric names: g = 0 and f <= E_planted")
+
+
+def leg_tts(pt, ctx, inst, wl, seed, events_done, total_sweeps, stream, dev):
+    """Time to target on the timed workload: the same runs continue (outside the
+    timed region) until `total_sweeps`; per run, sweeps until the bottom-right
+    replica first meets each target, and seconds = sweeps x the whole job's
+    measured wall time per sweep (all runs advance together)."""
+    interval = wl["interval"]
+    total_events = max(events_done, total_sweeps // interval)
+    more = total_events - events_done
+    with ClockSampler(dev) as clk:
+        secs = _timed(stream, lambda: ctx.run(more * interval, interval, seed)) if more else 0.0
+    sec_per_sweep = secs / max(more * interval, 1)
+    per = residual_tts(ctx.read(pt.TRACE_F), ctx.read(pt.TRACE_G), total_events,
+                       inst.E_planted, inst.N, inst.scale, interval)
+    best = ctx.read(pt.BEST_F)
+    feasible = best < np.iinfo(np.int64).max
+    rho = (best[feasible] - inst.E_planted) / (inst.N * inst.scale)
+    targets = tts_summary(per, sec_per_sweep)
+    for v in targets.values():
+        v["censored"] = v["runs"] - v["reached"]
+    return {"targets": targets, "sweeps_run": int(total_events * interval),
+            "seconds_per_sweep_all_runs": sec_per_sweep, "seconds_continued": secs,
+            "median_best_feasible_residual_per_spin": float(np.median(rho)) if rho.size else None,
+            "note": PROXY_NOTE + "; seconds = sweeps x the job's wall time per sweep (CUDA events)",
+            "clocks": clk.summary()}
+
+
+def batched_vs_plain(pt, probs, interval, *, batched_events, plain_events, tts_events, autotune,
+                     max_degree, stream, dev, chunk=20, plain=True):
+    """The batched persistent form against the one-instance-per-launch form on
+    the same problems (identical trajectories).
+
+    probs: (inst, phys, beta, P, seed).  The batch runs every problem in one
+    kernel launch per event (CUDA graph); the plain form is one context per
+    problem, run one after the other on the same stream.  Both forms are timed
+    with CUDA events over whole events of every problem; the plain form's
+    bottom-right (f, g) record of every event it ran is compared with the
+    batch's.  The batch then continues to `tts_events` events: per problem,
+    sweeps until each target (identical in both forms), and seconds = sweeps x
+    each form's measured wall time per sweep of the whole set."""
+    spins = sum(p[1].n for p in probs)
+    R = len(probs[0][2]) * len(probs[0][3])
+    upd_per_event = spins * R * interval
+    cap = max(tts_events, batched_events + 32)
+    probe = pt.Batch(1 << 22, max_degree, 8, stream=stream, trace_capacity=cap)
+    need = sum(probe.instance_bytes(p[1], len(p[2]), len(p[3]), 1) for p in probs)
+    probe.close()
+    batch = pt.Batch(int(need * 1.02) + (64 << 20), max_degree, len(probs), stream=stream,
+                     trace_capacity=cap)
+    ids = [batch.add(p[1], p[2], p[3], 1, p[4], p[0].E_planted) for p in probs]
+    tuned = batch.autotune(1, interval) if autotune else None
+    batch.run(1, interval)
+    done = int(batch.read(ids[0], pt.COUNTERS)[1])  # autotune trials advance the chains
+    with ClockSampler(dev) as clk_b:
+        t_batched = _timed(stream, lambda: batch.run(batched_events, interval))
+    done += batched_events
+    out = {"batched": {"seconds": t_batched, "events": batched_events,
+                       "updates_per_s": upd_per_event * batched_events / t_batched,
+                       "seconds_per_sweep": t_batched / (batched_events * interval),
+                       "shape": batch.shape, "autotuned": tuned is not None, "clocks": clk_b.summary()}}
+    if plain:
+        ctxs = [pt.PT2D(p[1], p[2], p[3], 1, stream=stream, trace_capacity=plain_events + 1)
+                for p in probs]
+        for c, p in zip(ctxs, probs):
+            c.run(interval, interval, p[4])  # warm-up event
+        stream.synchronize()
+
+        def plain_events_fn():
+            for c, p in zip(ctxs, probs):
+                c.run(plain_events * interval, interval, p[4])
+
+        with ClockSampler(dev) as clk_p:
+            t_plain = _timed(stream, plain_events_fn)
+        same, checked = 0, 0
+        for c, i in zip(ctxs, ids):
+            k = plain_events + 1
+            bt = (batch.read(i, pt.TRACE_F)[0, :k], batch.read(i, pt.TRACE_G)[0, :k])
+            ct = (c.read(pt.TRACE_F)[0, :k], c.read(pt.TRACE_G)[0, :k])
+            checked += 1
+            same += bool(np.array_equal(bt[0], ct[0]) and np.array_equal(bt[1], ct[1]))
+        launches = sum(c.launch_count for c in ctxs)
+        for c in ctxs:
+            c.close()
+        out["plain"] = {"seconds": t_plain, "events": plain_events,
+                        "updates_per_s": upd_per_event * plain_events / t_plain,
+                        "seconds_per_sweep": t_plain / (plain_events * interval),
+                        "launches_total": int(launches), "clocks": clk_p.summary(),
+                        "identical_records": f"{same} of {checked} problems: bottom-right (f, g) "
+                                             f"of all {plain_events + 1} events equal to the batch's"}
+        out["speedup_wall"] = out["plain"]["seconds_per_sweep"] / out["batched"]["seconds_per_sweep"]
+    t_more = 0.0
+    while done < tts_events:
+        k = min(chunk, tts_events - done)
+        t_more += _timed(stream, lambda: batch.run(k, interval))
+        done += k
+    per = {}
+    for i, p in zip(ids, probs):
+        r = residual_tts(batch.read(i, pt.TRACE_F), batch.read(i, pt.TRACE_G), done,
+                         p[0].E_planted, p[0].N, p[0].scale, interval)
+        for k, v in r.items():
+            per.setdefault(k, []).append(int(v[0]))
+    batch.close()
+    per = {k: np.array(v) for k, v in per.items()}
+    tts = {"events_run": int(done), "sweeps_run": int(done * interval),
+           "targets_batched": tts_summary(per, out["batched"]["seconds_per_sweep"]),
+           "seconds_continued_batched": t_more}
+    if plain:
+        tts["targets_plain"] = tts_summary(per, out["plain"]["seconds_per_sweep"])
+        tts["tts_speedup"] = {k: (tts["targets_plain"][k]["median_seconds"] /
+                                  tts["targets_batched"][k]["median_seconds"])
+                              if tts["targets_batched"][k]["median_seconds"] else None for k in per}
+        tts["plain_seconds_source"] = ("identical sweep counts x the plain form's measured wall time per "
+                                       f"sweep ({plain_events} events of every problem)")
+    out["tts"] = tts
+    out["per_problem_sweeps"] = per
+    out["spins_total"] = int(spins)
+    out["updates_per_event"] = int(upd_per_event)
+    return out
+
+
+def batched_problems(count, seed0=1000):
+    """The uneven batch: planted Wishart instances with N uniform on {50..400}
+    and alpha in {0.25, 0.5, 0.75}, each copy-chain sparsified to physical
+    degree <= 4, I = 16 x J = 8."""
+    import paper_2506_14781_gb300 as pt
+    import synth
+
+    probs = []
+    for N, alpha, seed in synth.batch_specs(count, seed0):
+        inst = synth.wishart_planted(N, alpha, seed)
+        phys = pt.sparsify(inst.Jq, "max_degree", 4)
+        probs.append((inst, phys, synth.beta_ladder(16, BETA_MIN, BETA_MAX, inst.scale),
+                      synth.penalty_ladder(8, P_MIN, P_MAX, 32767), seed))
+    return probs
+
+
+def ground_state_problems(Ns, per_N, alpha=0.75):
+    """Small planted Wishart instances with three copies per node (the paper's
+    sparsification for its ground-state runs), I = 16 x J = 8: sizes at which
+    2D-PT reaches the planted energy within 10^5 sweeps."""
+    import paper_2506_14781_gb300 as pt
+    import synth
+
+    probs = []
+    for N in Ns:
+        for k in range(per_N):
+            inst = synth.wishart_planted(N, alpha, 5000 + 100 * N + k)
+            phys = pt.sparsify(inst.Jq, "fixed", 3)
+            probs.append((inst, phys, synth.beta_ladder(16, BETA_MIN, BETA_MAX, inst.scale),
+                          synth.penalty_ladder(8, P_MIN, P_MAX, 32767), 777 + k))
+    return probs
+
+
+def _strip(out):
+    out = dict(out)
+    out.pop("per_problem_sweeps", None)
+    return out
+
+
+def leg_batched(pt, args, stream, dev):
+    """The uneven 1024-instance batch, batched vs one context per instance."""
+    t0 = time.perf_counter()
+    probs = batched_problems(args.instances)
+    gen_s = time.perf_counter() - t0
+    out = batched_vs_plain(pt, probs, 50, batched_events=args.batched_events,
+                           plain_events=args.plain_events, tts_events=args.tts_events,
+                           autotune=True, max_degree=3, stream=stream, dev=dev)
+    out = _strip(out)
+    out["workload"] = (f"{len(probs)} planted Wishart instances, N~U{{50..400}}, alpha in {{0.25,0.5,0.75}}, "
+                       "physical degree <= 4, I=16 x J=8, 1 run each, swap every 50 sweeps")
+    out["instance_generation_s"] = gen_s
+    out["tts"]["note"] = PROXY_NOTE
+    return out
+
+
+def leg_ground_state(pt, args, stream, dev):
+    """Time to the planted ground state, batched vs plain, where it is reached."""
+    probs = ground_state_problems(args.gs_ns, args.gs_instances)
+    degree = max(64, max(int(np.diff(p[1].cp_ptr).max()) for p in probs))
+    out = batched_vs_plain(pt, probs, 50, batched_events=args.gs_timed_events,
+                           plain_events=args.plain_events, tts_events=args.gs_events, autotune=False,
+                           max_degree=degree, stream=stream, dev=dev, chunk=100)
+    per = out["per_problem_sweeps"]["planted"]
+    out = _strip(out)
+    out["workload"] = (f"{len(probs)} planted Wishart instances (N in {list(args.gs_ns)}, alpha 0.75), "
+                       "three copies per node, I=16 x J=8, 1 run each, swap every 50 sweeps, "
+                       f"{args.gs_events * 50} sweeps")
+    out["planted_reached"] = int((per >= 0).sum())
+    out["tts"]["note"] = ("'planted': the bottom-right replica feasible (g = 0) with f <= E_planted, "
+                          "the planted ground state (or lower)")
+    return out
+
+
 def run_batched(args):
     """Uneven-batch workload: planted Wishart instances with N uniform on
     {50..400} and alpha in {0.25, 0.5, 0.75}, each copy-chain sparsified to
     physical degree <= 4, I = 16 x J = 8, one run each, swap interval 50.
     Times the batched persistent form against the one-instance-per-launch form
     on the same events (identical trajectories), then continues the batched
-    form to `--tts-events` events for time-to-planted-ground-state."""
+    form to `--tts-events` events for time to target."""
     if int(os.environ.get("RANK", "0")) != 0:
         return  # a one-GPU workload: under torchrun the other ranks do no work
     import torch
 
     import paper_2506_14781_gb300 as pt
-    import synth
 
-    interval, I, J = 50, 16, 8
-    t0 = time.perf_counter()
-    probs = []
-    for N, alpha, seed in synth.batch_specs(args.instances, 1000):
-        inst = synth.wishart_planted(N, alpha, seed)
-        phys = pt.sparsify(inst.Jq, "max_degree", 4)
-        probs.append((inst, phys, synth.beta_ladder(I, BETA_MIN, BETA_MAX, inst.scale),
-                      synth.penalty_ladder(J, P_MIN, P_MAX, 32767), seed))
-    gen_s = time.perf_counter() - t0
-    spins = sum(p[1].n for p in probs)
-    upd_per_event = spins * I * J * interval
     stream = torch.cuda.Stream()
+    dev = torch.cuda.current_device()
+    t0 = time.perf_counter()
+    probs = batched_problems(args.instances)
+    gen_s = time.perf_counter() - t0
     E = args.steps
-    probe = pt.Batch(1 << 22, 3, 8, stream=stream, trace_capacity=max(args.tts_events, E + 16))
-    need = sum(probe.instance_bytes(p[1], I, J, 1) for p in probs)
-    probe.close()
-    batch = pt.Batch(int(need * 1.02) + (64 << 20), 3, len(probs), stream=stream,
-                     trace_capacity=max(args.tts_events, E + 16))
-    ids = [batch.add(p[1], p[2], p[3], 1, p[4], p[0].E_planted) for p in probs]
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    tuned = None
-    done_events = 0
-    if args.autotune:
-        tuned = batch.autotune(1, interval)
-    batch.run(1, interval)
-    done_events = int(batch.read(ids[0], pt.COUNTERS)[1])  # trial launches advance the chains
-    ev0.record(stream)
-    batch.run(E, interval)
-    ev1.record(stream)
-    ev1.synchronize()
-    t_batched = ev0.elapsed_time(ev1) / 1e3
-    done_events += E
-    # one-instance-per-launch form: a context per instance, run one after the other
-    plain = None
-    if not args.no_plain:
-        ctxs = [pt.PT2D(p[1], p[2], p[3], 1, stream=stream, trace_capacity=1) for p in probs]
-        for c, p in zip(ctxs, probs):
-            c.run(interval, interval, p[4])
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for c, p in zip(ctxs, probs):
-            c.run(E * interval, interval, p[4])
-        ev1.record(stream)
-        ev1.synchronize()
-        t_plain = ev0.elapsed_time(ev1) / 1e3
-        launches = sum(c.launch_count for c in ctxs)
-        for c in ctxs:
-            c.close()
-        plain = {"seconds": t_plain, "updates_per_s": upd_per_event * E / t_plain,
-                 "launches_total": int(launches)}
-    # continue the batched form for time to planted ground state
-    t_tts = t_batched
-    chunk = 20
-    while done_events < args.tts_events:
-        k = min(chunk, args.tts_events - done_events)
-        ev0.record(stream)
-        batch.run(k, interval)
-        ev1.record(stream)
-        ev1.synchronize()
-        t_tts += ev0.elapsed_time(ev1) / 1e3
-        done_events += k
-    sec_per_event = t_batched / E
-    per_inst = {}
-    for i, p in zip(ids, probs):
-        r = residual_tts(batch.read(i, pt.TRACE_F), batch.read(i, pt.TRACE_G), done_events,
-                         p[0].E_planted, p[0].N, p[0].scale, interval)
-        for k, v in r.items():
-            per_inst.setdefault(k, []).append(int(v[0]))
-    per_inst = {k: np.array(v) for k, v in per_inst.items()}
+    out = batched_vs_plain(pt, probs, 50, batched_events=E, plain_events=args.plain_events,
+                           tts_events=args.tts_events, autotune=args.autotune, max_degree=3,
+                           stream=stream, dev=dev, plain=not args.no_plain)
     Ns = np.array([p[0].N for p in probs])
-    tts = {
-        "events_run": int(done_events), "sweeps_run": int(done_events * interval),
-        "targets_batched": tts_summary(per_inst, sec_per_event / interval),
-        "reached_by_N": {k: {f"{lo}-{lo + 49}": int((v[(Ns >= lo) & (Ns < lo + 50)] >= 0).sum())
-                             for lo in range(50, 401, 50)} for k, v in per_inst.items()},
-        "note": "trajectories are identical in both forms, so sweeps to target are the same; "
-                "seconds scale with each form's time per sweep",
-    }
-    if plain:
-        tts["targets_plain"] = tts_summary(per_inst, plain["seconds"] / E / interval)
+    per = out["per_problem_sweeps"]
+    out["tts"]["reached_by_N"] = {k: {f"{lo}-{lo + 49}": int((v[(Ns >= lo) & (Ns < lo + 50)] >= 0).sum())
+                                      for lo in range(50, 401, 50)} for k, v in per.items()}
+    out["tts"]["note"] = PROXY_NOTE
+    out = _strip(out)
+    t_b = out["batched"]["seconds"]
     line = {
         "metric": METRIC,
-        "value": upd_per_event * E / t_batched, "unit": UNIT, "n_gpus": 1, "steps": E,
-        "warmup": 1, "ms_per_step": t_batched / E * 1e3, "higher_is_better": True,
+        "value": out["batched"]["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": E,
+        "warmup": 1, "ms_per_step": t_b / E * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int8 spins, int32 fields, f32 decisions",
         "data": "synthetic (seeded planted Wishart instances)",
         "config": {"workload": f"{len(probs)} planted Wishart instances, N~U{{50..400}}, alpha in "
                                f"{{0.25,0.5,0.75}}, physical degree <= 4, I=16 x J=8, 1 run each, "
-                               f"swap every 50 sweeps", "physical_spins_total": int(spins),
+                               f"swap every 50 sweeps", "physical_spins_total": out["spins_total"],
                    "instance_generation_s": gen_s},
-        "batched": {"seconds": t_batched, "updates_per_s": upd_per_event * E / t_batched,
-                    "launches": 1, "shape": batch.shape, "autotuned": tuned is not None},
-        "plain": plain,
-        "speedup_batched_over_plain": (plain["seconds"] / t_batched) if plain else None,
-        "tts": tts,
+        **out,
     }
     peaks, peak_src = _peaks()
-    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    alu = upd_per_event * E / t_batched * OPS_PER_UPDATE / 1e12
+    alu = out["batched"]["updates_per_s"] * OPS_PER_UPDATE / 1e12
     line["roofline"] = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tops/s (lane-ops)",
                         "frac": alu / alu_peak, "traffic": None, "kernel": "k_batch",
                         "ops_per_update": OPS_PER_UPDATE,
@@ -1062,7 +1209,20 @@ def main():
     ap.add_argument("--max-requests", type=int, default=128, help="serving: most resident requests")
     ap.add_argument("--instances", type=int, default=1024)
     ap.add_argument("--runs", type=int, default=0, help="override the workload's run count")
-    ap.add_argument("--tts-events", type=int, default=400)
+    ap.add_argument("--tts-events", type=int, default=160,
+                    help="batched: events (of 50 sweeps) the batch runs for time to target")
+    ap.add_argument("--tts-sweeps", type=int, default=20000,
+                    help="default workload: sweeps the timed runs continue to for time to target")
+    ap.add_argument("--batched-events", type=int, default=4, help="batched leg: timed batched events")
+    ap.add_argument("--plain-events", type=int, default=2,
+                    help="batched legs: timed events of the one-context-per-instance form")
+    ap.add_argument("--gs-ns", type=int, nargs="+", default=[20])
+    ap.add_argument("--gs-instances", type=int, default=64)
+    ap.add_argument("--gs-events", type=int, default=2000)
+    ap.add_argument("--gs-timed-events", type=int, default=20)
+    ap.add_argument("--legs", default="all", choices=["all", "none"],
+                    help="default workload: also measure time to target, the batched vs plain forms "
+                         "and the ground-state leg (outside the timed region), or not")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()

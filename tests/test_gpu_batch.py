@@ -331,3 +331,32 @@ def test_runtime_degree_server_takes_penalty_requests(pt):
         assert np.array_equal(ctx.read(pt.BEST_STATE)[0], got["best_state"])
     ctx.close()
     srv.close()
+
+
+def test_runtime_degree_batch_penalty_problem_matches_oracle(pt):
+    """A problem with general penalty terms (one-hot groups, expanded by the
+    oracle's own code) in the runtime-degree batch, next to a three-copy
+    problem: the batch's record equals the oracle's for the same seed."""
+    from oracle.penalties import onehot
+
+    groups = [list(range(k, k + 5)) for k in range(0, 40, 5)]
+    pr = _penalty_problem(pt, 40, groups, 44, 8, 4)
+    other = _problem(pt, 45, 0.5, 42, ("fixed", 3), 16, 8, 1)
+    batch = pt.Batch(1 << 28, max_coupling_degree=64, max_runs=8, trace_capacity=16)
+    bid = batch.add(pr["phys"], pr["beta"], pr["P"], 1, pr["seed"], pr["target"])
+    batch.add(other["phys"], other["beta"], other["P"], 1, other["seed"], other["target"])
+    batch.run(6, 5)
+    ph = pr["phys"]
+    p2, c2, w2, k2, g2 = onehot(ph.n, groups)
+    phys_o = oracle.PhysInstance(ph.n, ph.cp_ptr, ph.cp_col, ph.cp_J, p2, c2, ph.h, ph.n,
+                                 np.arange(ph.n, dtype=np.int32), np.arange(ph.n + 1, dtype=np.int32),
+                                 lk_w=w2, hk=k2, g0=g2)
+    orc = oracle.OracleRun(oracle.OracleInstance(phys_o), pr["beta"], pr["P"], [0], pr["seed"], trace_cap=16,
+                           target=pr["target"])
+    orc.run(30, 5)
+    for w, attr in (("STATES", "spins"), ("WALKER_AT", "walker_at"), ("F", "f"), ("G", "g"),
+                    ("TRACE_F", "trace_f"), ("TRACE_G", "trace_g"), ("BEST_F", "best_f"),
+                    ("BEST_STATE", "best_state"), ("SOLVED_EVENT", "solved_event"), ("ACC_P", "acc_P"),
+                    ("ACC_B", "acc_B"), ("SUM_F", "sum_f"), ("SUM_G", "sum_g")):
+        assert np.array_equal(batch.read(bid, getattr(pt, w)), getattr(orc, attr)), w
+    batch.close()

@@ -564,50 +564,81 @@ def test_jcolumn_tiny_config_bit_exact(pt, tiny_config):
 
 
 # ---- full-size configurations, checked on samples the oracle computes -----------------
+def _bench_workload(key):
+    """The benchmark's own workload (instance, ladders, runs, swap interval)."""
+    import bench
+
+    return bench.make_workload(key)
+
+
+def _oracle_runs_in_threads(oinst, beta, P, run_ids, seed, sweeps, interval, **kw):
+    """One OracleRun per run id, run in parallel threads (the oracle's C code
+    releases the interpreter lock)."""
+    import threading
+
+    orcs = [oracle.OracleRun(oinst, beta, P, [r], seed, **kw) for r in run_ids]
+    ths = [threading.Thread(target=o.run, args=(sweeps, interval)) for o in orcs]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    return orcs
+
+
 def test_n200_full_size_sampled_runs(pt):
-    """N=200, alpha=0.5, <=3 edges per copy (13,400 spins), I=32 x J=8, 64 runs, in
-    the automatic launch configuration the benchmark uses; two runs checked in
-    full by the oracle after two events."""
-    inst = synth.wishart_planted(200, 0.5, 2)
+    """The benchmark's N=200 workload exactly as it is timed: planted Wishart
+    N=200, alpha=0.5, <=3 edges per copy (13,400 spins), I=32 x J=8 with the
+    benchmark's ladders (beta 0.1..5.0 / s, P 0.5..64 x 32767), 64 runs, swap
+    interval 50, in the benchmark's launch configuration (its own stream,
+    torch-allocated workspace, kernel timing on); two runs checked in full by
+    the oracle after two events (100 sweeps)."""
+    import torch
+
+    wl = _bench_workload("n200")
+    inst, beta, P, runs, interval = wl["inst"], wl["beta"], wl["P"], wl["runs"], wl["interval"]
+    assert (interval, runs, len(beta), len(P)) == (50, 64, 32, 8)
     phys_p = pt.sparsify(inst.Jq, "max_edges", 3)
-    assert phys_p.n == int(np.ceil(inst.degrees / 3).sum())
-    beta = synth.beta_ladder(32, 0.1, 2.0, inst.scale)
-    P = synth.penalty_ladder(8, 0.5, 4.0, 32767)
+    assert phys_p.n == 13400 == int(np.ceil(inst.degrees / 3).sum())
     seed = 100
-    ctx = pt.PT2D(phys_p, beta, P, 64, trace_capacity=8)
-    ctx.write(pt.TARGET, np.full(64, inst.E_planted))
-    ctx.run(20, 10, seed)
+    stream = torch.cuda.Stream()
+    ctx = pt.PT2D(phys_p, beta, P, runs, stream=stream, workspace="torch", trace_capacity=8,
+                  profile=True)
+    assert ctx.tiling["kernel"] == "smem"
+    ctx.write(pt.TARGET, np.full(runs, inst.E_planted))
+    with torch.cuda.stream(stream):
+        ctx.run(2 * interval, interval, seed)
     oinst = oracle.OracleInstance(oracle.sparsify(inst.Jq, "max_edges", 3))
-    for run_id in (0, 45):
-        orc = oracle.OracleRun(oinst, beta, P, [run_id], seed, trace_cap=8, target=inst.E_planted)
-        orc.run(20, 10)
+    orcs = _oracle_runs_in_threads(oinst, beta, P, (0, 45), seed, 2 * interval, interval, trace_cap=8,
+                                   target=inst.E_planted)
+    for run_id, orc in zip((0, 45), orcs):
         assert_same(pt, ctx, orc, runs_sel=[run_id])
+    ctx.close()
 
 
 def test_n800_full_size_sampled_walkers(pt):
-    """N=800 (213,600 spins), I=64 x J=16, 16 runs (3.5 GB of spins): after one
-    event, sampled walkers match the oracle spin for spin, their f and g match,
-    and the event's P-swap decisions match the oracle's swap event replayed on
-    the GPU's f and g."""
-    inst = synth.wishart_planted(800, 0.5, 3)
+    """The benchmark's N=800 workload as it is timed (213,551 spins, I=64 x
+    J=16, 16 runs, 3.5 GB of spins, the benchmark's ladders, one event of 50
+    sweeps): sampled walkers match the oracle spin for spin, their f and g
+    match, and the event's P-swap decisions match the oracle's swap event
+    replayed on the GPU's f and g."""
+    wl = _bench_workload("n800")
+    inst, beta, P, runs, interval = wl["inst"], wl["beta"], wl["P"], wl["runs"], wl["interval"]
+    assert (interval, runs, len(beta), len(P)) == (50, 16, 64, 16)
     phys_p = pt.sparsify(inst.Jq, "max_edges", 3)
     # ~3 edges per copy of ~799 neighbours (a few quantised couplings round to 0)
     assert phys_p.n == int(np.ceil(inst.degrees / 3).sum()) and phys_p.n > 213000
-    beta = synth.beta_ladder(64, 0.1, 2.0, inst.scale)
-    P = synth.penalty_ladder(16, 0.5, 4.0, 32767)
-    seed = 4242
-    runs = 16
-    ctx = pt.PT2D(phys_p, beta, P, runs, trace_capacity=4)
+    seed = 100
+    ctx = pt.PT2D(phys_p, beta, P, runs, trace_capacity=4, profile=True)
     # the automatic tiling holds this instance bit-packed in shared memory, 8 walkers a CTA
     assert ctx.tiling["kernel"] == "bits" and ctx.tiling["walkers_per_cta"] == 8
-    ctx.run(2, 2, seed)
+    ctx.run(interval, interval, seed)
     oinst = oracle.OracleInstance(oracle.sparsify(inst.Jq, "max_edges", 3))
     f_gpu = ctx.read(pt.F)
     g_gpu = ctx.read(pt.G)
     for run_id, w in ((0, 0), (3, 511), (3, 1023), (15, 777), (9, 14)):
         s = oinst.init_walker(seed, run_id, w)
         i, j = divmod(w, 16)  # walker w starts in slot w
-        for t in range(2):
+        for t in range(interval):
             oinst.sweep_walker(s, seed, run_id, w, t, beta[i], P[j])
         assert np.array_equal(ctx.read_walker(run_id, w), s), (run_id, w)
         assert f_gpu[run_id, w] == oinst.cost_f(s)
@@ -619,6 +650,58 @@ def test_n800_full_size_sampled_walkers(pt):
                                           np.arange(64 * 16), seed, run_id, 1, 1)
         assert np.array_equal(at_gpu[run_id], at)
         assert np.array_equal(acc_gpu[run_id], accP)
+    ctx.close()
+
+
+def _bench_ladder_pairs():
+    """(beta, H) pairs from the benchmark's ladders: betas of a few rows of the
+    N=200, N=800 and uneven-batch ladders, each with fields H that put the
+    heat-bath probability 1/(1 + exp(-beta H)) at several levels between
+    2^-23 and 1 - 2^-23 (where the decision turns on the uniform), within the
+    largest field the benchmark's instances produce, |H| <= 2 x 3 x 32767
+    (three couplings) + 2 x 64 x 32767 (two links at the largest penalty),
+    and that largest field itself."""
+    import bench
+
+    betas = []
+    for key in ("n200", "n800"):
+        wl = bench.make_workload(key)
+        b = wl["beta"]
+        betas += [b[k * (len(b) - 1) // 5] for k in range(6)]
+    inst = synth.wishart_planted(57, 0.25, 1001)
+    b = synth.beta_ladder(16, bench.BETA_MIN, bench.BETA_MAX, inst.scale)
+    betas += [b[0], b[-1]]
+    big = 2 * 3 * 32767 + 2 * 64 * 32767
+    pairs = set()
+    for k, beta in enumerate(betas):
+        beta = np.float32(beta)
+        for z in (-15.5, -5.1, -0.7, 2.3, 9.6):
+            H = int(np.clip(np.rint((z + 0.01 * k) / float(beta)), -big, big))
+            pairs.add((beta, H))
+    for beta in (betas[0], betas[4], betas[-2]):
+        pairs |= {(np.float32(beta), big), (np.float32(beta), -big)}
+    return sorted(pairs)
+
+
+def test_heatbath_fast_path_band_over_bench_ladders(pt):
+    """The hardware-exponential fast path decides only outside its error band
+    and defers to the exact single-precision contract inside it; over every
+    uniform of the 2^23-point grid, for (beta, H) pairs taken from the
+    benchmark's ladders, the decisions equal the oracle's one by one and their
+    count equals the oracle's exhaustive count."""
+    pairs = _bench_ladder_pairs()
+    assert len(pairs) >= 50
+    r = (np.arange(2**23, dtype=np.uint64) << np.uint64(9)).astype(np.uint32)
+    for beta, H in pairs:
+        assert abs(H) < 2**24
+        b = np.full(r.size, beta, np.float32)
+        h = np.full(r.size, H, np.int32)
+        got = pt.diag_heatbath(b, h, r)
+        exp = ocore.heatbath_array(b, h, r)
+        if not np.array_equal(got, exp):
+            bad = np.nonzero(got != exp)[0]
+            raise AssertionError(f"beta={beta!r} H={H}: {bad.size} uniforms differ, first {bad[:4]}")
+        assert int((got > 0).sum()) == oracle.heatbath_count(float(beta), H), (beta, H)
 
 
 def test_colouring_full_size_sampled_runs(pt):

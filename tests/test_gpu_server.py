@@ -34,7 +34,7 @@ def _requests(pt):
         phys = pt.sparsify(inst.Jq, "max_edges", 3)
         beta = synth.beta_ladder(8, 0.2, 3.0, inst.scale)
         P = synth.penalty_ladder(4, 0.5, 4.0, 32767)
-        out.append(dict(phys=phys, beta=beta, P=P, seed=9000 + k, target=inst.E_planted))
+        out.append(dict(phys=phys, beta=beta, P=P, seed=9000 + k, target=inst.E_planted, inst=inst))
     return out
 
 
@@ -134,4 +134,33 @@ def test_submit_rejects_what_can_never_run(pt):
     pen = pt.PhysicalInstance(6, np.zeros(7, np.int32), [], [], lk_ptr, lk_col, lk_w=lk_w, hk=hk, g0=g0)
     with pytest.raises(pt.Pt2dError):
         srv.submit(pen, small["beta"], small["P"], 1, 0, 40)
+    srv.close()
+
+
+def test_requests_in_a_mix_match_the_oracle(pt):
+    """Requests served in a mix (arrivals while others run, a pool that holds
+    only some of them) give the oracle's result for the same instance, ladders
+    and seed, run for the sweeps the server reports: best feasible f, the event
+    it was found at, the solving event and the best state."""
+    import oracle
+
+    reqs = _requests(pt)
+    probe = pt.Batch(1 << 24, 3, 8, trace_capacity=0)
+    sizes = [probe.instance_bytes(r["phys"], 8, 4, 1) for r in reqs]
+    probe.close()
+    srv = pt.Server(sum(sorted(sizes)[-3:]) + 4096, 3, 8, INTERVAL, EVENTS_PER_STEP)
+    ids = [srv.submit(r["phys"], r["beta"], r["P"], r["seed"], r["target"], MAX_SWEEPS) for r in reqs[:4]]
+    srv.step()
+    ids += [srv.submit(r["phys"], r["beta"], r["P"], r["seed"], r["target"], MAX_SWEEPS) for r in reqs[4:]]
+    _drain(srv, ids)
+    for k in (0, 3, 5):
+        r, got = reqs[k], srv.status(ids[k], with_state=True)
+        orc = oracle.OracleRun(oracle.OracleInstance(oracle.sparsify(r["inst"].Jq, "max_edges", 3)), r["beta"],
+                               r["P"], [0], r["seed"], target=r["target"])
+        orc.run(got["sweeps_done"], INTERVAL)
+        assert got["best_f"] == orc.best_f[0], k
+        assert got["best_event"] == orc.best_event[0], k
+        assert got["solved_event"] == orc.solved_event[0], k
+        if got["best_event"] >= 0:
+            assert np.array_equal(got["best_state"], orc.best_state[0]), k
     srv.close()
