@@ -822,6 +822,136 @@ def run_compare(args):
     print(json.dumps(line))
 
 
+def run_adaptive(args):
+    """Algorithm 2's adaptive ladders at length (the paper's ground-state
+    setting): planted Wishart instances, alpha = 0.75, three copies per node,
+    N in `--ad-ns` (100, 200), `--ad-instances` per N.  Per instance the
+    library's pt2d_adaptive_schedule builds the beta and P ladders (capped at
+    20 x 20; beta0 = 0.1 / s, P0 = 0.5 x 32767, alpha_beta = alpha_P =
+    2 erfc^-1(1/2) for swap rates near 1/2, populations of `--ad-chains`
+    chains x `--ad-mcs` sweeps, the row walk stopping at sigma_E <=
+    `--ad-sigma-min` couplings of 32767).  Then, on the same instances and
+    seeds, three arms run `--ad-events` events of 50 sweeps: 2D-PT on the
+    adaptive ladders, J-column PT on the same beta ladder at the mean of the
+    adaptive penalties, and 2D-PT on the fixed ladders of the other workloads
+    (I = 16 x J = 8).  Ladders of up to 400 replicas exceed the batch's 128 per
+    run, so each instance is one context; 16 run at a time on their own
+    streams.  Reported per N and arm: the median over instances of the residual
+    energy per spin of the best feasible bottom-right state so far, rho =
+    (f - E_gs) / (N s), against sweeps, and the instances reaching rho <= 0.1,
+    0.05 and 0 (E_gs: the planted energy or anything lower any arm found)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return  # a one-GPU workload
+    import concurrent.futures as cf
+
+    import torch
+    from scipy.special import erfcinv
+
+    import paper_2506_14781_gb300 as pt
+    import synth
+
+    interval, E, per_N = 50, args.ad_events, args.ad_instances
+    Ns = tuple(args.ad_ns)
+    probs = []
+    for N in Ns:
+        for k in range(per_N):
+            inst = synth.wishart_planted(N, 0.75, 7000 + 100 * N + k)
+            probs.append((inst, pt.sparsify(inst.Jq, "fixed", 3), 4242 + k))
+    alpha = float(2 * erfcinv(0.5))
+
+    def schedule(p):
+        inst, phys, seed = p
+        stream = torch.cuda.Stream()
+        t0 = time.perf_counter()
+        beta, P, samples = pt.adaptive_schedule(
+            phys, beta0=BETA_MIN / inst.scale, P0=int(P_MIN * 32767), max_rows=20, max_cols=20,
+            sigma_min=args.ad_sigma_min * 32767, alpha_beta=alpha, alpha_P=alpha, n_chain=args.ad_chains,
+            mcs=args.ad_mcs, seed=seed * 1000, stream=stream)
+        stream.synchronize()
+        return beta, P, samples, time.perf_counter() - t0
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(16) as ex:
+        ladders = list(ex.map(schedule, probs))
+    sched_s = time.perf_counter() - t0
+    arms = {
+        "2d_adaptive": [(b, P, "2d") for b, P, _, _ in ladders],
+        "jcolumn_adaptive": [(b, np.full(P.size, int(np.rint(P.mean())), np.int32), "jcolumn")
+                             for b, P, _, _ in ladders],
+        "2d_fixed": [(synth.beta_ladder(16, BETA_MIN, BETA_MAX, p[0].scale),
+                      synth.penalty_ladder(8, P_MIN, P_MAX, 32767), "2d") for p in probs],
+    }
+
+    def run_one(job):
+        (inst, phys, seed), (beta, P, mode) = job
+        stream = torch.cuda.Stream()
+        ctx = pt.PT2D(phys, beta, P, 1, stream=stream, trace_capacity=E, swap_mode=mode)
+        ctx.write(pt.TARGET, [inst.E_planted])
+        ctx.run(E * interval, interval, seed)
+        out = (ctx.read(pt.TRACE_F)[0], ctx.read(pt.TRACE_G)[0])
+        ctx.close()
+        return out
+
+    traces, arm_s = {}, {}
+    for arm, lad in arms.items():
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(16) as ex:
+            res = list(ex.map(run_one, zip(probs, lad)))
+        arm_s[arm] = time.perf_counter() - t0
+        traces[arm] = (np.stack([r[0] for r in res]), np.stack([r[1] for r in res]))
+    big = np.iinfo(np.int64).max
+    E_gs = np.array([min(int(p[0].E_planted),
+                         min(int(np.where(traces[a][1][k] == 0, traces[a][0][k], big).min()) for a in traces))
+                     for k, p in enumerate(probs)])
+    norm = np.array([p[0].N * p[0].scale for p in probs])
+    Narr = np.array([p[0].N for p in probs])
+    checkpoints = sorted({int(x) for x in np.unique(np.round(np.geomspace(1, E, 14)))})
+    results = {}
+    for arm, (tf, tg) in traces.items():
+        best = np.minimum.accumulate(np.where(tg == 0, tf, big), axis=1)
+        rho = np.where(best < big, (best - E_gs[:, None]) / norm[:, None], np.inf)
+        planted = np.minimum.accumulate(np.where(tg == 0, tf, big), axis=1) <= np.array(
+            [p[0].E_planted for p in probs])[:, None]
+        res = {"seconds": arm_s[arm], "feasible_record_fraction": float((tg == 0).mean())}
+        for N in Ns:
+            sel = Narr == N
+            curve = {str(c * interval): float(np.median(rho[sel, c - 1])) for c in checkpoints}
+            reach = {}
+            for target in (0.1, 0.05, 0.0):
+                hit = rho[sel] <= target + 1e-12
+                first = np.where(hit.any(1), hit.argmax(1) + 1, -1) * interval
+                reach[f"rho<={target}"] = {"reached": int((first > 0).sum()), "of": int(sel.sum()),
+                                           "median_sweeps": float(np.median(first[first > 0]))
+                                           if (first > 0).any() else None}
+            hitp = planted[sel]
+            firstp = np.where(hitp.any(1), hitp.argmax(1) + 1, -1) * interval
+            reach["planted"] = {"reached": int((firstp > 0).sum()), "of": int(sel.sum()),
+                                "median_sweeps": float(np.median(firstp[firstp > 0])) if (firstp > 0).any() else None}
+            res[str(N)] = {"median_rho_by_sweeps": curve, "sweeps_to_target": reach}
+        results[arm] = res
+    lad_stats = {}
+    for N in Ns:
+        sel = [k for k, p in enumerate(probs) if p[0].N == N]
+        Is = [ladders[k][0].size for k in sel]
+        Js = [ladders[k][1].size for k in sel]
+        lad_stats[str(N)] = {"I_median": float(np.median(Is)), "I_range": [int(min(Is)), int(max(Is))],
+                             "J_median": float(np.median(Js)), "J_range": [int(min(Js)), int(max(Js))],
+                             "beta_max_times_s_median": float(np.median([ladders[k][0][-1] * probs[k][0].scale
+                                                                         for k in sel])),
+                             "P_max_over_32767_median": float(np.median([ladders[k][1][-1] / 32767 for k in sel])),
+                             "samples_median": float(np.median([ladders[k][2] for k in sel]))}
+    line = {
+        "metric": "residual energy per spin vs sweeps on Algorithm 2's adaptive ladders",
+        "value": None, "unit": "rho", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+        "config": {"workload": f"{per_N} planted Wishart instances per N in {list(Ns)}, alpha 0.75, three "
+                               f"copies per node; adaptive ladders capped at 20 x 20 (populations of "
+                               f"{args.ad_chains} chains x {args.ad_mcs} sweeps, sigma_min = "
+                               f"{args.ad_sigma_min} x 32767); {E} events of {interval} sweeps per arm"},
+        "schedule_seconds": sched_s, "ladders": lad_stats, "results": results,
+    }
+    print(json.dumps(line))
+
+
 def run_fig2(args):
     """The paper's Fig. 2 experiment shape: a 5-node all-to-all instance with two
     copies per node (10 physical spins, physical degree 3), one row at beta = 1,
@@ -1092,7 +1222,11 @@ def run_serving(args):
     `--drain` seconds to finish what was admitted.  A request is a planted
     Wishart problem (N uniform on 50..800, alpha uniform on [0.25, 0.75], <= 3
     original edges per copy) with an I = 16 x J = 8 grid, run until its
-    bottom-right replica is feasible at the planted energy or 5 x 10^4 sweeps.
+    bottom-right replica is feasible at its target energy or 5 x 10^4 sweeps.
+    `--serve-stops` lists the targets, each a separate pass over every rate:
+    "planted" (f <= E_planted, the target the metric names) and "rho0.1" (f <=
+    E_planted + 0.1 N s, residual energy per spin <= 0.1, so that latency is
+    the time to that residual and solves/s counts the requests reaching it).
     At most `--max-requests` requests are resident (they share the GPU in one
     batched launch per step); the rest wait in FIFO order.  Problems are drawn
     from 256 pre-generated instances, each request with its own seed, so
@@ -1113,76 +1247,92 @@ def run_serving(args):
                      synth.penalty_ladder(8, P_MIN, P_MAX, 32767)))
     max_sweeps, interval = 50000, 50
     results = []
-    for rate in args.rates:
-        arrivals = synth.poisson_arrivals(rate, args.duration, 5 + int(rate))
-        rng = np.random.default_rng(int(rate))
-        picks = rng.integers(0, len(pool), arrivals.size)
-        srv = pt.Server(args.pool_gb << 30, 3, args.max_requests, interval, args.events_per_step)
-        ids = []
-        t0 = time.perf_counter()
-        nxt = 0
-        steps = 0
-        pool_bytes = args.pool_gb << 30
-        free0 = srv.free_bytes
-        peak_used, peak_active = 0, 0
-        while True:
-            now = time.perf_counter() - t0
-            while nxt < arrivals.size and arrivals[nxt] <= now:
-                inst, phys, beta, P = pool[picks[nxt]]
-                ids.append((srv.submit(phys, beta, P, 77 + nxt, inst.E_planted, max_sweeps), picks[nxt]))
-                nxt += 1
-            if now > args.duration + args.drain:
-                break
-            active, queued, _ = srv.step()
-            steps += 1
-            peak_active = max(peak_active, active)
-            peak_used = max(peak_used, free0 - srv.free_bytes)
-            if active == 0 and queued == 0:
-                if nxt >= arrivals.size:
-                    break
-                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
-        wall = time.perf_counter() - t0
-        lat, wait, service, rho, solved, done, updates = [], [], [], [], 0, 0, 0
-        for rid, k in ids:
-            st = srv.status(rid)
-            inst, phys = pool[k][0], pool[k][1]
-            if st["state"] == "done":
-                done += 1
-                lat.append(st["t_done"] - st["t_submit"])
-                wait.append(st["t_admit"] - st["t_submit"])
-                service.append(st["t_done"] - st["t_admit"])
-                solved += st["solved_event"] >= 0
-                updates += phys.n * 128 * st["sweeps_done"]
-                if st["best_event"] >= 0:
-                    rho.append((st["best_f"] - inst.E_planted) / (inst.N * inst.scale))
-        srv.close()
-
-        def pct(v, q):
-            return float(np.percentile(np.array(v), q)) if v else None
-
-        results.append({
-            "rate_per_min": rate, "submitted": len(ids), "completed": done, "solved": int(solved),
-            "unfinished_at_end": len(ids) - done, "wall_s": wall, "steps": steps,
-            "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
-            "p50_queue_wait_s": pct(wait, 50), "p50_service_s": pct(service, 50),
-            "solves_per_s": solved / wall, "completed_per_s": done / wall,
-            "spin_updates_per_s_completed": updates / wall,
-            "median_best_residual_per_spin": pct(rho, 50),
-            "resident_peak": int(peak_active), "memory_admitted_peak_bytes": int(peak_used),
-            "pool_bytes": int(pool_bytes),
-        })
+    for stop in args.serve_stops:
+        for rate in args.rates:
+            results.append(_serve_load(pt, synth, pool, stop, rate, max_sweeps, interval, args))
     line = {
         "metric": "serving p50/p99 latency and solves/sec", "value": results[0]["solves_per_s"],
         "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "Poisson stream of planted Wishart requests, N~U[50,800], "
                                "alpha~U[0.25,0.75], <=3 edges/copy, I=16 x J=8, stop at g=0 + "
-                               "planted energy or 5e4 sweeps", "duration_s": args.duration,
+                               "target energy or 5e4 sweeps", "duration_s": args.duration,
                    "drain_s": args.drain, "events_per_step": args.events_per_step,
                    "swap_interval": interval, "pool_gb": args.pool_gb,
-                   "max_resident": args.max_requests},
+                   "max_resident": args.max_requests, "stops": list(args.serve_stops)},
         "loads": results,
     }
     print(json.dumps(line))
+
+
+def _serve_load(pt, synth, pool, stop, rate, max_sweeps, interval, args):
+    """One offered load: Poisson arrivals for `duration` s, then drain."""
+    arrivals = synth.poisson_arrivals(rate, args.duration, 5 + int(rate))
+    rng = np.random.default_rng(int(rate))
+    picks = rng.integers(0, len(pool), arrivals.size)
+
+    def target(inst):
+        if stop == "planted":
+            return int(inst.E_planted)
+        return int(inst.E_planted) + int(np.floor(0.1 * inst.N * inst.scale))
+
+    srv = pt.Server(args.pool_gb << 30, 3, args.max_requests, interval, args.events_per_step)
+    ids = []
+    t0 = time.perf_counter()
+    nxt = 0
+    steps = 0
+    pool_bytes = args.pool_gb << 30
+    free0 = srv.free_bytes
+    peak_used, peak_active = 0, 0
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < arrivals.size and arrivals[nxt] <= now:
+            inst, phys, beta, P = pool[picks[nxt]]
+            ids.append((srv.submit(phys, beta, P, 77 + nxt, target(inst), max_sweeps), picks[nxt]))
+            nxt += 1
+        if now > args.duration + args.drain:
+            break
+        active, queued, _ = srv.step()
+        steps += 1
+        peak_active = max(peak_active, active)
+        peak_used = max(peak_used, free0 - srv.free_bytes)
+        if active == 0 and queued == 0:
+            if nxt >= arrivals.size:
+                break
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    lat, wait, service, rho, solved_lat, solved, done, updates = [], [], [], [], [], 0, 0, 0
+    for rid, k in ids:
+        st = srv.status(rid)
+        inst, phys = pool[k][0], pool[k][1]
+        if st["state"] == "done":
+            done += 1
+            lat.append(st["t_done"] - st["t_submit"])
+            wait.append(st["t_admit"] - st["t_submit"])
+            service.append(st["t_done"] - st["t_admit"])
+            if st["solved_event"] >= 0:
+                solved += 1
+                solved_lat.append(st["t_done"] - st["t_submit"])
+            updates += phys.n * 128 * st["sweeps_done"]
+            if st["best_event"] >= 0:
+                rho.append((st["best_f"] - inst.E_planted) / (inst.N * inst.scale))
+    srv.close()
+
+    def pct(v, q):
+        return float(np.percentile(np.array(v), q)) if v else None
+
+    return {
+        "stop": stop, "rate_per_min": rate, "submitted": len(ids), "completed": done, "solved": int(solved),
+        "unfinished_at_end": len(ids) - done, "wall_s": wall, "steps": steps,
+        "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
+        "p50_latency_solved_s": pct(solved_lat, 50), "p99_latency_solved_s": pct(solved_lat, 99),
+        "p50_queue_wait_s": pct(wait, 50), "p50_service_s": pct(service, 50),
+        "solves_per_s": solved / wall, "completed_per_s": done / wall,
+        "completed_per_min": 60.0 * done / wall,
+        "spin_updates_per_s_completed": updates / wall,
+        "median_best_residual_per_spin": pct(rho, 50),
+        "resident_peak": int(peak_active), "memory_admitted_peak_bytes": int(peak_used),
+        "pool_bytes": int(pool_bytes),
+    }
 
 
 def main():
@@ -1193,7 +1343,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=100, help="oracle sample, N=200 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2", "constrained", "membw", "threecopy"])
+    ap.add_argument("--workload", default="n200", choices=["n200", "n800", "batched", "serving", "compare", "fig2", "constrained", "membw", "threecopy", "adaptive"])
     ap.add_argument("--fig2-events", type=int, default=8000)
     ap.add_argument("--cmp-events", type=int, default=2000)
     ap.add_argument("--cmp-instances", type=int, default=64)
@@ -1202,6 +1352,7 @@ def main():
     ap.add_argument("--col-vertices", type=int, default=2000, help="constrained: vertices of the cubic graph")
     ap.add_argument("--threecopy-ns", type=int, nargs="+", default=[50, 100])
     ap.add_argument("--rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
+    ap.add_argument("--serve-stops", nargs="+", default=["planted", "rho0.1"], choices=["planted", "rho0.1"])
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--drain", type=float, default=30.0)
     ap.add_argument("--events-per-step", type=int, default=20)
@@ -1217,9 +1368,15 @@ def main():
     ap.add_argument("--plain-events", type=int, default=2,
                     help="batched legs: timed events of the one-context-per-instance form")
     ap.add_argument("--gs-ns", type=int, nargs="+", default=[20])
-    ap.add_argument("--gs-instances", type=int, default=64)
+    ap.add_argument("--gs-instances", type=int, default=256)
     ap.add_argument("--gs-events", type=int, default=2000)
     ap.add_argument("--gs-timed-events", type=int, default=20)
+    ap.add_argument("--ad-ns", type=int, nargs="+", default=[100, 200])
+    ap.add_argument("--ad-instances", type=int, default=64)
+    ap.add_argument("--ad-events", type=int, default=2000)
+    ap.add_argument("--ad-chains", type=int, default=64)
+    ap.add_argument("--ad-mcs", type=int, default=500)
+    ap.add_argument("--ad-sigma-min", type=float, default=1.0)
     ap.add_argument("--legs", default="all", choices=["all", "none"],
                     help="default workload: also measure time to target, the batched vs plain forms "
                          "and the ground-state leg (outside the timed region), or not")
@@ -1244,6 +1401,8 @@ def main():
         run_membw(args)
     elif args.workload == "threecopy":
         run_threecopy(args)
+    elif args.workload == "adaptive":
+        run_adaptive(args)
     else:
         run_gpu(args)
 
