@@ -117,6 +117,11 @@ __global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
     const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
     const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
     const uint32_t c3 = (run << 4) | kTagSweep;
+    // the thread's second quad (WPT = 8) starts the next run when a run holds
+    // an odd number of quads
+    const uint32_t run_b = static_cast<uint32_t>((quad + 1) / quads_per_run);
+    const uint32_t lqb = static_cast<uint32_t>(quad + 1 - static_cast<int64_t>(run_b) * quads_per_run);
+    const uint32_t c3b = (run_b << 4) | kTagSweep;
     const int lane_off = WPT * lane;
     const Quad qa = load_quad(wk, col0 + lane_off);
     const Quad qb = NQ == 2 ? load_quad(wk, col0 + lane_off + 4) : qa;
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
                 if (NQ == 1) {
                     *reinterpret_cast<uint32_t *>(dst) = update4<DC, DL>(rc, qa, fetch4, sweep, lq, c3, keys);
                 } else {
-                    *reinterpret_cast<uint2 *>(dst) = update8<DC, DL>(rc, qa, qb, fetch8, sweep, lq, c3, keys);
+                    *reinterpret_cast<uint2 *>(dst) = update8<DC, DL>(rc, qa, qb, fetch8, sweep, lq, c3, lqb, c3b, keys);
                 }
             }
             __syncthreads();

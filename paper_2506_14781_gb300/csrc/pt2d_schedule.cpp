@@ -21,7 +21,10 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/pt2d.h"
+#include "pt2d_trace.h"
 
 namespace {
 
@@ -125,6 +128,29 @@ extern "C" int pt2d_adaptive_schedule(const pt2d_instance *inst, const pt2d_sche
     }
     s.opt.trace_capacity = 0;
     s.opt.profile = 0;
+    // Every population sample is a 1 x 1 context of n_chain runs: one device
+    // workspace, allocated here and reused by each of them (a context on caller
+    // memory clears what it carves at creation), saves a cudaMalloc / cudaFree
+    // pair per sample.
+    struct Workspace {
+        void *p = nullptr;
+        ~Workspace() {
+            if (p) cudaFree(p);
+        }
+    } ws;
+    if (!s.opt.workspace) {
+        size_t need = 0;
+        if (int e = pt2d_workspace_size(inst, 1, 1, prm->n_chain, &s.opt, &need)) return e;
+        if (s.opt.device >= 0 && cudaSetDevice(s.opt.device) != cudaSuccess) return PT2D_ERR_UNSUPPORTED;
+        if (int e = pt2d::check_device()) return e;
+        if (pt2d::device_alloc(&ws.p, need) != cudaSuccess) {
+            cudaGetLastError();
+            ws.p = nullptr;
+            return PT2D_ERR_OOM;
+        }
+        s.opt.workspace = ws.p;
+        s.opt.workspace_bytes = need;
+    }
     s.f.resize(prm->n_chain);
     s.g.resize(prm->n_chain);
     s.E.resize(prm->n_chain);

@@ -167,11 +167,13 @@ __device__ __forceinline__ uint32_t update4(const Rec<DC, DL> &rc, const Quad &q
 }
 
 // Eight walkers (two quads) at one position: one 8-byte fetch per neighbour,
-// two independent Philox calls (quads lq and lq + 1).
+// two independent Philox calls (quad lq of run c3, and quad lqb of run c3b:
+// the next quad, which starts the next run when a run holds an odd number of
+// quads).
 template <int DC, int DL, typename Fetch8>
 __device__ __forceinline__ uint2 update8(const Rec<DC, DL> &rc, const Quad &qa, const Quad &qb,
                                          Fetch8 fetch8, uint32_t sweep, uint32_t lq, uint32_t c3,
-                                         const KeysConst &keys) {
+                                         uint32_t lqb, uint32_t c3b, const KeysConst &keys) {
     uint32_t xa[DC], ya[DL], xb[DC], yb[DL];
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
@@ -187,7 +189,7 @@ __device__ __forceinline__ uint2 update8(const Rec<DC, DL> &rc, const Quad &qa, 
     }
     const uint32_t id = static_cast<uint32_t>(rc.pid());
     const uint4 ra = keys(make_uint4(id, sweep, lq, c3));
-    const uint4 rb = keys(make_uint4(id, sweep, lq + 1, c3));
+    const uint4 rb = keys(make_uint4(id, sweep, lqb, c3b));
     return make_uint2(decide4<DC, DL>(rc, qa, xa, ya, ra), decide4<DC, DL>(rc, qb, xb, yb, rb));
 }
 

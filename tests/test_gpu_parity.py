@@ -200,6 +200,20 @@ def test_ragged_tiles_and_resume(pt, kernel, wpc, threads, wpt):
     assert_same(pt, ctx, orc)
 
 
+@pytest.mark.parametrize("wpc,threads", [(16, 64), (32, 128), (128, 512)])
+def test_eight_walkers_per_thread_across_runs(pt, wpc, threads):
+    """Eight walkers a thread with runs of 5 x 4 = 20 replicas (5 quads): a
+    thread's second quad starts the next run at every odd run boundary, and
+    must draw that run's random numbers."""
+    inst = synth.wishart_planted(24, 0.5, 33)
+    beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
+    P = synth.penalty_ladder(4, 0.5, 4.0, 32767)
+    ctx, orc = both(pt, inst, ("max_edges", 3), beta, P, 7, 4321, [(30, 6), (12, 6)],
+                    target=inst.E_planted, wpc=wpc, threads=threads, kernel="smem", wpt=8)
+    assert ctx.tiling["walkers_per_thread"] == 8
+    assert_same(pt, ctx, orc)
+
+
 @pytest.mark.parametrize("kernel,wpt", [("global", 0), ("smem", 4), ("smem", 8), ("bits", 0)])
 def test_degree_layouts_both_kernels(pt, kernel, wpt):
     """Specialised neighbour layouts DC = 4 and 6 (max-degree and fixed-copy
