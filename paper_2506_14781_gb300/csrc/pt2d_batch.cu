@@ -515,12 +515,11 @@ size_t batch_small_smem_bytes() {
 }
 
 cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state) {
-    const int smem = smem_state + static_cast<int>(batch_small_smem_bytes());
-    if (DL != 2) return cudaErrorInvalidValue;
-    if (DC == 0) return cudaFuncSetAttribute(k_batch<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (DC == 3) return cudaFuncSetAttribute(k_batch<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (DC == 4) return cudaFuncSetAttribute(k_batch<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (DC == 6) return cudaFuncSetAttribute(k_batch<6, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (smem_state < 0 || DL != 2) return cudaErrorInvalidValue;
+    if (DC == 0) return allow_max_dynamic_smem(k_batch<0, 0>);
+    if (DC == 3) return allow_max_dynamic_smem(k_batch<3, 2>);
+    if (DC == 4) return allow_max_dynamic_smem(k_batch<4, 2>);
+    if (DC == 6) return allow_max_dynamic_smem(k_batch<6, 2>);
     return cudaErrorInvalidValue;
 }
 

@@ -1,12 +1,39 @@
 // Internal interface between the C-ABI host layer and the CUDA kernels.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
 #include <cuda_runtime.h>
 
 namespace pt2d {
+
+// Raise a kernel's dynamic shared memory limit to the most the current device
+// allows next to the kernel's static shared memory, once per device.  The
+// limit belongs to the kernel and is shared by every host thread, so it is
+// never set to one launch's own size: contexts on other threads, whose slabs
+// differ in size, would lower it under each other's launches (which then fail
+// with cudaErrorInvalidValue).  Concurrent first calls set the same value.
+template <typename Kernel>
+cudaError_t allow_max_dynamic_smem(Kernel kernel) {
+    static std::atomic<uint64_t> done_mask{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (uint64_t{1} << dev) : 0;
+    if (bit && (done_mask.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - static_cast<int>(fa.sharedSizeBytes));
+    if (e == cudaSuccess && bit) done_mask.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // Device layout of one instance and its replica grid.
 //  * Spins: int8 S[n + 1][Wc], one row per spin in colour-sorted position

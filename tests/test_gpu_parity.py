@@ -778,3 +778,40 @@ def test_wide_records_without_links(pt, kernel):
     assert ctx.tiling["kernel"] == ("generic_smem" if kernel == "auto" else "generic")
     assert_same(pt, ctx, orc)
     assert np.all(ctx.read(pt.G) == 0)
+
+
+def test_contexts_on_concurrent_threads(pt):
+    """Contexts of different sizes (so different shared-memory slabs, on the
+    int8, bit-packed and runtime-degree kernels) run at the same time from
+    several host threads on their own streams; each gives the same result as
+    the same context run alone."""
+    import concurrent.futures as cf
+
+    import torch
+
+    jobs = []
+    for k, (N, rule) in enumerate([(30, ("max_edges", 3)), (60, ("max_edges", 3)), (24, ("fixed", 3)),
+                                   (45, ("fixed", 3)), (80, ("max_edges", 3)), (36, ("max_edges", 3))]):
+        inst = synth.wishart_planted(N, 0.5, 70 + k)
+        kern = "bits" if k == 5 else "auto"
+        jobs.append((pt.sparsify(inst.Jq, *rule), synth.beta_ladder(8, 0.2, 3.0, inst.scale),
+                     synth.penalty_ladder(4, 0.5, 4.0, 32767), 3 + k, 900 + k, kern))
+
+    def run(job, stream=None):
+        phys, beta, P, runs, seed, kern = job
+        ctx = pt.PT2D(phys, beta, P, runs, stream=stream, trace_capacity=8, sweep_kernel=kern,
+                      walkers_per_cta=8 if kern == "bits" else 0)
+        for _ in range(6):
+            ctx.run(20, 5, seed)
+        out = (ctx.read(pt.STATES), ctx.read(pt.F), ctx.read(pt.WALKER_AT), ctx.tiling["kernel"])
+        ctx.close()
+        return out
+
+    alone = [run(j) for j in jobs]
+    assert {a[3] for a in alone} >= {"smem", "bits", "generic_smem"}
+    with cf.ThreadPoolExecutor(len(jobs)) as ex:
+        for rep in range(3):
+            mixed = list(ex.map(lambda j: run(j, torch.cuda.Stream()), jobs))
+            for a, b in zip(alone, mixed):
+                for x, y in zip(a[:3], b[:3]):
+                    assert np.array_equal(x, y), rep
