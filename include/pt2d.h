@@ -124,8 +124,9 @@ typedef struct {
     int32_t trace_capacity;  /* events kept in the bottom-right trace (default 1024) */
     int32_t walkers_per_cta; /* sweep tiling: 4..128 (16..128 int8 in shared memory,
                                 8..128 bit-packed), power of two; 0 = automatic      */
-    int32_t threads_per_cta; /* multiple of 32, >= walkers_per_cta/4, <= 256 (global
-                                slab) or 1024 (shared slab); 0 = automatic          */
+    int32_t threads_per_cta; /* multiple of 32, >= walkers_per_cta/walkers_per_thread,
+                                <= 256 (global slab), 1024 (shared slab, 4 walkers
+                                a thread) or 512 (8 walkers a thread); 0 = automatic */
     int32_t device;          /* CUDA device ordinal; -1 = current device            */
     int32_t profile;         /* nonzero: time every kernel launch with CUDA events  */
     int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 int8 slab in
@@ -134,8 +135,10 @@ typedef struct {
                                 (specialised layouts and penalty terms with coupling
                                 degree <= 6 and link degree <= 3 only, else
                                 INVALID_ARG; 2, 3: INVALID_ARG if it does not fit)   */
-    int32_t walkers_per_thread; /* int8 shared-memory kernel: 4 or 8, others: 4;
-                                   0 = automatic                                     */
+    int32_t walkers_per_thread; /* int8 and bit-packed shared-memory kernels of the
+                                   specialised layouts: 4 or 8, others: 4; 0 =
+                                   automatic (bit-packed: 8, or 4 when more than
+                                   512 threads are asked for; int8: 4)             */
     int32_t swap_mode;       /* PT2D_SWAP_2D (0): Algorithm 1.  PT2D_SWAP_JCOLUMN (1):
                                 the paper's J-column PT baseline -- every event is a
                                 beta-swap event (pairs starting at the first row on

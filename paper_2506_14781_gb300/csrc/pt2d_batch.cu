@@ -516,10 +516,10 @@ size_t batch_small_smem_bytes() {
 
 cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state) {
     if (smem_state < 0 || DL != 2) return cudaErrorInvalidValue;
-    if (DC == 0) return allow_max_dynamic_smem(k_batch<0, 0>);
-    if (DC == 3) return allow_max_dynamic_smem(k_batch<3, 2>);
-    if (DC == 4) return allow_max_dynamic_smem(k_batch<4, 2>);
-    if (DC == 6) return allow_max_dynamic_smem(k_batch<6, 2>);
+    if (DC == 0) return allow_max_dynamic_smem<k_batch<0, 0>>();
+    if (DC == 3) return allow_max_dynamic_smem<k_batch<3, 2>>();
+    if (DC == 4) return allow_max_dynamic_smem<k_batch<4, 2>>();
+    if (DC == 6) return allow_max_dynamic_smem<k_batch<6, 2>>();
     return cudaErrorInvalidValue;
 }
 

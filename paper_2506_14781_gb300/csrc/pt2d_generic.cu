@@ -233,7 +233,7 @@ cudaError_t launch_generic_sweeps(const Layout &L, const Walkers &wk, const Swee
         while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
         if (shift < 4) return cudaErrorInvalidValue;
         const size_t smem = smem_sweep_bytes(L.n, 1 << shift);
-        cudaError_t e = allow_max_dynamic_smem(k_sweep_generic_smem);
+        cudaError_t e = allow_max_dynamic_smem<k_sweep_generic_smem>();
         if (e != cudaSuccess) return e;
         const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
         k_sweep_generic_smem<<<blocks, tl.threads, smem, st>>>(L, wk, shift, quads_per_run, rk, sweep0, nsweeps);

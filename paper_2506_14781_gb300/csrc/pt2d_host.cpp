@@ -311,15 +311,22 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     if (mode == 2 && sw == 0) return PT2D_ERR_INVALID_ARG;
     int ql, threads, wpt = 4;
     if (bw) {
-        if (opt && opt->walkers_per_thread != 0 && opt->walkers_per_thread != 4)
-            return PT2D_ERR_INVALID_ARG;
+        // a thread owns a byte of 8 walkers (k_sweep_bits8, up to 512 threads), or
+        // a nibble of 4 when asked for or when more threads are asked for
+        // (k_sweep_bits); the penalty-specialised bit-packed kernel takes nibbles
+        const int req_t = opt ? opt->walkers_per_thread : 0;
+        const int req_threads = opt ? opt->threads_per_cta : 0;
+        if (req_t != 0 && req_t != 4 && req_t != 8) return PT2D_ERR_INVALID_ARG;
+        if (req_t == 8 && !specialised) return PT2D_ERR_INVALID_ARG;
+        wpt = req_t ? req_t : (specialised && req_threads <= 512 ? 8 : 4);
         ql = bw / 4;
+        const int lanes = bw / wpt;  // threads per spin row
+        const int tmax = wpt == 4 ? 1024 : 512;
         int32_t widest = 0;
         for (int32_t c = 0; c < C; ++c) widest = std::max(widest, pp.cofs[c + 1] - pp.cofs[c]);
-        const int64_t want = (static_cast<int64_t>(widest) * ql + 31) / 32 * 32;
-        threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta
-                                                    : static_cast<int>(std::min<int64_t>(1024, want));
-        if (threads < 32 || threads > 1024 || threads % 32 || threads < ql) return PT2D_ERR_INVALID_ARG;
+        const int64_t want = (static_cast<int64_t>(widest) * lanes + 31) / 32 * 32;
+        threads = req_threads > 0 ? req_threads : static_cast<int>(std::min<int64_t>(tmax, want));
+        if (threads < 32 || threads > tmax || threads % 32 || threads < lanes) return PT2D_ERR_INVALID_ARG;
     } else
     if (sw) {
         ql = sw / 4;

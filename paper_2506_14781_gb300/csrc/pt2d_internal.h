@@ -15,8 +15,10 @@ namespace pt2d {
 // never set to one launch's own size: contexts on other threads, whose slabs
 // differ in size, would lower it under each other's launches (which then fail
 // with cudaErrorInvalidValue).  Concurrent first calls set the same value.
-template <typename Kernel>
-cudaError_t allow_max_dynamic_smem(Kernel kernel) {
+// The kernel is a template argument, so each kernel has its own record of the
+// devices it was set on.
+template <auto kernel>
+cudaError_t allow_max_dynamic_smem() {
     static std::atomic<uint64_t> done_mask{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -97,7 +99,7 @@ struct SweepTiling {
     int lanes_per_spin;  // quads (4 walkers) per spin row segment of a CTA
     int threads;         // threads per CTA
     bool smem;           // slab in shared memory (k_sweep_smem) or global (k_sweep_global)
-    int walkers_per_thread;  // 4, or 8 in the shared-memory kernel
+    int walkers_per_thread;  // 4, or 8 in the int8 and bit-packed shared-memory kernels
     bool bits;           // slab bit-packed in shared memory (k_sweep_bits)
 };
 

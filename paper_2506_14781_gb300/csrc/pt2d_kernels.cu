@@ -6,6 +6,9 @@
 //                    sweeps of every walker, colour class by colour class) with the
 //                    CTA's replica slab held in shared memory for the whole block, then
 //                    f and g of the final sweep (Eq. 1) as an epilogue
+//  k_sweep_bits8     the same with the slab bit-packed in shared memory (one bit per
+//                    walker), a thread owning a byte of 8 walkers (instances whose int8
+//                    slab does not fit); k_sweep_bits: a thread owning a nibble
 //  k_sweep_global    the same with the slab in global memory (instances whose slab does
 //                    not fit in shared memory)
 //  k_swap_event      one swap event per run: P-swaps (Eq. 2) or beta-swaps (Eq. 3) on
@@ -256,6 +259,88 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_bits(Layout L, Walkers wk, in
     energies<DC, DL, 1>(L, wk, fetch_q, own_q, 4 * lane_q, grp, G, SW, col0);
 }
 
+// Bit-packed slab with one byte (8 walkers, two quads) per thread: a 256-entry
+// table expands a byte to both quads' int8 spin words with one 8-byte shared
+// load, so no nibble shift and no pair shuffle; the byte is written whole.
+template <int DC, int DL>
+__global__ void __launch_bounds__(512, 1) k_sweep_bits8(Layout L, Walkers wk, int sw_shift,
+                                                        int32_t quads_per_run, RoundKeys rk,
+                                                        uint32_t sweep0, int32_t nsweeps) {
+    extern __shared__ __align__(16) uint8_t smb[];
+    const int SW = 1 << sw_shift;  // walkers per CTA, >= 8
+    const int B = SW >> 3;         // bytes per spin row = threads per row
+    const int lane_b = threadIdx.x & (B - 1);
+    const int grp = threadIdx.x >> (sw_shift - 3);
+    const int G = blockDim.x >> (sw_shift - 3);
+    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * SW;
+    const int64_t quad = col0 / 4 + 2 * lane_b;
+    const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
+    const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
+    const uint32_t c3 = (run << 4) | kTagSweep;
+    const uint32_t run_b = static_cast<uint32_t>((quad + 1) / quads_per_run);
+    const uint32_t lqb = static_cast<uint32_t>(quad + 1 - static_cast<int64_t>(run_b) * quads_per_run);
+    const uint32_t c3b = (run_b << 4) | kTagSweep;
+    const Quad qa = load_quad(wk, col0 + 8 * lane_b);
+    const Quad qb = load_quad(wk, col0 + 8 * lane_b + 4);
+    const KeysConst keys{rk};
+    const int n = L.n;
+    uint8_t *bits = smb;
+    uint2 *lut = reinterpret_cast<uint2 *>(smb + ((static_cast<int64_t>(n + 1) * B + 15) & ~15LL));
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = make_uint2(word_of_bits(i & 15), word_of_bits(i >> 4));
+    const int64_t nbytes = static_cast<int64_t>(n + 1) * B;
+    for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {
+        const int64_t row = i / B;
+        const int b = static_cast<int>(i - row * B);
+        const uint2 v = *reinterpret_cast<const uint2 *>(L.S + row * L.Wc + col0 + 8 * b);
+        bits[i] = static_cast<uint8_t>(bits_of_word(v.x) | (bits_of_word(v.y) << 4));
+    }
+    __syncthreads();
+    auto fetch8 = [&](int off) -> uint2 { return lut[bits[off + lane_b]]; };
+    const int pad = L.pad_ref;
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
+        for (int c = 0; c < L.C; ++c) {
+            const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                Rec<DC, DL> rc;
+                rc.load(L.rec, pos);
+                uint32_t xa[DC], xb[DC], ya[DL], yb[DL];
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const uint2 w = fetch8(rc.nb(k));
+                    xa[k] = w.x;
+                    xb[k] = w.y;
+                }
+#pragma unroll
+                for (int l = 0; l < DL; ++l) {
+                    const uint2 w = rc.lk(l) != pad ? fetch8(rc.lk(l)) : make_uint2(0u, 0u);
+                    ya[l] = w.x;
+                    yb[l] = w.y;
+                }
+                const uint32_t id = static_cast<uint32_t>(rc.pid());
+                const uint4 ra = keys(make_uint4(id, sweep, lq, c3));
+                const uint32_t na = bits_of_word(decide4<DC, DL>(rc, qa, xa, ya, ra));
+                const uint4 rb = keys(make_uint4(id, sweep, lqb, c3b));
+                const uint32_t nb = bits_of_word(decide4<DC, DL>(rc, qb, xb, yb, rb));
+                bits[pos * B + lane_b] = static_cast<uint8_t>(na | (nb << 4));
+            }
+            __syncthreads();
+        }
+    }
+    const int64_t nb_out = static_cast<int64_t>(n) * B;
+    for (int64_t i = threadIdx.x; i < nb_out; i += blockDim.x) {
+        const int64_t row = i / B;
+        const int b = static_cast<int>(i - row * B);
+        *reinterpret_cast<uint2 *>(L.S + row * L.Wc + col0 + 8 * b) = lut[bits[i]];
+    }
+    auto fetch_q = [&](int off, int h) -> uint32_t {
+        const uint2 w = fetch8(off);
+        return h ? w.y : w.x;
+    };
+    auto own_q = [&](int p, int h) -> uint32_t { return fetch_q(p * B, h); };
+    energies<DC, DL, 2>(L, wk, fetch_q, own_q, 8 * lane_b, grp, G, SW, col0);
+}
+
 // Sweep block with the slab in global memory.
 template <int DC, int DL>
 __global__ void __launch_bounds__(256) k_sweep_global(Layout L, Walkers wk, int ql_shift,
@@ -423,7 +508,7 @@ cudaError_t launch_smem_variant(const Layout &L, const Walkers &wk, const SweepT
     int shift = 0;
     while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
     const size_t smem = static_cast<size_t>(L.n + 1) << shift;
-    cudaError_t e = allow_max_dynamic_smem(k_sweep_smem<DC, DL, WPT>);
+    cudaError_t e = allow_max_dynamic_smem<k_sweep_smem<DC, DL, WPT>>();
     if (e != cudaSuccess) return e;
     const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
     k_sweep_smem<DC, DL, WPT><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
@@ -445,7 +530,14 @@ cudaError_t launch_bits_variant(const Layout &L, const Walkers &wk, const SweepT
     int shift = 0;
     while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
     const size_t smem = bits_sweep_bytes(L.n, 1 << shift);
-    cudaError_t e = allow_max_dynamic_smem(k_sweep_bits<DC, DL>);
+    if (tl.walkers_per_thread == 8) {
+        cudaError_t e = allow_max_dynamic_smem<k_sweep_bits8<DC, DL>>();
+        if (e != cudaSuccess) return e;
+        const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
+        k_sweep_bits8<DC, DL><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
+        return cudaGetLastError();
+    }
+    cudaError_t e = allow_max_dynamic_smem<k_sweep_bits<DC, DL>>();
     if (e != cudaSuccess) return e;
     const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
     k_sweep_bits<DC, DL><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
@@ -470,7 +562,9 @@ size_t smem_sweep_bytes(int32_t n, int walkers_per_cta) {
 }
 
 size_t bits_sweep_bytes(int32_t n, int walkers_per_cta) {
-    return ((static_cast<size_t>(n + 1) * (walkers_per_cta / 8) + 15) & ~static_cast<size_t>(15)) + 64;
+    // the slab, then the byte table of k_sweep_bits8 (256 x 8 bytes; k_sweep_bits
+    // uses the first 64 bytes as its nibble table)
+    return ((static_cast<size_t>(n + 1) * (walkers_per_cta / 8) + 15) & ~static_cast<size_t>(15)) + 2048;
 }
 
 // ---- launchers --------------------------------------------------------------

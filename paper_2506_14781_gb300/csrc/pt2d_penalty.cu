@@ -333,7 +333,7 @@ cudaError_t launch_bits_variant(const Layout &L, const Walkers &wk, const SweepT
     int shift = 0;
     while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
     const size_t smem = bits_sweep_bytes(L.n, 1 << shift);
-    cudaError_t e = allow_max_dynamic_smem(k_sweep_penalty_bits<DC, DL>);
+    cudaError_t e = allow_max_dynamic_smem<k_sweep_penalty_bits<DC, DL>>();
     if (e != cudaSuccess) return e;
     const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
     k_sweep_penalty_bits<DC, DL><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
@@ -346,7 +346,7 @@ cudaError_t launch_variant(const Layout &L, const Walkers &wk, const SweepTiling
     int shift = 0;
     while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
     const size_t smem = smem_sweep_bytes(L.n, 1 << shift);
-    cudaError_t e = allow_max_dynamic_smem(k_sweep_penalty_smem<DC, DL>);
+    cudaError_t e = allow_max_dynamic_smem<k_sweep_penalty_smem<DC, DL>>();
     if (e != cudaSuccess) return e;
     const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
     k_sweep_penalty_smem<DC, DL><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);

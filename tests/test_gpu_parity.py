@@ -186,7 +186,8 @@ def test_tiny_config_bit_exact_full_length(pt, tiny_config):
     ("global", 4, 32, 0), ("global", 16, 64, 0), ("global", 32, 256, 0), ("global", 128, 256, 0),
     ("smem", 16, 32, 4), ("smem", 32, 64, 4), ("smem", 64, 1024, 4), ("smem", 128, 128, 4),
     ("smem", 16, 64, 8), ("smem", 64, 512, 8), ("smem", 128, 32, 8), ("bits", 8, 32, 0),
-    ("bits", 16, 64, 0), ("bits", 64, 1024, 0), ("bits", 128, 96, 0), ("auto", 0, 0, 0)])
+    ("bits", 16, 64, 0), ("bits", 64, 1024, 0), ("bits", 128, 96, 0), ("bits", 8, 64, 4),
+    ("bits", 16, 64, 4), ("bits", 64, 512, 8), ("bits", 128, 512, 8), ("auto", 0, 0, 0)])
 def test_ragged_tiles_and_resume(pt, kernel, wpc, threads, wpt):
     inst = synth.wishart_planted(30, 0.5, 21)
     beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
@@ -200,8 +201,9 @@ def test_ragged_tiles_and_resume(pt, kernel, wpc, threads, wpt):
     assert_same(pt, ctx, orc)
 
 
-@pytest.mark.parametrize("wpc,threads", [(16, 64), (32, 128), (128, 512)])
-def test_eight_walkers_per_thread_across_runs(pt, wpc, threads):
+@pytest.mark.parametrize("kernel,wpc,threads", [("smem", 16, 64), ("smem", 32, 128), ("smem", 128, 512),
+                                                ("bits", 8, 64), ("bits", 16, 96), ("bits", 64, 512)])
+def test_eight_walkers_per_thread_across_runs(pt, kernel, wpc, threads):
     """Eight walkers a thread with runs of 5 x 4 = 20 replicas (5 quads): a
     thread's second quad starts the next run at every odd run boundary, and
     must draw that run's random numbers."""
@@ -209,12 +211,12 @@ def test_eight_walkers_per_thread_across_runs(pt, wpc, threads):
     beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
     P = synth.penalty_ladder(4, 0.5, 4.0, 32767)
     ctx, orc = both(pt, inst, ("max_edges", 3), beta, P, 7, 4321, [(30, 6), (12, 6)],
-                    target=inst.E_planted, wpc=wpc, threads=threads, kernel="smem", wpt=8)
-    assert ctx.tiling["walkers_per_thread"] == 8
+                    target=inst.E_planted, wpc=wpc, threads=threads, kernel=kernel, wpt=8)
+    assert ctx.tiling["walkers_per_thread"] == 8 and ctx.tiling["kernel"] == kernel
     assert_same(pt, ctx, orc)
 
 
-@pytest.mark.parametrize("kernel,wpt", [("global", 0), ("smem", 4), ("smem", 8), ("bits", 0)])
+@pytest.mark.parametrize("kernel,wpt", [("global", 0), ("smem", 4), ("smem", 8), ("bits", 0), ("bits", 4)])
 def test_degree_layouts_both_kernels(pt, kernel, wpt):
     """Specialised neighbour layouts DC = 4 and 6 (max-degree and fixed-copy
     sparsifications), on both sweep kernels."""
