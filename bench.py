@@ -92,6 +92,15 @@ def kernel_source_hash(kernel=None):
     return h.hexdigest()[:16]
 
 
+def sweep_kernel_name(tiling):
+    """Name of the sweep kernel a context's tiling selects."""
+    if tiling["kernel"] == "bits" and tiling.get("walkers_per_thread") == 8:
+        return "k_sweep_bits8"
+    return {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
+            "generic": "k_sweep_generic", "generic_smem": "k_sweep_generic_smem",
+            "penalty_smem": "k_sweep_penalty_smem", "penalty_bits": "k_sweep_penalty_bits"}[tiling["kernel"]]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -293,9 +302,7 @@ def run_gpu(args):
     hbm_achieved = algo_bytes / (avg_launch_ms / 1e3) / 1e9
     ops_per_update = OPS_PER_UPDATE
     tiling = ctx.tiling
-    kernel = {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
-              "generic": "k_sweep_generic", "generic_smem": "k_sweep_generic_smem",
-              "penalty_smem": "k_sweep_penalty_smem", "penalty_bits": "k_sweep_penalty_bits"}[tiling["kernel"]]
+    kernel = sweep_kernel_name(tiling)
     prof = PROFILED_TRAFFIC.get((args.workload, kernel))
     src_hash = kernel_source_hash(kernel)
     traffic = prof["dram_bytes_per_launch"] if prof and prof["src"] == src_hash else None
@@ -1080,9 +1087,7 @@ def run_constrained(args):
     value = updates_per_event * args.steps / (elapsed_ms / 1e3)
     avg_launch_ms = sweep_ms / max(launches, 1)
     tiling = ctx.tiling
-    kernel = {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
-              "generic": "k_sweep_generic", "generic_smem": "k_sweep_generic_smem",
-              "penalty_smem": "k_sweep_penalty_smem", "penalty_bits": "k_sweep_penalty_bits"}[tiling["kernel"]]
+    kernel = sweep_kernel_name(tiling)
     peaks, peak_src = _peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12

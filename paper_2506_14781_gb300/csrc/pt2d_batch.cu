@@ -358,6 +358,57 @@ __device__ __forceinline__ void int8_slab(const BatchArgs &a, const BatchRun &d,
     slab_energies<DC, DL>(d, rec, fetch, grp, G, lane_off, s_F, s_G);
 }
 
+// Beta and P of the current slots of walkers w0 .. w0 + 3 of a run (a quad).
+__device__ __forceinline__ Quad batch_quad(const uint8_t *pool, const BatchRun &d, int w0, bool inited) {
+    const float kNegL2E = -1.4426950408889634f;
+    float b[4];
+    int p[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int w = w0 + k;
+        if (inited) {
+            b[k] = reinterpret_cast<const float *>(pool + d.wparam)[w];
+            p[k] = reinterpret_cast<const int32_t *>(pool + d.wparam + 4 * d.Rp)[w];
+        } else {  // walker w starts in slot w
+            b[k] = w < d.R ? reinterpret_cast<const float *>(pool + d.beta)[w / d.J] : 0.0f;
+            p[k] = w < d.R ? reinterpret_cast<const int32_t *>(pool + d.P)[w % d.J] : 0;
+        }
+    }
+    return Quad{b[0], b[1], b[2], b[3], b[0] * kNegL2E, b[1] * kNegL2E, b[2] * kNegL2E,
+                b[3] * kNegL2E, p[0], p[1], p[2], p[3]};
+}
+
+// The end of one slab's event: f and g of its walkers (from s_F / s_G) to the
+// run's arrays, then the run's swap event when this slab is the last of its run
+// to finish (found with a fence and an atomic counter, so nothing waits).
+template <int DC, int DL>
+__device__ __forceinline__ void slab_finish(const BatchArgs &a, const BatchRun &d, const BatchItem it,
+                                            uint8_t *small, const long long *s_F, const int *s_G) {
+    uint8_t *pool = a.pool;
+    const int col0 = it.slab * d.sw;
+    __syncthreads();
+    {
+        int64_t *g_f = reinterpret_cast<int64_t *>(pool + d.fg);
+        int32_t *g_g = reinterpret_cast<int32_t *>(pool + d.fg + 8 * d.Rp);
+        for (int i = threadIdx.x; i < d.sw; i += blockDim.x) {
+            g_f[col0 + i] = -(s_F[i] / 4);
+            g_g[col0 + i] = s_G[i] / 2 + d.g0;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        const int done = atomicAdd(reinterpret_cast<int32_t *>(pool + d.counter), 1);
+        s_last = (done == d.nslab - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        run_swap<DC, DL>(a, d, it.run, small);
+    }
+}
+
 // One event of one slab: sweeps, f and g, and the run's swap when this slab is
 // the last of its run to finish.  The slab's spins are int8 in global memory
 // (mode 0), int8 in shared memory (mode 1) or bit-packed in shared memory
@@ -383,33 +434,14 @@ __device__ __forceinline__ void slab_event(const BatchArgs &a, const BatchItem i
     const int64_t sweeps_done = sc[kScSweeps];
     const uint32_t lq = static_cast<uint32_t>((col0 >> 2) + lane_q);
 
-    // this thread's four walkers: beta and P of their current slots
-    Quad q;
-    {
-        const float kNegL2E = -1.4426950408889634f;
-        float b[4];
-        int p[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int w = col0 + lane_off + k;
-            if (inited) {
-                b[k] = reinterpret_cast<const float *>(pool + d.wparam)[w];
-                p[k] = reinterpret_cast<const int32_t *>(pool + d.wparam + 4 * Rp)[w];
-            } else {  // walker w starts in slot w
-                b[k] = w < R ? reinterpret_cast<const float *>(pool + d.beta)[w / J] : 0.0f;
-                p[k] = w < R ? reinterpret_cast<const int32_t *>(pool + d.P)[w % J] : 0;
-            }
-        }
-        q = Quad{b[0], b[1], b[2], b[3], b[0] * kNegL2E, b[1] * kNegL2E, b[2] * kNegL2E,
-                 b[3] * kNegL2E, p[0], p[1], p[2], p[3]};
-    }
+    const Quad q = batch_quad(pool, d, col0 + lane_off, inited);  // this thread's four walkers
     uint8_t *small = dsm + a.smem_state;
     long long *s_F = reinterpret_cast<long long *>(small);
     int *s_G = reinterpret_cast<int *>(s_F + kMaxR);
     __shared__ uint4 s_keys[5];  // the run's Philox round keys, visible after the next barrier
     stage_round_keys(s_keys, d.k0, d.k1);
 
-    if (d.mode == 2) {
+    if (DC == 0 && d.mode == 2) {  // specialised records: bit-packed slabs go to k_batch_bits8
         const int B = SW >> 3;
         const int byte_lane = lane_q >> 1;
         const int nib_shift = (lane_q & 1) * 4;
@@ -464,27 +496,195 @@ __device__ __forceinline__ void slab_event(const BatchArgs &a, const BatchItem i
         int8_slab<DC, DL, false>(a, d, rec, cofs, q, S_g, col0, lane_off, grp, G, lq, inited, sweeps_done,
                                  s_keys, s_F, s_G);
     }
+    slab_finish<DC, DL>(a, d, it, small, s_F, s_G);
+}
+
+// One event of one bit-packed slab of a run with specialised records, one byte
+// (8 walkers, two quads) per thread: the scheme of k_sweep_bits8.  A 256-entry
+// table expands a byte to the two quads' int8 spin words with one 8-byte shared
+// load; each position's record and each neighbour byte serve 8 walkers.  Slabs
+// are >= 8 walkers and runs a power of two >= 8 wide, so a byte's two quads lie
+// in one run.
+template <int DC, int DL>
+__device__ __forceinline__ void slab_event_bits8(const BatchArgs &a, const BatchItem it, uint8_t *dsm) {
+    const BatchRun d = a.runs[it.run];
+    uint8_t *pool = a.pool;
+    const int n = d.n, Rp = d.Rp;
+    const int SW = d.sw;
+    const int B = SW >> 3;  // bytes per spin row = threads per row
+    const int lane_b = threadIdx.x & (B - 1);
+    const int grp = threadIdx.x / B;
+    const int G = blockDim.x / B;
+    const int col0 = it.slab * SW;
+    const int lane_off = 8 * lane_b;  // the thread's first walker within the slab
+    int8_t *S_g = reinterpret_cast<int8_t *>(pool + d.state);
+    const int4 *rec = reinterpret_cast<const int4 *>(pool + d.rec);
+    const int32_t *cofs = reinterpret_cast<const int32_t *>(pool + d.cofs);
+    const int64_t *sc = reinterpret_cast<const int64_t *>(pool + d.scalars);
+    const bool inited = sc[kScInited] != 0;
+    const int64_t sweeps_done = sc[kScSweeps];
+    const uint32_t lq = static_cast<uint32_t>((col0 >> 2) + 2 * lane_b);
+    const Quad qa = batch_quad(pool, d, col0 + lane_off, inited);
+    const Quad qb = batch_quad(pool, d, col0 + lane_off + 4, inited);
+    uint8_t *small = dsm + a.smem_state;
+    long long *s_F = reinterpret_cast<long long *>(small);
+    int *s_G = reinterpret_cast<int *>(s_F + kMaxR);
+    __shared__ uint4 s_keys[5];  // the run's Philox round keys, visible after the next barrier
+    stage_round_keys(s_keys, d.k0, d.k1);
+    uint8_t *bits = dsm;
+    uint2 *lut = reinterpret_cast<uint2 *>(dsm + ((static_cast<int64_t>(n + 1) * B + 15) & ~int64_t{15}));
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = make_uint2(word_of_bits(i & 15), word_of_bits(i >> 4));
+    const int64_t nbytes = static_cast<int64_t>(n + 1) * B;
+    for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {
+        const int pos = static_cast<int>(i / B);
+        const int b = static_cast<int>(i - static_cast<int64_t>(pos) * B);
+        uint32_t lo = 0, hi = 0;
+        if (pos == n) {
+        } else if (!inited) {
+            const uint32_t lq0 = static_cast<uint32_t>((col0 >> 2) + 2 * b);
+            lo = bits_of_word(init_word<DC, DL>(d, rec, pos, lq0));
+            hi = bits_of_word(init_word<DC, DL>(d, rec, pos, lq0 + 1));
+        } else {
+            const uint2 v = *reinterpret_cast<const uint2 *>(S_g + static_cast<int64_t>(pos) * Rp + col0 + 8 * b);
+            lo = bits_of_word(v.x);
+            hi = bits_of_word(v.y);
+        }
+        bits[i] = static_cast<uint8_t>(lo | (hi << 4));
+    }
     __syncthreads();
-    {
-        int64_t *g_f = reinterpret_cast<int64_t *>(pool + d.fg);
-        int32_t *g_g = reinterpret_cast<int32_t *>(pool + d.fg + 8 * Rp);
-        for (int i = threadIdx.x; i < SW; i += blockDim.x) {
-            g_f[col0 + i] = -(s_F[i] / 4);
-            g_g[col0 + i] = s_G[i] / 2 + d.g0;
+    // the run's round keys in per-thread registers (see slab_sweeps)
+    RoundKeys rk;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        uint32_t z;
+        asm volatile("mov.u32 %0, %%laneid;" : "=r"(z));
+        z &= ~31u;
+        uint4 kk = s_keys[r];
+        rk.k0[2 * r] = kk.x ^ z;
+        rk.k1[2 * r] = kk.y ^ z;
+        rk.k0[2 * r + 1] = kk.z ^ z;
+        rk.k1[2 * r + 1] = kk.w ^ z;
+    }
+    const KeysConst keys{rk};
+    const uint32_t c3 = (static_cast<uint32_t>(d.run) << 4) | kTagSweep;
+    auto fetch8 = [&](int row) -> uint2 { return lut[bits[row * B + lane_b]]; };
+    for (int t = 0; t < a.interval; ++t) {
+        const uint32_t sweep = static_cast<uint32_t>(sweeps_done + t);
+        for (int c = 0; c < d.C; ++c) {
+            const int beg = __ldg(cofs + c), end = __ldg(cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                Rec<DC, DL> rc;
+                rc.load(rec, pos);
+                uint32_t xa[DC], xb[DC], ya[DL], yb[DL];
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const uint2 w = fetch8(rc.nb(k));
+                    xa[k] = w.x;
+                    xb[k] = w.y;
+                }
+#pragma unroll
+                for (int l = 0; l < DL; ++l) {  // a missing link reads as no spin
+                    const uint2 w = rc.lk(l) != n ? fetch8(rc.lk(l)) : make_uint2(0u, 0u);
+                    ya[l] = w.x;
+                    yb[l] = w.y;
+                }
+                const uint32_t id = static_cast<uint32_t>(rc.pid());
+                const uint4 ra = keys(make_uint4(id, sweep, lq, c3));
+                const uint32_t na = bits_of_word(decide4<DC, DL>(rc, qa, xa, ya, ra));
+                const uint4 rb = keys(make_uint4(id, sweep, lq + 1, c3));
+                const uint32_t nb = bits_of_word(decide4<DC, DL>(rc, qb, xb, yb, rb));
+                bits[pos * B + lane_b] = static_cast<uint8_t>(na | (nb << 4));
+            }
+            __syncthreads();
         }
     }
-    // publish this slab; the CTA finishing the run's last slab does its swap event
-    __threadfence();
-    __syncthreads();
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-        const int done = atomicAdd(reinterpret_cast<int32_t *>(pool + d.counter), 1);
-        s_last = (done == d.nslab - 1) ? 1 : 0;
+    // rows 0..n-1 back as int8 spins
+    const int64_t nout = static_cast<int64_t>(n) * B;
+    for (int64_t i = threadIdx.x; i < nout; i += blockDim.x) {
+        const int64_t row = i / B;
+        const int b = static_cast<int>(i - row * B);
+        *reinterpret_cast<uint2 *>(S_g + row * Rp + col0 + 8 * b) = lut[bits[i]];
+    }
+    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+        s_F[i] = 0;
+        s_G[i] = 0;
     }
     __syncthreads();
-    if (s_last) {
-        __threadfence();
-        run_swap<DC, DL>(a, d, it.run, small);
+    // f and g of the final sweep for the thread's 8 walkers (Eq. 1), as in slab_energies
+    {
+        long long F[8];
+        int g[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            F[i] = 0;
+            g[i] = 0;
+        }
+        for (int pos = grp; pos < n; pos += G) {
+            Rec<DC, DL> rc;
+            rc.load(rec, pos);
+            const uint2 xs = fetch8(pos);
+            const int h4 = 2 * rc.h2();
+            int cs[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) cs[i] = h4;
+#pragma unroll
+            for (int k = 0; k < DC; ++k) {
+                const uint2 x = fetch8(rc.nb(k));
+                const int j2 = rc.j2(k);
+                cs[0] += j2 * sbyte<0>(x.x);
+                cs[1] += j2 * sbyte<1>(x.x);
+                cs[2] += j2 * sbyte<2>(x.x);
+                cs[3] += j2 * sbyte<3>(x.x);
+                cs[4] += j2 * sbyte<0>(x.y);
+                cs[5] += j2 * sbyte<1>(x.y);
+                cs[6] += j2 * sbyte<2>(x.y);
+                cs[7] += j2 * sbyte<3>(x.y);
+            }
+            F[0] += static_cast<long long>(sbyte<0>(xs.x)) * cs[0];
+            F[1] += static_cast<long long>(sbyte<1>(xs.x)) * cs[1];
+            F[2] += static_cast<long long>(sbyte<2>(xs.x)) * cs[2];
+            F[3] += static_cast<long long>(sbyte<3>(xs.x)) * cs[3];
+            F[4] += static_cast<long long>(sbyte<0>(xs.y)) * cs[4];
+            F[5] += static_cast<long long>(sbyte<1>(xs.y)) * cs[5];
+            F[6] += static_cast<long long>(sbyte<2>(xs.y)) * cs[6];
+            F[7] += static_cast<long long>(sbyte<3>(xs.y)) * cs[7];
+#pragma unroll
+            for (int l = 0; l < DL; ++l) {
+                if (rc.lk(l) == n) continue;  // padding link
+                const uint2 y = fetch8(rc.lk(l));
+                g[0] += sbyte<0>(xs.x) != sbyte<0>(y.x);
+                g[1] += sbyte<1>(xs.x) != sbyte<1>(y.x);
+                g[2] += sbyte<2>(xs.x) != sbyte<2>(y.x);
+                g[3] += sbyte<3>(xs.x) != sbyte<3>(y.x);
+                g[4] += sbyte<0>(xs.y) != sbyte<0>(y.y);
+                g[5] += sbyte<1>(xs.y) != sbyte<1>(y.y);
+                g[6] += sbyte<2>(xs.y) != sbyte<2>(y.y);
+                g[7] += sbyte<3>(xs.y) != sbyte<3>(y.y);
+            }
+        }
+        unsigned long long *uf = reinterpret_cast<unsigned long long *>(s_F);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            atomicAdd(uf + lane_off + i, static_cast<unsigned long long>(F[i]));
+            atomicAdd(s_G + lane_off + i, g[i]);
+        }
+    }
+    slab_finish<DC, DL>(a, d, it, small, s_F, s_G);
+}
+
+// Bit-packed slabs of runs with specialised records (one launch per event,
+// beside k_batch, which takes the int8 slabs).
+template <int DC, int DL>
+__global__ void __launch_bounds__(512, 1) k_batch_bits8(BatchArgs a) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.n_items) break;
+        slab_event_bits8<DC, DL>(a, a.items[item], dsm);
     }
 }
 
@@ -508,6 +708,14 @@ cudaError_t launch_batch_variant(const BatchArgs &a, int grid, int threads, size
     return cudaGetLastError();
 }
 
+template <int DC, int DL>
+cudaError_t launch_bits8_variant(const BatchArgs &a, int grid, int threads, size_t smem, cudaStream_t st) {
+    cudaError_t e = allow_max_dynamic_smem<k_batch_bits8<DC, DL>>();
+    if (e != cudaSuccess) return e;
+    k_batch_bits8<DC, DL><<<grid, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t batch_small_smem_bytes() {
@@ -520,6 +728,15 @@ cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state) {
     if (DC == 3) return allow_max_dynamic_smem<k_batch<3, 2>>();
     if (DC == 4) return allow_max_dynamic_smem<k_batch<4, 2>>();
     if (DC == 6) return allow_max_dynamic_smem<k_batch<6, 2>>();
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_bits8(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st) {
+    const size_t smem = static_cast<size_t>(a.smem_state) + batch_small_smem_bytes();
+    if (DL != 2) return cudaErrorInvalidValue;
+    if (DC == 3) return launch_bits8_variant<3, 2>(a, grid, threads, smem, st);
+    if (DC == 4) return launch_bits8_variant<4, 2>(a, grid, threads, smem, st);
+    if (DC == 6) return launch_bits8_variant<6, 2>(a, grid, threads, smem, st);
     return cudaErrorInvalidValue;
 }
 

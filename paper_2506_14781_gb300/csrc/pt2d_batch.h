@@ -70,13 +70,19 @@ struct BatchArgs {
 };
 
 size_t batch_small_smem_bytes();
-// Shared memory of a bit-packed slab: (n + 1) rows of sw / 8 bytes, then the nibble table.
+// Shared memory of a bit-packed slab: (n + 1) rows of sw / 8 bytes, then the
+// byte table of k_batch_bits8 (256 x 8 bytes; the runtime-degree kernel's
+// nibble table takes the first 64 of them).
 inline int64_t batch_bits_bytes(int32_t n, int32_t sw) {
-    return ((static_cast<int64_t>(n + 1) * (sw / 8) + 15) & ~int64_t{15}) + 64;
+    return ((static_cast<int64_t>(n + 1) * (sw / 8) + 15) & ~int64_t{15}) + 2048;
 }
 // DC = 0 selects the runtime-degree kernel (degrees and penalty terms read
 // from each run's descriptor).
 cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state);
 cudaError_t launch_batch(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
+// Bit-packed slabs of runs with specialised records (DC = 3, 4 or 6): k_batch_bits8,
+// at most 512 threads per CTA.
+cudaError_t launch_batch_bits8(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
+constexpr int kBatchBits8Threads = 512;
 
 }  // namespace pt2d

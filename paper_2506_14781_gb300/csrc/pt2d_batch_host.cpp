@@ -158,7 +158,8 @@ struct pt2d_batch {
     int32_t *d_queue = nullptr;
     int64_t *d_status = nullptr;                      // [max_runs][2]
     std::vector<std::pair<int64_t, int32_t>> order;  // run array order: (id, run)
-    int32_t n_items = 0;
+    int32_t n_items = 0;                              // slabs for k_batch (d_items[0 .. n_items))
+    int32_t n_items_bits8 = 0;                        // bit-packed slabs for k_batch_bits8, after them
     int glob_sw = 32;                                 // slab width when spins stay in global memory
     int swap_mode = 0;                                // PT2D_SWAP_2D or PT2D_SWAP_JCOLUMN, all problems
     bool generic = false;                             // runtime-degree kernel
@@ -285,12 +286,22 @@ int upload_descriptors(pt2d_batch *b) {
             item_work.push_back(static_cast<int64_t>(t.first.n) * t.first.sw);
         }
     }
-    // largest slabs first, so the event ends on small ones
+    // largest slabs first, so the event ends on small ones; with specialised
+    // records the bit-packed slabs form a second list (k_batch_bits8), after the
+    // int8 ones (k_batch)
     std::vector<size_t> perm(items.size());
     for (size_t k = 0; k < perm.size(); ++k) perm[k] = k;
-    std::stable_sort(perm.begin(), perm.end(), [&](size_t x, size_t y) { return item_work[x] > item_work[y]; });
+    auto bits8 = [&](size_t k) { return !b->generic && all[items[k].run].mode == 2; };
+    std::stable_sort(perm.begin(), perm.end(), [&](size_t x, size_t y) {
+        if (bits8(x) != bits8(y)) return !bits8(x);
+        return item_work[x] > item_work[y];
+    });
     std::vector<pt2d::BatchItem> sorted(items.size());
-    for (size_t k = 0; k < perm.size(); ++k) sorted[k] = items[perm[k]];
+    int32_t n_bits8 = 0;
+    for (size_t k = 0; k < perm.size(); ++k) {
+        sorted[k] = items[perm[k]];
+        n_bits8 += bits8(perm[k]) ? 1 : 0;
+    }
     items.swap(sorted);
     if (!all.empty()) {
         BK(b, cudaMemcpyAsync(b->d_runs, all.data(), sizeof(pt2d::BatchRun) * all.size(),
@@ -299,7 +310,8 @@ int upload_descriptors(pt2d_batch *b) {
                               cudaMemcpyHostToDevice, b->stream));
     }
     b->n_runs = static_cast<int32_t>(all.size());
-    b->n_items = static_cast<int32_t>(items.size());
+    b->n_items = static_cast<int32_t>(items.size()) - n_bits8;
+    b->n_items_bits8 = n_bits8;
     b->dirty = false;
     drop_graph(b);
     return PT2D_OK;
@@ -311,18 +323,31 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
         if (st) return st;
     }
     if (b->n_runs == 0 || events == 0) return PT2D_OK;
+    // k_batch takes the int8 slabs (all slabs of a runtime-degree batch),
+    // k_batch_bits8 the bit-packed slabs of specialised records; each has its
+    // own work counter
     pt2d::BatchArgs a{b->pool, b->d_runs, b->d_items, b->n_runs, b->n_items, b->d_queue, interval,
                       b->smem_state, b->d_status};
+    pt2d::BatchArgs a8{b->pool, b->d_runs, b->d_items + b->n_items, b->n_runs, b->n_items_bits8,
+                       b->d_queue + 1, interval, b->smem_state, b->d_status};
     const int grid = std::min(b->grid, b->n_items);
+    const int grid8 = std::min(b->grid, b->n_items_bits8);
+    const int threads8 = std::min(b->threads, pt2d::kBatchBits8Threads);
     const int kdc = b->generic ? 0 : b->DC;
-    BK(b, pt2d::batch_kernel_attributes(kdc, 2, b->smem_state));
-    // one launch per event: the counter is cleared, then every slab of every run
+    if (grid > 0) BK(b, pt2d::batch_kernel_attributes(kdc, 2, b->smem_state));
+    // per event: the counters are cleared, then every slab of every run
     auto enqueue = [&]() -> cudaError_t {
         for (int32_t e = 0; e < events; ++e) {
-            cudaError_t x = cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), b->stream);
+            cudaError_t x = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int32_t), b->stream);
             if (x != cudaSuccess) return x;
-            x = pt2d::launch_batch(a, kdc, 2, grid, b->threads, b->stream);
-            if (x != cudaSuccess) return x;
+            if (grid8 > 0) {
+                x = pt2d::launch_batch_bits8(a8, kdc, 2, grid8, threads8, b->stream);
+                if (x != cudaSuccess) return x;
+            }
+            if (grid > 0) {
+                x = pt2d::launch_batch(a, kdc, 2, grid, b->threads, b->stream);
+                if (x != cudaSuccess) return x;
+            }
         }
         return cudaSuccess;
     };
@@ -347,7 +372,7 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
         }
         BK(b, cudaGraphLaunch(b->graph, b->stream));
     }
-    b->launches += events;
+    b->launches += static_cast<int64_t>(events) * ((grid > 0 ? 1 : 0) + (grid8 > 0 ? 1 : 0));
     return PT2D_OK;
 }
 
