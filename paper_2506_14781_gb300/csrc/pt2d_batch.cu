@@ -15,6 +15,7 @@
 // seed and run index.  Events are chained by replaying launches from a CUDA
 // graph.
 #include <cstdint>
+#include <type_traits>
 
 #include "pt2d_batch.h"
 #include "pt2d_device.cuh"
@@ -126,33 +127,30 @@ __device__ void run_swap(const BatchArgs &a, const BatchRun &d, int run_index, u
 // __syncthreads).  fetch(row) / fetch_link(row) give the quad's spin word of a
 // neighbour / copy-link row, store(pos, word) writes the new word.
 //
-// The run's ten Philox round keys are read from shared memory once and held in
-// per-thread registers for the whole block: a shared load per round and update
-// costs ~9 % on bit-packed slabs, and keys the compiler can see to be
-// warp-uniform go to uniform registers at a further ~3 %.  XOR with
-// (laneid & ~31), which is zero, hides that uniformity.
+// Where the run's ten Philox round keys live: the int8 slabs of specialised
+// records hold them in per-thread registers for the whole block (1 % faster than
+// reading them from shared memory at every use, which costs 3 %); the
+// runtime-degree kernel, whose wide records already need more registers than
+// its 1024 threads allow (it spilled), reads them from shared memory, two
+// rounds per 16-byte load (22 % faster than holding them).
 template <int DC, int DL, typename Fetch, typename FetchLink, typename Store>
 __device__ __forceinline__ void slab_sweeps(const BatchArgs &a, const BatchRun &d, const int4 *rec,
                                             const int32_t *cofs, const Quad &q, Fetch fetch,
                                             FetchLink fetch_link, Store store, int grp, int G,
                                             uint32_t lq, int64_t sweeps_done, const uint4 *round_keys) {
     RoundKeys rk;
+    if constexpr (DC != 0) {
 #pragma unroll
-    for (int r = 0; r < 5; ++r) {
-        uint32_t z;
-        asm volatile("mov.u32 %0, %%laneid;" : "=r"(z));
-        z &= ~31u;
-        uint4 kk = round_keys[r];
-        kk.x ^= z;
-        kk.y ^= z;
-        kk.z ^= z;
-        kk.w ^= z;
-        rk.k0[2 * r] = kk.x;
-        rk.k1[2 * r] = kk.y;
-        rk.k0[2 * r + 1] = kk.z;
-        rk.k1[2 * r + 1] = kk.w;
+        for (int r = 0; r < 5; ++r) {
+            const uint4 kk = round_keys[r];
+            rk.k0[2 * r] = kk.x;
+            rk.k1[2 * r] = kk.y;
+            rk.k0[2 * r + 1] = kk.z;
+            rk.k1[2 * r + 1] = kk.w;
+        }
     }
-    const KeysConst keys{rk};
+    using Keys = std::conditional_t<DC == 0, KeysShared, KeysConst>;
+    const Keys keys = make_keys<Keys>(rk, round_keys);
     const uint32_t c3 = (static_cast<uint32_t>(d.run) << 4) | kTagSweep;
     for (int t = 0; t < a.interval; ++t) {
         const uint32_t sweep = static_cast<uint32_t>(sweeps_done + t);

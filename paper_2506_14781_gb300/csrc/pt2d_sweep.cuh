@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "pt2d_device.cuh"
 #include "pt2d_internal.h"
@@ -18,6 +19,28 @@ struct KeysConst {
     RoundKeys rk;
     __device__ __forceinline__ uint4 operator()(uint4 x) const { return philox4x32_10(x, rk); }
 };
+// Round keys read from shared memory at every use, two rounds per 16-byte load
+// (a run's keys staged by stage_round_keys).
+struct KeysShared {
+    const uint4 *rk;
+    __device__ __forceinline__ uint4 operator()(uint4 x) const {
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            const uint4 kk = rk[r];
+            x = philox_round(x, kk.x, kk.y);
+            x = philox_round(x, kk.z, kk.w);
+        }
+        return x;
+    }
+};
+template <typename Keys>
+__device__ __forceinline__ Keys make_keys(const RoundKeys &rk, const uint4 *staged) {
+    if constexpr (std::is_same_v<Keys, KeysShared>) {
+        return KeysShared{staged};
+    } else {
+        return KeysConst{rk};
+    }
+}
 // A run's round keys staged in shared memory, two rounds per 16-byte word:
 // dst[r] = (k0 of round 2r, k1 of round 2r, k0 of round 2r+1, k1 of round 2r+1).
 __device__ __forceinline__ void stage_round_keys(uint4 *dst, uint32_t k0, uint32_t k1) {
