@@ -79,7 +79,8 @@ PROFILED_TRAFFIC = {
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h", "pt2d_wide.cuh")
 # kernels defined outside pt2d_kernels.cu hash their own file as well
-KERNEL_EXTRA_SOURCES = {"k_sweep_penalty_smem": ("pt2d_penalty.cu",), "k_sweep_penalty_bits": ("pt2d_penalty.cu",)}
+KERNEL_EXTRA_SOURCES = {"k_sweep_penalty_smem": ("pt2d_penalty.cu",), "k_sweep_penalty_bits": ("pt2d_penalty.cu",),
+                        "k_sweep_penalty_bits8": ("pt2d_penalty.cu",)}
 
 
 def kernel_source_hash(kernel=None):
@@ -94,8 +95,8 @@ def kernel_source_hash(kernel=None):
 
 def sweep_kernel_name(tiling):
     """Name of the sweep kernel a context's tiling selects."""
-    if tiling["kernel"] == "bits" and tiling.get("walkers_per_thread") == 8:
-        return "k_sweep_bits8"
+    if tiling["kernel"] in ("bits", "penalty_bits") and tiling.get("walkers_per_thread") == 8:
+        return "k_sweep_bits8" if tiling["kernel"] == "bits" else "k_sweep_penalty_bits8"
     return {"smem": "k_sweep_smem", "bits": "k_sweep_bits", "global": "k_sweep_global",
             "generic": "k_sweep_generic", "generic_smem": "k_sweep_generic_smem",
             "penalty_smem": "k_sweep_penalty_smem", "penalty_bits": "k_sweep_penalty_bits"}[tiling["kernel"]]

@@ -135,10 +135,11 @@ typedef struct {
                                 (specialised layouts and penalty terms with coupling
                                 degree <= 6 and link degree <= 3 only, else
                                 INVALID_ARG; 2, 3: INVALID_ARG if it does not fit)   */
-    int32_t walkers_per_thread; /* int8 and bit-packed shared-memory kernels of the
-                                   specialised layouts: 4 or 8, others: 4; 0 =
-                                   automatic (bit-packed: 8, or 4 when more than
-                                   512 threads are asked for; int8: 4)             */
+    int32_t walkers_per_thread; /* 4 or 8 for the int8 shared-memory kernel of the
+                                   specialised layouts and for the bit-packed
+                                   kernels, others: 4; 0 = automatic (bit-packed:
+                                   8, or 4 when more than 512 threads are asked
+                                   for; int8: 4)                                   */
     int32_t swap_mode;       /* PT2D_SWAP_2D (0): Algorithm 1.  PT2D_SWAP_JCOLUMN (1):
                                 the paper's J-column PT baseline -- every event is a
                                 beta-swap event (pairs starting at the first row on

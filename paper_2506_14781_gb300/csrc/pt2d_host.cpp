@@ -311,14 +311,13 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     if (mode == 2 && sw == 0) return PT2D_ERR_INVALID_ARG;
     int ql, threads, wpt = 4;
     if (bw) {
-        // a thread owns a byte of 8 walkers (k_sweep_bits8, up to 512 threads), or
-        // a nibble of 4 when asked for or when more threads are asked for
-        // (k_sweep_bits); the penalty-specialised bit-packed kernel takes nibbles
+        // a thread owns a byte of 8 walkers (k_sweep_bits8 / k_sweep_penalty_bits8,
+        // up to 512 threads), or a nibble of 4 when asked for or when more threads
+        // are asked for (k_sweep_bits / k_sweep_penalty_bits)
         const int req_t = opt ? opt->walkers_per_thread : 0;
         const int req_threads = opt ? opt->threads_per_cta : 0;
         if (req_t != 0 && req_t != 4 && req_t != 8) return PT2D_ERR_INVALID_ARG;
-        if (req_t == 8 && !specialised) return PT2D_ERR_INVALID_ARG;
-        wpt = req_t ? req_t : (specialised && req_threads <= 512 ? 8 : 4);
+        wpt = req_t ? req_t : (req_threads <= 512 ? 8 : 4);
         ql = bw / 4;
         const int lanes = bw / wpt;  // threads per spin row
         const int tmax = wpt == 4 ? 1024 : 512;
@@ -360,7 +359,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     pp.tiling.smem = sw != 0;
     pp.tiling.bits = bw != 0;
     pp.tiling.walkers_per_thread = wpt;
-    pp.pen_kernel = pen_ok && (sw != 0 || bw != 0) && wpt == 4;
+    pp.pen_kernel = pen_ok && ((sw != 0 && wpt == 4) || bw != 0);
     if (pp.pen_kernel) {
         // padded up to a layout of the penalty-specialised kernel (padding
         // entries point at the zero row with J = 0, K = 0)

@@ -7,11 +7,12 @@
 //      reading the penalty record layout [nb x DC, lk x DL, pid, 2h,
 //      2J x DC, K x DL, k] with compile-time offsets (16-byte loads, unrolled
 //      neighbour loops), then f and g of the final sweep.
-//  k_sweep_penalty_bits<DC, DL>  the same with the slab bit-packed in shared
-//      memory (instances whose int8 slab does not fit), as k_sweep_bits:
-//      one bit per walker, a 16-entry table expands a thread's nibble to four
-//      int8 spins, padding links (a bit cannot hold the zero row's 0) are
-//      skipped by predicate.
+//  k_sweep_penalty_bits8<DC, DL>  the same with the slab bit-packed in shared
+//      memory (instances whose int8 slab does not fit), as k_sweep_bits8:
+//      one bit per walker, a thread owning a byte of 8 walkers that a
+//      256-entry table expands to int8 spins; padding links (a bit cannot hold
+//      the zero row's 0) are skipped by predicate.  k_sweep_penalty_bits: the
+//      same with a nibble of 4 walkers per thread, as k_sweep_bits.
 //
 // The heat-bath field of spin a is H_a = 2 sum_b J_ab s_b + 2h_a +
 // P (sum_l K_al s_l + k_a); padding neighbours and links point at the slab's
@@ -327,12 +328,180 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_penalty_bits(Layout L, Walker
     }
 }
 
+// The same with one byte (8 walkers, two quads) per thread, as k_sweep_bits8: a
+// 256-entry table expands a byte to both quads' int8 spin words with one 8-byte
+// shared load; the byte is written whole (no shuffle).
+template <int DC, int DL>
+__global__ void __launch_bounds__(512, 1) k_sweep_penalty_bits8(Layout L, Walkers wk, int sw_shift,
+                                                                int32_t quads_per_run, RoundKeys rk,
+                                                                uint32_t sweep0, int32_t nsweeps) {
+    extern __shared__ __align__(16) uint8_t spb[];
+    const int SW = 1 << sw_shift;  // walkers per CTA, >= 8
+    const int B = SW >> 3;         // bytes per spin row = threads per row
+    const int lane_b = threadIdx.x & (B - 1);
+    const int grp = threadIdx.x >> (sw_shift - 3);
+    const int G = blockDim.x >> (sw_shift - 3);
+    const int64_t col0 = static_cast<int64_t>(blockIdx.x) * SW;
+    const int64_t quad = col0 / 4 + 2 * lane_b;
+    const uint32_t run = static_cast<uint32_t>(quad / quads_per_run);
+    const uint32_t lq = static_cast<uint32_t>(quad - static_cast<int64_t>(run) * quads_per_run);
+    const uint32_t c3 = (run << 4) | kTagSweep;
+    // the second quad starts the next run when a run holds an odd number of quads
+    const uint32_t run_b = static_cast<uint32_t>((quad + 1) / quads_per_run);
+    const uint32_t lqb = static_cast<uint32_t>(quad + 1 - static_cast<int64_t>(run_b) * quads_per_run);
+    const uint32_t c3b = (run_b << 4) | kTagSweep;
+    const Quad qa = load_quad(wk, col0 + 8 * lane_b);
+    const Quad qb = load_quad(wk, col0 + 8 * lane_b + 4);
+    const KeysConst keys{rk};
+    const int n = L.n;
+    uint8_t *bits = spb;
+    uint2 *lut = reinterpret_cast<uint2 *>(spb + ((static_cast<int64_t>(n + 1) * B + 15) & ~15LL));
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = make_uint2(word_of_bits(i & 15), word_of_bits(i >> 4));
+    const int64_t nbytes = static_cast<int64_t>(n + 1) * B;
+    for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {
+        const int64_t row = i / B;
+        const int b = static_cast<int>(i - row * B);
+        const uint2 v = *reinterpret_cast<const uint2 *>(L.S + row * L.Wc + col0 + 8 * b);
+        bits[i] = static_cast<uint8_t>(bits_of_word(v.x) | (bits_of_word(v.y) << 4));
+    }
+    __syncthreads();
+
+    auto fetch8 = [&](int off) -> uint2 { return lut[bits[off + lane_b]]; };
+    // fields of one quad (walkers of word x / y) at one position, the decision, four bits
+    auto quad_bits = [&](const PenRec<DC, DL> &rc, const Quad &q, const uint32_t *x, const uint32_t *y,
+                         const uint4 &r) -> uint32_t {
+        int a0 = rc.h2(), a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) {
+            const int j = rc.j2(k);
+            a0 += j * sbyte<0>(x[k]);
+            a1 += j * sbyte<1>(x[k]);
+            a2 += j * sbyte<2>(x[k]);
+            a3 += j * sbyte<3>(x[k]);
+        }
+        int l0 = rc.kk(), l1 = l0, l2 = l0, l3 = l0;
+#pragma unroll
+        for (int l = 0; l < DL; ++l) {
+            const int w = rc.w(l);
+            l0 += w * sbyte<0>(y[l]);
+            l1 += w * sbyte<1>(y[l]);
+            l2 += w * sbyte<2>(y[l]);
+            l3 += w * sbyte<3>(y[l]);
+        }
+        return bits_of_word(
+            decide_fields(q, a0 + q.p0 * l0, a1 + q.p1 * l1, a2 + q.p2 * l2, a3 + q.p3 * l3, r));
+    };
+    const int pad = L.pad_ref;
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t sweep = sweep0 + static_cast<uint32_t>(t);
+        for (int c = 0; c < L.C; ++c) {
+            const int beg = __ldg(L.cofs + c), end = __ldg(L.cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                PenRec<DC, DL> rc;
+                rc.load(L.rec, pos);
+                uint32_t xa[DC], xb[DC], ya[DL], yb[DL];
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const uint2 w = fetch8(rc.nb(k));
+                    xa[k] = w.x;
+                    xb[k] = w.y;
+                }
+#pragma unroll
+                for (int l = 0; l < DL; ++l) {
+                    const uint2 w = rc.lk(l) != pad ? fetch8(rc.lk(l)) : make_uint2(0u, 0u);
+                    ya[l] = w.x;
+                    yb[l] = w.y;
+                }
+                const uint32_t id = static_cast<uint32_t>(rc.pid());
+                const uint32_t na = quad_bits(rc, qa, xa, ya, keys(make_uint4(id, sweep, lq, c3)));
+                const uint32_t nb = quad_bits(rc, qb, xb, yb, keys(make_uint4(id, sweep, lqb, c3b)));
+                bits[pos * B + lane_b] = static_cast<uint8_t>(na | (nb << 4));
+            }
+            __syncthreads();
+        }
+    }
+    // write back rows 0..n-1 as int8 spins
+    const int64_t nb_out = static_cast<int64_t>(n) * B;
+    for (int64_t i = threadIdx.x; i < nb_out; i += blockDim.x) {
+        const int64_t row = i / B;
+        const int b = static_cast<int>(i - row * B);
+        *reinterpret_cast<uint2 *>(L.S + row * L.Wc + col0 + 8 * b) = lut[bits[i]];
+    }
+    // f and g of the final sweep, as in k_sweep_penalty_smem, for the thread's 8 walkers
+    __shared__ long long s_F[kMaxSlab];
+    __shared__ int s_g[kMaxSlab];
+    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+        s_F[i] = 0;
+        s_g[i] = 0;
+    }
+    __syncthreads();
+    long long F[8];
+    int g[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        F[i] = 0;
+        g[i] = 0;
+    }
+    auto sb = [](const uint2 &w, int i) -> int {
+        const uint32_t x = i < 4 ? w.x : w.y;
+        return sbyte_rt(x, i & 3);
+    };
+    for (int pos = grp; pos < n; pos += G) {
+        PenRec<DC, DL> rc;
+        rc.load(L.rec, pos);
+        const uint2 xs = fetch8(pos * B);
+        const int h4 = 2 * rc.h2();
+        int cs[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cs[i] = h4;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) {
+            const uint2 x = fetch8(rc.nb(k));
+            const int j = rc.j2(k);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) cs[i] += j * sb(x, i);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) F[i] += static_cast<long long>(sb(xs, i)) * cs[i];
+#pragma unroll
+        for (int l = 0; l < DL; ++l) {
+            if (rc.lk(l) == pad) continue;
+            const uint2 y = fetch8(rc.lk(l));
+            const int w = rc.w(l);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) g[i] += w * (sb(xs, i) != sb(y, i));
+        }
+        const int k2 = 2 * rc.kk();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) g[i] += sb(xs, i) < 0 ? k2 : 0;
+    }
+    const int w0 = 8 * lane_b;
+    unsigned long long *sF = reinterpret_cast<unsigned long long *>(s_F);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        atomicAdd(sF + w0 + i, static_cast<unsigned long long>(F[i]));
+        atomicAdd(&s_g[w0 + i], g[i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+        wk.f[col0 + i] = -(s_F[i] / 4);
+        wk.g[col0 + i] = s_g[i] / 2 + L.g0;
+    }
+}
+
 template <int DC, int DL>
 cudaError_t launch_bits_variant(const Layout &L, const Walkers &wk, const SweepTiling &tl, int32_t qpr,
                                 const RoundKeys &rk, uint32_t sweep0, int32_t nsweeps, cudaStream_t st) {
     int shift = 0;
     while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
     const size_t smem = bits_sweep_bytes(L.n, 1 << shift);
+    if (tl.walkers_per_thread == 8) {
+        cudaError_t e = allow_max_dynamic_smem<k_sweep_penalty_bits8<DC, DL>>();
+        if (e != cudaSuccess) return e;
+        const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
+        k_sweep_penalty_bits8<DC, DL><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
+        return cudaGetLastError();
+    }
     cudaError_t e = allow_max_dynamic_smem<k_sweep_penalty_bits<DC, DL>>();
     if (e != cudaSuccess) return e;
     const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
@@ -362,11 +531,12 @@ bool penalty_kernel_degrees(int DC, int DL) {
 cudaError_t launch_penalty_sweeps(const Layout &L, const Walkers &wk, const SweepTiling &tl,
                                   int32_t quads_per_run, uint64_t seed, uint32_t sweep0, int32_t nsweeps,
                                   cudaStream_t st) {
-    if (!L.penalty || tl.walkers_per_thread != 4) return cudaErrorInvalidValue;
+    if (!L.penalty || (tl.walkers_per_thread != 4 && !(tl.bits && tl.walkers_per_thread == 8)))
+        return cudaErrorInvalidValue;
     const RoundKeys rk = round_keys(seed);
     const int k = L.DC * 8 + L.DL;
     if (tl.bits) {
-        if (tl.lanes_per_spin < 2) return cudaErrorInvalidValue;
+        if (tl.lanes_per_spin < 2) return cudaErrorInvalidValue;  // slabs of >= 8 walkers
         switch (k) {
             case 3 * 8 + 2: return launch_bits_variant<3, 2>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);
             case 3 * 8 + 3: return launch_bits_variant<3, 3>(L, wk, tl, quads_per_run, rk, sweep0, nsweeps, st);

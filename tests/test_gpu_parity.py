@@ -524,10 +524,11 @@ def _graph_colouring_pair(pt, V, k, max_deg, seed):
     return phys_p, phys_o, int(deg.max())
 
 
-@pytest.mark.parametrize("k,max_deg,wpc,kernel", [
-    (3, 3, 0, "auto"), (4, 3, 16, "auto"), (3, 4, 0, "auto"), (4, 4, 32, "auto"), (3, 6, 0, "auto"),
-    (4, 5, 64, "auto"), (3, 3, 8, "bits"), (4, 3, 16, "bits"), (3, 4, 64, "bits"), (4, 5, 128, "bits")])
-def test_penalty_specialised_kernel_bit_exact(pt, k, max_deg, wpc, kernel):
+@pytest.mark.parametrize("k,max_deg,wpc,kernel,wpt", [
+    (3, 3, 0, "auto", 0), (4, 3, 16, "auto", 0), (3, 4, 0, "auto", 0), (4, 4, 32, "auto", 0),
+    (3, 6, 0, "auto", 0), (4, 5, 64, "auto", 0), (3, 3, 8, "bits", 0), (4, 3, 16, "bits", 0),
+    (3, 4, 64, "bits", 0), (4, 5, 128, "bits", 0), (3, 3, 8, "bits", 4), (4, 5, 32, "bits", 4)])
+def test_penalty_specialised_kernel_bit_exact(pt, k, max_deg, wpc, kernel, wpt):
     """Instances with penalty terms and coupling degree <= 6, link degree <= 3
     run on the degree-specialised kernels (records padded to coupling width 3,
     4 or 6 and link width 2 or 3), with the slab as int8 or bit-packed in
@@ -538,8 +539,10 @@ def test_penalty_specialised_kernel_bit_exact(pt, k, max_deg, wpc, kernel):
     beta = np.array([0.03, 0.1, 0.4, 1.2, 3.0], np.float32)
     P = np.array([1, 2, 4, 9], np.int32)
     ctx, orc = both(pt, None, None, beta, P, 7, 97531, [(48, 4), (20, 4)], phys=(phys_p, phys_o), trace=24,
-                    target=-10 ** 6, wpc=wpc, kernel=kernel)
+                    target=-10 ** 6, wpc=wpc, kernel=kernel, wpt=wpt)
     assert ctx.tiling["kernel"] == ("penalty_bits" if kernel == "bits" else "penalty_smem")
+    if kernel == "bits":
+        assert ctx.tiling["walkers_per_thread"] == (wpt or 8)
     assert_same(pt, ctx, orc)
     assert np.all(ctx.read(pt.G) >= 0)
 
