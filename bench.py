@@ -66,11 +66,11 @@ BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
 # DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only while the kernel sources hash to `src`; the summaries are under profiles/.
 PROFILED_TRAFFIC = {
-    ("n200", "k_sweep_smem"): dict(src="adee74855b0e7033", dram_bytes_per_launch=386_782_976,
+    ("n200", "k_sweep_smem"): dict(src="c80185e33775ecd0", dram_bytes_per_launch=386_512_128,
                                    profile="profiles/k_sweep_smem_n200.md"),
     # captured at 4 of the 16 runs and scaled by the walkers
-    ("n800", "k_sweep_bits"): dict(src="adee74855b0e7033", dram_bytes_per_launch=18_430_910_464,
-                                   profile="profiles/k_sweep_bits_n800.md (4 runs x 4)"),
+    ("n800", "k_sweep_bits8"): dict(src="c80185e33775ecd0", dram_bytes_per_launch=19_904_616_448,
+                                    profile="profiles/k_sweep_bits8_n800.md (4 runs x 4)"),
     ("constrained", "k_sweep_penalty_smem"): dict(src="704df347ebd1e10c", dram_bytes_per_launch=341_058_304,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
     # V = 40000 colouring: captured at 16 of the 64 runs and scaled by the walkers
@@ -734,7 +734,7 @@ def run_batched(args):
     line["roofline"] = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tops/s (lane-ops)",
                         "frac": alu / alu_peak, "traffic": None, "kernel": "k_batch",
                         "ops_per_update": OPS_PER_UPDATE,
-                        "traffic_source": "profiles/k_batch_256.md (256-instance capture, not scaled)",
+                        "traffic_source": "profiles/k_batch_uneven128.md (128-instance capture, not scaled)",
                         "peak_source": f"{sm_count} SMs x 128 lanes x max clock ({peak_src})"}
     print(json.dumps(line))
 
