@@ -126,7 +126,9 @@ typedef struct {
                                 8..128 bit-packed), power of two; 0 = automatic      */
     int32_t threads_per_cta; /* multiple of 32, >= walkers_per_cta/walkers_per_thread,
                                 <= 256 (global slab), 1024 (shared slab, 4 walkers
-                                a thread) or 512 (8 walkers a thread); 0 = automatic */
+                                a thread), 640 (bit-packed slab of a specialised
+                                layout, 8 walkers a thread) or 512 (other slabs, 8
+                                walkers a thread); 0 = automatic                  */
     int32_t device;          /* CUDA device ordinal; -1 = current device            */
     int32_t profile;         /* nonzero: time every kernel launch with CUDA events  */
     int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 int8 slab in

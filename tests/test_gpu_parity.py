@@ -187,7 +187,8 @@ def test_tiny_config_bit_exact_full_length(pt, tiny_config):
     ("smem", 16, 32, 4), ("smem", 32, 64, 4), ("smem", 64, 1024, 4), ("smem", 128, 128, 4),
     ("smem", 16, 64, 8), ("smem", 64, 512, 8), ("smem", 128, 32, 8), ("bits", 8, 32, 0),
     ("bits", 16, 64, 0), ("bits", 64, 1024, 0), ("bits", 128, 96, 0), ("bits", 8, 64, 4),
-    ("bits", 16, 64, 4), ("bits", 64, 512, 8), ("bits", 128, 512, 8), ("auto", 0, 0, 0)])
+    ("bits", 16, 64, 4), ("bits", 64, 512, 8), ("bits", 128, 512, 8), ("bits", 8, 640, 8),
+    ("auto", 0, 0, 0)])
 def test_ragged_tiles_and_resume(pt, kernel, wpc, threads, wpt):
     inst = synth.wishart_planted(30, 0.5, 21)
     beta = synth.beta_ladder(5, 0.2, 3.0, inst.scale)
