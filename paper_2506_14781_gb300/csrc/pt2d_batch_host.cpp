@@ -388,7 +388,7 @@ size_t pt2d_batch_instance_bytes(const pt2d_batch *b, const pt2d_instance *inst,
     pt2d_options o;
     pt2d_default_options(&o);
     o.sweep_kernel = 1;
-    if (pt2d::prepare(inst, I, nullptr, J, nullptr, 1, &o, pp, b->generic ? -1 : b->DC)) return 0;
+    if (pt2d::prepare(inst, I, nullptr, J, nullptr, 1, &o, pp, b->generic ? -1 : b->DC, false)) return 0;
     if (b->generic && !degrees_fit(b, pp)) return 0;
     const int32_t R = I * J;
     return align_up(block_layout(inst->n, pp.C, pp.rec_vec, I, J, R, pow2_at_least(R), runs, b->trace_cap)

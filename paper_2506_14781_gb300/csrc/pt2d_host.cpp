@@ -43,21 +43,36 @@ std::atomic<int32_t> g_fail_allocs{0};  // injected allocation failures still to
 
 // Validates a symmetric CSR (no self loops, no duplicates, equal values both
 // ways; `val` may be NULL for unweighted links) and returns sorted adjacency.
-int check_csr(int32_t n, const int32_t *ptr, const int32_t *col, const int16_t *val,
-              std::vector<std::vector<std::pair<int32_t, int32_t>>> *adj) {
+// Adjacency of a validated CSR: one flat array of (neighbour, value) pairs,
+// each row sorted by neighbour (a row per spin, no allocation per row).
+struct Adjacency {
+    std::vector<int32_t> ptr;
+    std::vector<std::pair<int32_t, int32_t>> e;
+    struct Row {
+        std::pair<int32_t, int32_t> *b, *en;
+        std::pair<int32_t, int32_t> *begin() const { return b; }
+        std::pair<int32_t, int32_t> *end() const { return en; }
+        size_t size() const { return static_cast<size_t>(en - b); }
+        std::pair<int32_t, int32_t> &operator[](size_t i) const { return b[i]; }
+    };
+    Row operator[](int32_t a) { return Row{e.data() + ptr[a], e.data() + ptr[a + 1]}; }
+};
+
+int check_csr(int32_t n, const int32_t *ptr, const int32_t *col, const int16_t *val, Adjacency *adj) {
     if (!ptr) return PT2D_ERR_INVALID_ARG;
     if (ptr[0] != 0) return PT2D_ERR_INVALID_ARG;
     for (int32_t a = 0; a < n; ++a)
         if (ptr[a + 1] < ptr[a]) return PT2D_ERR_INVALID_ARG;
     if (ptr[n] > 0 && !col) return PT2D_ERR_INVALID_ARG;
-    adj->assign(n, {});
+    adj->ptr.assign(ptr, ptr + n + 1);
+    adj->e.resize(static_cast<size_t>(ptr[n]));
     for (int32_t a = 0; a < n; ++a) {
         for (int32_t k = ptr[a]; k < ptr[a + 1]; ++k) {
             const int32_t b = col[k];
             if (b < 0 || b >= n || b == a) return PT2D_ERR_INVALID_ARG;
-            (*adj)[a].push_back({b, val ? static_cast<int32_t>(val[k]) : 0});
+            adj->e[k] = {b, val ? static_cast<int32_t>(val[k]) : 0};
         }
-        auto &v = (*adj)[a];
+        auto v = (*adj)[a];
         std::sort(v.begin(), v.end());
         for (size_t i = 1; i < v.size(); ++i)
             if (v[i].first == v[i - 1].first) return PT2D_ERR_INVALID_ARG;  // duplicate edge
@@ -65,7 +80,7 @@ int check_csr(int32_t n, const int32_t *ptr, const int32_t *col, const int16_t *
     // symmetry with equal values
     for (int32_t a = 0; a < n; ++a)
         for (const auto &e : (*adj)[a]) {
-            const auto &w = (*adj)[e.first];
+            const auto w = (*adj)[e.first];
             auto it = std::lower_bound(w.begin(), w.end(), std::make_pair(a, INT32_MIN));
             if (it == w.end() || it->first != a || it->second != e.second) return PT2D_ERR_INVALID_ARG;
         }
@@ -96,13 +111,13 @@ int check_device() {
 }
 
 int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, const int32_t *P,
-            int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc) {
+            int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc, bool records) {
     if (!inst || inst->n < 1 || I < 1 || J < 1 || runs < 1) return PT2D_ERR_INVALID_ARG;
     // the swap kernel keeps one run's slot -> walker map in shared memory
     if (static_cast<int64_t>(I) * J > kMaxSlots) return PT2D_ERR_INVALID_ARG;
     if (runs >= (1 << 27)) return PT2D_ERR_INVALID_ARG;
     const int32_t n = inst->n;
-    std::vector<std::vector<std::pair<int32_t, int32_t>>> cadj, ladj;
+    Adjacency cadj, ladj;
     if (!inst->cp_ptr || !inst->lk_ptr) return PT2D_ERR_INVALID_ARG;
     if (inst->cp_ptr[n] > 0 && !inst->cp_J) return PT2D_ERR_INVALID_ARG;
     int st = check_csr(n, inst->cp_ptr, inst->cp_col, inst->cp_J, &cadj);
@@ -383,6 +398,12 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     const int32_t rec_vec = (rec_ints + 3) / 4;
     const size_t ri = static_cast<size_t>(rec_vec) * 4;
     pp.rec_vec = rec_vec;
+    // neighbour references become byte offsets into the shared-memory slab
+    const int scale = sw ? sw : (bw ? bw / 8 : 1);
+    pp.pad_ref = n * scale;
+    const int64_t slab = 4LL * ql;
+    pp.Wc = (walkers + slab - 1) / slab * slab;
+    if (!records) return PT2D_OK;
     pp.rec.assign(static_cast<size_t>(n) * ri, 0);
     for (int32_t p = 0; p < n; ++p) {
         const int32_t a = pp.pid[p];
@@ -420,16 +441,11 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
             r[ko + DL] = inst->hk ? inst->hk[a] : 0;
         }
     }
-    // neighbour references become byte offsets into the shared-memory slab
-    const int scale = sw ? sw : (bw ? bw / 8 : 1);
     if (scale > 1) {
         const size_t ri2 = static_cast<size_t>(pp.rec_vec) * 4;
         for (int32_t p = 0; p < n; ++p)
             for (int32_t k = 0; k < DC + DL; ++k) pp.rec[static_cast<size_t>(p) * ri2 + k] *= scale;
     }
-    pp.pad_ref = n * scale;
-    const int64_t slab = 4LL * ql;
-    pp.Wc = (walkers + slab - 1) / slab * slab;
     return PT2D_OK;
 }
 
@@ -573,7 +589,7 @@ int pt2d_workspace_size(const pt2d_instance *inst, int32_t I, int32_t J, int32_t
                         const pt2d_options *opt, size_t *bytes) {
     if (!bytes) return PT2D_ERR_INVALID_ARG;
     pt2d_ctx tmp;
-    int st = prepare(inst, I, nullptr, J, nullptr, runs, opt, tmp.pp);
+    int st = prepare(inst, I, nullptr, J, nullptr, runs, opt, tmp.pp, 0, false);
     if (st) return st;
     *bytes = carve(&tmp, nullptr);
     return PT2D_OK;
@@ -968,7 +984,7 @@ int pt2d_greedy_color(const pt2d_instance *inst, int32_t *color, int32_t *n_colo
     pt2d_default_options(&o);
     o.walkers_per_cta = 4;
     o.threads_per_cta = 32;
-    int st = prepare(&tmp, 1, nullptr, 1, nullptr, 1, &o, pp);
+    int st = prepare(&tmp, 1, nullptr, 1, nullptr, 1, &o, pp, 0, false);
     if (st) return st;
     std::memcpy(color, pp.color.data(), sizeof(int32_t) * pp.n);
     *n_colors = pp.C;

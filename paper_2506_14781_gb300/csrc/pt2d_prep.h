@@ -28,8 +28,10 @@ struct Prep {
 // colours it, orders spins by colour and packs the neighbour records; with
 // force_dc > 0 the records use that coupling width (links 2) or the call fails;
 // with force_dc < 0 they use the wide layout of the runtime-degree kernels.
-// Also chooses the plain-context sweep tiling from `opt` and `runs`.
+// Also chooses the plain-context sweep tiling from `opt` and `runs`.  With
+// records = false it stops before packing the records (the sizes, colours and
+// tiling are set; pp.rec stays empty), for callers that only need sizes.
 int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, const int32_t *P,
-            int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc = 0);
+            int32_t runs, const pt2d_options *opt, Prep &pp, int force_dc = 0, bool records = true);
 
 }  // namespace pt2d
