@@ -309,17 +309,21 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     // penalty-specialised or the runtime-degree shared-memory kernel.
     int sw = 0;
     pp.tiling.pair = false;
-    // Two CTAs per SM for the int8 kernel of the specialised layouts, when asked
-    // for (8 walkers per CTA, at most 640 threads): 8-walker slabs, <= 48
-    // registers, 40 warps per SM against 32 for one 1024-thread CTA.  Measured at
-    // N = 200 it is 1 % slower than one CTA of 16-walker slabs (14.97 vs 14.84
-    // ms per launch), so the automatic tiling does not pick it.
+    // Two CTAs per SM for the int8 kernel of the specialised layouts: 8-walker
+    // slabs, 640 threads at <= 48 registers (40 warps per SM against 32 for one
+    // 1024-thread CTA; 3 % faster at N = 200), when two such slabs fit in an SM's
+    // shared memory and the grid fills at least one wave of CTA pairs.
     const bool pair_fits = specialised &&
                            2 * (pt2d::smem_sweep_bytes(n, 8) + pt2d::kSweepStaticSmem + smem_reserved) <=
                                static_cast<size_t>(smem_sm);
+    const int req_threads_sm = opt ? opt->threads_per_cta : 0;
+    const int req_wpt_sm = opt ? opt->walkers_per_thread : 0;
     if (mode == 0 || mode == 2) {
         if (req_w) {
             if (req_w >= (specialised ? 8 : 16) && fits(req_w)) sw = req_w;  // 8: k_sweep_smem only
+        } else if (pair_fits && req_wpt_sm != 8 && (req_threads_sm == 0 || req_threads_sm <= 640) &&
+                   walkers / 8 >= 2LL * sms) {
+            sw = 8;
         } else {
             sw = pick_width(128, 16, fits);
         }

@@ -105,7 +105,7 @@ __device__ __forceinline__ void energies(const Layout &L, const Walkers &wk, Fet
 // once, swept `nsweeps` times, written back once.  SW >= 8; each thread owns
 // WPT = 4 or 8 consecutive walkers of the slab.
 // PAIR: two CTAs share an SM (8-walker slabs of at most ~110 KB, 640 threads at
-// <= 48 registers: 40 warps per SM instead of 32), chosen only when asked for.
+// <= 48 registers: 40 warps per SM instead of 32).
 template <int DC, int DL, int WPT, bool PAIR>
 __global__ void __launch_bounds__(PAIR ? 640 : (WPT == 4 ? 1024 : 512), PAIR ? 2 : 1)
     k_sweep_smem(Layout L, Walkers wk, int sw_shift, int32_t quads_per_run, RoundKeys rk,

@@ -611,8 +611,9 @@ def test_n200_full_size_sampled_runs(pt):
     N=200, alpha=0.5, <=3 edges per copy (13,400 spins), I=32 x J=8 with the
     benchmark's ladders (beta 0.1..5.0 / s, P 0.5..64 x 32767), 64 runs, swap
     interval 50, in the benchmark's launch configuration (its own stream,
-    torch-allocated workspace, kernel timing on, the automatic tiling); two
-    runs checked in full by the oracle after two events (100 sweeps)."""
+    torch-allocated workspace, kernel timing on, the automatic tiling: two
+    640-thread CTAs per SM on 8-walker int8 slabs); two runs checked in full
+    by the oracle after two events (100 sweeps)."""
     import torch
 
     wl = _bench_workload("n200")
@@ -625,7 +626,7 @@ def test_n200_full_size_sampled_runs(pt):
     ctx = pt.PT2D(phys_p, beta, P, runs, stream=stream, workspace="torch", trace_capacity=8,
                   profile=True)
     assert ctx.tiling["kernel"] == "smem"
-    assert ctx.tiling["walkers_per_cta"] == 16 and ctx.tiling["threads_per_cta"] == 1024
+    assert ctx.tiling["walkers_per_cta"] == 8 and ctx.tiling["threads_per_cta"] == 640
     ctx.write(pt.TARGET, np.full(runs, inst.E_planted))
     with torch.cuda.stream(stream):
         ctx.run(2 * interval, interval, seed)
