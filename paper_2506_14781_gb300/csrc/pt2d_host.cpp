@@ -245,7 +245,7 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     // (n + 1) x SW bytes (int8) or (n + 1) x SW / 8 bytes (bit-packed, the
     // specialised layouts only), for the swap interval; otherwise the slab
     // stays in global memory.
-    int sms = 152, smem_max = 232448, smem_sm = 233472, smem_reserved = 1024;
+    int sms = 152, smem_max = 232448;
     {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) {
@@ -255,12 +255,6 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
             if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
                 v > 0)
                 smem_max = v;
-            if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
-                v > 0)
-                smem_sm = v;
-            if (cudaDeviceGetAttribute(&v, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess && v >= 0)
-                smem_reserved = v;
-            cudaGetLastError();
         } else {
             cudaGetLastError();
         }
@@ -308,22 +302,9 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     // int8 shared-memory slab width (0 = global kernel): the specialised, the
     // penalty-specialised or the runtime-degree shared-memory kernel.
     int sw = 0;
-    pp.tiling.pair = false;
-    // Two CTAs per SM for the int8 kernel of the specialised layouts: 8-walker
-    // slabs, 640 threads at <= 48 registers (40 warps per SM against 32 for one
-    // 1024-thread CTA; 3 % faster at N = 200), when two such slabs fit in an SM's
-    // shared memory and the grid fills at least one wave of CTA pairs.
-    const bool pair_fits = specialised &&
-                           2 * (pt2d::smem_sweep_bytes(n, 8) + pt2d::kSweepStaticSmem + smem_reserved) <=
-                               static_cast<size_t>(smem_sm);
-    const int req_threads_sm = opt ? opt->threads_per_cta : 0;
-    const int req_wpt_sm = opt ? opt->walkers_per_thread : 0;
     if (mode == 0 || mode == 2) {
         if (req_w) {
-            if (req_w >= (specialised ? 8 : 16) && fits(req_w)) sw = req_w;  // 8: k_sweep_smem only
-        } else if (pair_fits && req_wpt_sm != 8 && (req_threads_sm == 0 || req_threads_sm <= 640) &&
-                   walkers / 8 >= 2LL * sms) {
-            sw = 8;
+            if (req_w >= 16 && fits(req_w)) sw = req_w;
         } else {
             sw = pick_width(128, 16, fits);
         }
@@ -373,12 +354,9 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         int32_t widest = 0;
         for (int32_t c = 0; c < C; ++c) widest = std::max(widest, pp.cofs[c + 1] - pp.cofs[c]);
         const int64_t want = (static_cast<int64_t>(widest) * lanes + 31) / 32 * 32;
-        const bool pair_width = sw == 8 && wpt == 4 && pair_fits;
-        threads = (opt && opt->threads_per_cta > 0)
-                      ? opt->threads_per_cta
-                      : static_cast<int>(std::min<int64_t>(pair_width ? 640 : tmax, want));
+        threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta
+                                                    : static_cast<int>(std::min<int64_t>(tmax, want));
         if (threads < 32 || threads > tmax || threads % 32 || threads < lanes) return PT2D_ERR_INVALID_ARG;
-        pp.tiling.pair = pair_width && threads <= 640;
     } else {
         if (opt && opt->walkers_per_thread != 0 && opt->walkers_per_thread != 4)
             return PT2D_ERR_INVALID_ARG;

@@ -101,7 +101,6 @@ struct SweepTiling {
     bool smem;           // slab in shared memory (k_sweep_smem) or global (k_sweep_global)
     int walkers_per_thread;  // 4, or 8 in the int8 and bit-packed shared-memory kernels
     bool bits;           // slab bit-packed in shared memory (k_sweep_bits)
-    bool pair;           // int8 slab kernel, two 640-thread CTAs per SM (8-walker slabs)
 };
 
 // Dynamic shared memory of k_sweep_smem for n spins and a slab of W walkers.

@@ -102,12 +102,10 @@ __device__ __forceinline__ void energies(const Layout &L, const Walkers &wk, Fet
 }
 
 // Sweep block with the slab in shared memory: (n + 1) rows x SW bytes, loaded
-// once, swept `nsweeps` times, written back once.  SW >= 8; each thread owns
+// once, swept `nsweeps` times, written back once.  SW >= 16; each thread owns
 // WPT = 4 or 8 consecutive walkers of the slab.
-// PAIR: two CTAs share an SM (8-walker slabs of at most ~110 KB, 640 threads at
-// <= 48 registers: 40 warps per SM instead of 32).
-template <int DC, int DL, int WPT, bool PAIR>
-__global__ void __launch_bounds__(PAIR ? 640 : (WPT == 4 ? 1024 : 512), PAIR ? 2 : 1)
+template <int DC, int DL, int WPT>
+__global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
     k_sweep_smem(Layout L, Walkers wk, int sw_shift, int32_t quads_per_run, RoundKeys rk,
                  uint32_t sweep0, int32_t nsweeps) {
     extern __shared__ __align__(16) int8_t sm[];
@@ -132,19 +130,14 @@ __global__ void __launch_bounds__(PAIR ? 640 : (WPT == 4 ? 1024 : 512), PAIR ? 2
     const Quad qb = NQ == 2 ? load_quad(wk, col0 + lane_off + 4) : qa;
     const KeysConst keys{rk};
 
-    // load the slab, 16 bytes per access (8 for 8-walker slabs)
+    // load the slab, 16 bytes per access
     const int vec_per_row = SW >> 4;
-    if (SW >= 16) {
-        const int64_t nvec = static_cast<int64_t>(L.n + 1) * vec_per_row;
-        for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
-            const int64_t row = i / vec_per_row;
-            const int part = static_cast<int>(i - row * vec_per_row);
-            reinterpret_cast<uint4 *>(sm)[i] =
-                *reinterpret_cast<const uint4 *>(L.S + row * L.Wc + col0 + 16 * part);
-        }
-    } else {
-        for (int64_t row = threadIdx.x; row <= L.n; row += blockDim.x)
-            reinterpret_cast<uint2 *>(sm)[row] = *reinterpret_cast<const uint2 *>(L.S + row * L.Wc + col0);
+    const int64_t nvec = static_cast<int64_t>(L.n + 1) * vec_per_row;
+    for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
+        const int64_t row = i / vec_per_row;
+        const int part = static_cast<int>(i - row * vec_per_row);
+        reinterpret_cast<uint4 *>(sm)[i] =
+            *reinterpret_cast<const uint4 *>(L.S + row * L.Wc + col0 + 16 * part);
     }
     __syncthreads();
 
@@ -174,17 +167,12 @@ __global__ void __launch_bounds__(PAIR ? 640 : (WPT == 4 ? 1024 : 512), PAIR ? 2
     }
 
     // write the slab back (rows 0..n-1)
-    if (SW >= 16) {
-        const int64_t nvec_out = static_cast<int64_t>(L.n) * vec_per_row;
-        for (int64_t i = threadIdx.x; i < nvec_out; i += blockDim.x) {
-            const int64_t row = i / vec_per_row;
-            const int part = static_cast<int>(i - row * vec_per_row);
-            *reinterpret_cast<uint4 *>(L.S + row * L.Wc + col0 + 16 * part) =
-                reinterpret_cast<const uint4 *>(sm)[i];
-        }
-    } else {
-        for (int64_t row = threadIdx.x; row < L.n; row += blockDim.x)
-            *reinterpret_cast<uint2 *>(L.S + row * L.Wc + col0) = reinterpret_cast<const uint2 *>(sm)[row];
+    const int64_t nvec_out = static_cast<int64_t>(L.n) * vec_per_row;
+    for (int64_t i = threadIdx.x; i < nvec_out; i += blockDim.x) {
+        const int64_t row = i / vec_per_row;
+        const int part = static_cast<int>(i - row * vec_per_row);
+        *reinterpret_cast<uint4 *>(L.S + row * L.Wc + col0 + 16 * part) =
+            reinterpret_cast<const uint4 *>(sm)[i];
     }
     auto fetch_q = [&](int off, int h) -> uint32_t {
         return *reinterpret_cast<const uint32_t *>(sm + off + lane_off + 4 * h);
@@ -513,17 +501,17 @@ cudaError_t to_device(T **d, const T *h, int64_t count) {
     return cudaMemcpy(*d, h, sizeof(T) * count, cudaMemcpyHostToDevice);
 }
 
-template <int DC, int DL, int WPT, bool PAIR>
+template <int DC, int DL, int WPT>
 cudaError_t launch_smem_variant(const Layout &L, const Walkers &wk, const SweepTiling &tl,
                                 int32_t qpr, const RoundKeys &rk, uint32_t sweep0,
                                 int32_t nsweeps, cudaStream_t st) {
     int shift = 0;
     while ((1 << shift) < 4 * tl.lanes_per_spin) ++shift;
     const size_t smem = static_cast<size_t>(L.n + 1) << shift;
-    cudaError_t e = allow_max_dynamic_smem<k_sweep_smem<DC, DL, WPT, PAIR>>();
+    cudaError_t e = allow_max_dynamic_smem<k_sweep_smem<DC, DL, WPT>>();
     if (e != cudaSuccess) return e;
     const unsigned blocks = static_cast<unsigned>(L.Wc >> shift);
-    k_sweep_smem<DC, DL, WPT, PAIR><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
+    k_sweep_smem<DC, DL, WPT><<<blocks, tl.threads, smem, st>>>(L, wk, shift, qpr, rk, sweep0, nsweeps);
     return cudaGetLastError();
 }
 
@@ -531,9 +519,8 @@ template <int DC, int DL>
 cudaError_t launch_smem(const Layout &L, const Walkers &wk, const SweepTiling &tl, int32_t qpr,
                         const RoundKeys &rk, uint32_t sweep0, int32_t nsweeps, cudaStream_t st) {
     if (tl.walkers_per_thread == 8)
-        return launch_smem_variant<DC, DL, 8, false>(L, wk, tl, qpr, rk, sweep0, nsweeps, st);
-    if (tl.pair) return launch_smem_variant<DC, DL, 4, true>(L, wk, tl, qpr, rk, sweep0, nsweeps, st);
-    return launch_smem_variant<DC, DL, 4, false>(L, wk, tl, qpr, rk, sweep0, nsweeps, st);
+        return launch_smem_variant<DC, DL, 8>(L, wk, tl, qpr, rk, sweep0, nsweeps, st);
+    return launch_smem_variant<DC, DL, 4>(L, wk, tl, qpr, rk, sweep0, nsweeps, st);
 }
 
 template <int DC, int DL>
