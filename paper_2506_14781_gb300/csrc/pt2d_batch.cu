@@ -416,7 +416,7 @@ template <int DC, int DL>
 __device__ __forceinline__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm) {
     const BatchRun d = a.runs[it.run];
     uint8_t *pool = a.pool;
-    const int n = d.n, Rp = d.Rp, R = d.R, J = d.J;
+    const int n = d.n, Rp = d.Rp;
     const int SW = d.sw;
     const int QL = SW >> 2;
     const int lane_q = threadIdx.x & (QL - 1);
