@@ -84,5 +84,7 @@ cudaError_t launch_batch(const BatchArgs &a, int DC, int DL, int grid, int threa
 // at most 512 threads per CTA.
 cudaError_t launch_batch_bits8(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
 constexpr int kBatchBits8Threads = 512;
+// Most threads per CTA of the runtime-degree batch kernel.
+constexpr int kBatchGenericThreads = 768;
 
 }  // namespace pt2d

@@ -333,6 +333,7 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
     const int grid = std::min(b->grid, b->n_items);
     const int grid8 = std::min(b->grid, b->n_items_bits8);
     const int threads8 = std::min(b->threads, pt2d::kBatchBits8Threads);
+    const int threads = b->generic ? std::min(b->threads, pt2d::kBatchGenericThreads) : b->threads;
     const int kdc = b->generic ? 0 : b->DC;
     if (grid > 0) BK(b, pt2d::batch_kernel_attributes(kdc, 2, b->smem_state));
     // per event: the counters are cleared, then every slab of every run
@@ -345,7 +346,7 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
                 if (x != cudaSuccess) return x;
             }
             if (grid > 0) {
-                x = pt2d::launch_batch(a, kdc, 2, grid, b->threads, b->stream);
+                x = pt2d::launch_batch(a, kdc, 2, grid, threads, b->stream);
                 if (x != cudaSuccess) return x;
             }
         }
