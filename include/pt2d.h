@@ -126,9 +126,10 @@ typedef struct {
                                 8..128 bit-packed), power of two; 0 = automatic      */
     int32_t threads_per_cta; /* multiple of 32, >= walkers_per_cta/walkers_per_thread,
                                 <= 256 (global slab), 1024 (shared slab, 4 walkers
-                                a thread), 640 (bit-packed slab of a specialised
-                                layout, 8 walkers a thread) or 512 (other slabs, 8
-                                walkers a thread); 0 = automatic                  */
+                                a thread), 768 (int8 slab, 8 walkers a thread), 640
+                                (bit-packed slab of a specialised layout, 8 walkers
+                                a thread) or 512 (other bit-packed slabs, 8 walkers
+                                a thread); 0 = automatic                          */
     int32_t device;          /* CUDA device ordinal; -1 = current device            */
     int32_t profile;         /* nonzero: time every kernel launch with CUDA events  */
     int32_t sweep_kernel;    /* 0 automatic, 1 slab in global memory, 2 int8 slab in
@@ -139,9 +140,9 @@ typedef struct {
                                 INVALID_ARG; 2, 3: INVALID_ARG if it does not fit)   */
     int32_t walkers_per_thread; /* 4 or 8 for the int8 shared-memory kernel of the
                                    specialised layouts and for the bit-packed
-                                   kernels, others: 4; 0 = automatic (bit-packed:
-                                   8, or 4 when more than 512 threads are asked
-                                   for; int8: 4)                                   */
+                                   kernels, others: 4; 0 = automatic: 8, or 4 when
+                                   more threads are asked for than 8 walkers a
+                                   thread allow                                    */
     int32_t swap_mode;       /* PT2D_SWAP_2D (0): Algorithm 1.  PT2D_SWAP_JCOLUMN (1):
                                 the paper's J-column PT baseline -- every event is a
                                 beta-swap event (pairs starting at the first row on

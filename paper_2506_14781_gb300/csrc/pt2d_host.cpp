@@ -345,12 +345,16 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     } else
     if (sw) {
         ql = sw / 4;
+        // the specialised layouts' int8 kernel: a thread owns 8 walkers (two
+        // quads) at up to 768 threads unless 4 or more threads are asked for
+        // (N = 200: 14.26 ms per launch against 14.84 with 4 walkers at 1024)
         const int req_t = opt ? opt->walkers_per_thread : 0;
+        const int req_threads = opt ? opt->threads_per_cta : 0;
         if (req_t != 0 && req_t != 4 && req_t != 8) return PT2D_ERR_INVALID_ARG;
         if (req_t == 8 && !specialised) return PT2D_ERR_INVALID_ARG;
-        wpt = req_t ? req_t : 4;
+        wpt = req_t ? req_t : (specialised && req_threads <= 768 ? 8 : 4);
         const int lanes = sw / wpt;  // threads per spin row segment
-        const int tmax = wpt == 4 ? 1024 : 512;
+        const int tmax = wpt == 4 ? 1024 : 768;
         int32_t widest = 0;
         for (int32_t c = 0; c < C; ++c) widest = std::max(widest, pp.cofs[c + 1] - pp.cofs[c]);
         const int64_t want = (static_cast<int64_t>(widest) * lanes + 31) / 32 * 32;

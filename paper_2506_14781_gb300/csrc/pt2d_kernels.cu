@@ -105,7 +105,7 @@ __device__ __forceinline__ void energies(const Layout &L, const Walkers &wk, Fet
 // once, swept `nsweeps` times, written back once.  SW >= 16; each thread owns
 // WPT = 4 or 8 consecutive walkers of the slab.
 template <int DC, int DL, int WPT>
-__global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
+__global__ void __launch_bounds__(WPT == 4 ? 1024 : 768, 1)
     k_sweep_smem(Layout L, Walkers wk, int sw_shift, int32_t quads_per_run, RoundKeys rk,
                  uint32_t sweep0, int32_t nsweeps) {
     extern __shared__ __align__(16) int8_t sm[];

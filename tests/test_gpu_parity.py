@@ -185,7 +185,8 @@ def test_tiny_config_bit_exact_full_length(pt, tiny_config):
 @pytest.mark.parametrize("kernel,wpc,threads,wpt", [
     ("global", 4, 32, 0), ("global", 16, 64, 0), ("global", 32, 256, 0), ("global", 128, 256, 0),
     ("smem", 16, 32, 4), ("smem", 32, 64, 4), ("smem", 64, 1024, 4), ("smem", 128, 128, 4),
-    ("smem", 16, 64, 8), ("smem", 64, 512, 8), ("smem", 128, 32, 8), ("bits", 8, 32, 0),
+    ("smem", 16, 64, 8), ("smem", 64, 512, 8), ("smem", 128, 32, 8), ("smem", 16, 768, 8),
+    ("smem", 32, 768, 0), ("bits", 8, 32, 0),
     ("bits", 16, 64, 0), ("bits", 64, 1024, 0), ("bits", 128, 96, 0), ("bits", 8, 64, 4),
     ("bits", 16, 64, 4), ("bits", 64, 512, 8), ("bits", 128, 512, 8), ("bits", 8, 640, 8),
     ("auto", 0, 0, 0)])
@@ -623,7 +624,8 @@ def test_n200_full_size_sampled_runs(pt):
     stream = torch.cuda.Stream()
     ctx = pt.PT2D(phys_p, beta, P, runs, stream=stream, workspace="torch", trace_capacity=8,
                   profile=True)
-    assert ctx.tiling["kernel"] == "smem"
+    assert ctx.tiling["kernel"] == "smem" and ctx.tiling["walkers_per_thread"] == 8
+    assert ctx.tiling["walkers_per_cta"] == 16 and ctx.tiling["threads_per_cta"] == 768
     ctx.write(pt.TARGET, np.full(runs, inst.E_planted))
     with torch.cuda.stream(stream):
         ctx.run(2 * interval, interval, seed)
