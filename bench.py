@@ -66,10 +66,10 @@ BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
 # DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only while the kernel sources hash to `src`; the summaries are under profiles/.
 PROFILED_TRAFFIC = {
-    ("n200", "k_sweep_smem"): dict(src="73a0f242adb58594", dram_bytes_per_launch=386_374_144,
+    ("n200", "k_sweep_smem"): dict(src="49db11e6661d236b", dram_bytes_per_launch=389_465_856,
                                    profile="profiles/k_sweep_smem_n200.md"),
     # captured at 4 of the 16 runs and scaled by the walkers
-    ("n800", "k_sweep_bits8"): dict(src="73a0f242adb58594", dram_bytes_per_launch=17_894_226_944,
+    ("n800", "k_sweep_bits8"): dict(src="49db11e6661d236b", dram_bytes_per_launch=18_695_494_656,
                                     profile="profiles/k_sweep_bits8_n800.md (4 runs x 4)"),
     ("constrained", "k_sweep_penalty_smem"): dict(src="704df347ebd1e10c", dram_bytes_per_launch=341_058_304,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
