@@ -126,7 +126,7 @@ typedef struct {
                                 8..128 bit-packed), power of two; 0 = automatic      */
     int32_t threads_per_cta; /* multiple of 32, >= walkers_per_cta/walkers_per_thread,
                                 <= 256 (global slab), 1024 (shared slab, 4 walkers
-                                a thread), 768 (int8 slab, 8 walkers a thread), 640
+                                a thread), 768 (int8 slab, 8 walkers a thread), 896
                                 (bit-packed slab of a specialised layout, 8 walkers
                                 a thread) or 512 (other bit-packed slabs, 8 walkers
                                 a thread); 0 = automatic                          */

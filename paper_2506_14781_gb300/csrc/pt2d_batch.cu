@@ -132,7 +132,8 @@ __device__ void run_swap(const BatchArgs &a, const BatchRun &d, int run_index, u
 // reading them from shared memory at every use, which costs 3 %); the
 // runtime-degree kernel, whose wide records already need more registers than
 // its 1024 threads allow (it spilled), reads them from shared memory, two
-// rounds per 16-byte load (22 % faster than holding them).
+// rounds per 16-byte load (22 % faster than holding them); so does
+// slab_event_bits8, whose two Philox calls per position share each load.
 template <int DC, int DL, typename Fetch, typename FetchLink, typename Store>
 __device__ __forceinline__ void slab_sweeps(const BatchArgs &a, const BatchRun &d, const int4 *rec,
                                             const int32_t *cofs, const Quad &q, Fetch fetch,
@@ -502,7 +503,9 @@ __device__ __forceinline__ void slab_event(const BatchArgs &a, const BatchItem i
 // table expands a byte to the two quads' int8 spin words with one 8-byte shared
 // load; each position's record and each neighbour byte serve 8 walkers.  Slabs
 // are >= 8 walkers and runs a power of two >= 8 wide, so a byte's two quads lie
-// in one run.
+// in one run.  The round keys are read from shared memory (philox_pair_shared):
+// held in registers they took 20 of them and capped the CTA at 512 threads; at
+// 896 threads the 1024-instance uneven mix runs 4.6 % faster.
 template <int DC, int DL>
 __device__ __forceinline__ void slab_event_bits8(const BatchArgs &a, const BatchItem it, uint8_t *dsm) {
     const BatchRun d = a.runs[it.run];
@@ -550,20 +553,6 @@ __device__ __forceinline__ void slab_event_bits8(const BatchArgs &a, const Batch
         bits[i] = static_cast<uint8_t>(lo | (hi << 4));
     }
     __syncthreads();
-    // the run's round keys in per-thread registers (see slab_sweeps)
-    RoundKeys rk;
-#pragma unroll
-    for (int r = 0; r < 5; ++r) {
-        uint32_t z;
-        asm volatile("mov.u32 %0, %%laneid;" : "=r"(z));
-        z &= ~31u;
-        uint4 kk = s_keys[r];
-        rk.k0[2 * r] = kk.x ^ z;
-        rk.k1[2 * r] = kk.y ^ z;
-        rk.k0[2 * r + 1] = kk.z ^ z;
-        rk.k1[2 * r + 1] = kk.w ^ z;
-    }
-    const KeysConst keys{rk};
     const uint32_t c3 = (static_cast<uint32_t>(d.run) << 4) | kTagSweep;
     auto fetch8 = [&](int row) -> uint2 { return lut[bits[row * B + lane_b]]; };
     for (int t = 0; t < a.interval; ++t) {
@@ -587,9 +576,9 @@ __device__ __forceinline__ void slab_event_bits8(const BatchArgs &a, const Batch
                     yb[l] = w.y;
                 }
                 const uint32_t id = static_cast<uint32_t>(rc.pid());
-                const uint4 ra = keys(make_uint4(id, sweep, lq, c3));
+                uint4 ra = make_uint4(id, sweep, lq, c3), rb = make_uint4(id, sweep, lq + 1, c3);
+                philox_pair_shared(s_keys, ra, rb);
                 const uint32_t na = bits_of_word(decide4<DC, DL>(rc, qa, xa, ya, ra));
-                const uint4 rb = keys(make_uint4(id, sweep, lq + 1, c3));
                 const uint32_t nb = bits_of_word(decide4<DC, DL>(rc, qb, xb, yb, rb));
                 bits[pos * B + lane_b] = static_cast<uint8_t>(na | (nb << 4));
             }
@@ -673,7 +662,7 @@ __device__ __forceinline__ void slab_event_bits8(const BatchArgs &a, const Batch
 // Bit-packed slabs of runs with specialised records (one launch per event,
 // beside k_batch, which takes the int8 slabs).
 template <int DC, int DL>
-__global__ void __launch_bounds__(512, 1) k_batch_bits8(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchBits8Threads, 1) k_batch_bits8(BatchArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ int s_item;
     for (;;) {

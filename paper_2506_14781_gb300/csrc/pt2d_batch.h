@@ -81,9 +81,9 @@ inline int64_t batch_bits_bytes(int32_t n, int32_t sw) {
 cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state);
 cudaError_t launch_batch(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
 // Bit-packed slabs of runs with specialised records (DC = 3, 4 or 6): k_batch_bits8,
-// at most 512 threads per CTA.
+// at most kBatchBits8Threads threads per CTA.
 cudaError_t launch_batch_bits8(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
-constexpr int kBatchBits8Threads = 512;
+constexpr int kBatchBits8Threads = 896;
 // Most threads per CTA of the runtime-degree batch kernel.
 constexpr int kBatchGenericThreads = 768;
 

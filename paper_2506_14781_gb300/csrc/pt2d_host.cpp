@@ -326,17 +326,19 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
     if (mode == 2 && sw == 0) return PT2D_ERR_INVALID_ARG;
     int ql, threads, wpt = 4;
     if (bw) {
-        // a thread owns a byte of 8 walkers (k_sweep_bits8 / k_sweep_penalty_bits8,
-        // up to 512 threads), or a nibble of 4 when asked for or when more threads
-        // are asked for (k_sweep_bits / k_sweep_penalty_bits)
+        // a thread owns a byte of 8 walkers (k_sweep_bits8 / k_sweep_penalty_bits8),
+        // or a nibble of 4 when asked for or when more threads than those kernels
+        // take are asked for (k_sweep_bits / k_sweep_penalty_bits)
         const int req_t = opt ? opt->walkers_per_thread : 0;
         const int req_threads = opt ? opt->threads_per_cta : 0;
         if (req_t != 0 && req_t != 4 && req_t != 8) return PT2D_ERR_INVALID_ARG;
-        wpt = req_t ? req_t : (req_threads <= 512 ? 8 : 4);
+        // k_sweep_bits8 runs up to 896 threads at 72 registers (N = 800: 1.4 %
+        // faster than 640 threads, which were 5 % faster than 512)
+        const int tmax8 = specialised ? pt2d::kBits8Threads : pt2d::kPenaltyBits8Threads;
+        wpt = req_t ? req_t : (req_threads <= tmax8 ? 8 : 4);
         ql = bw / 4;
         const int lanes = bw / wpt;  // threads per spin row
-        // k_sweep_bits8 runs 640 threads at its 92 registers (20 warps, 5 % faster than 512)
-        const int tmax = wpt == 4 ? 1024 : (specialised ? 640 : 512);
+        const int tmax = wpt == 4 ? 1024 : tmax8;
         int32_t widest = 0;
         for (int32_t c = 0; c < C; ++c) widest = std::max(widest, pp.cofs[c + 1] - pp.cofs[c]);
         const int64_t want = (static_cast<int64_t>(widest) * lanes + 31) / 32 * 32;

@@ -103,6 +103,11 @@ struct SweepTiling {
     bool bits;           // slab bit-packed in shared memory (k_sweep_bits)
 };
 
+// Most threads per CTA of the byte-per-thread bit-packed sweep kernels: the
+// launch bounds the kernels are compiled with and the host's tiling limit.
+constexpr int kBits8Threads = 896;         // k_sweep_bits8: 72 registers, 28 warps
+constexpr int kPenaltyBits8Threads = 512;  // k_sweep_penalty_bits8
+
 // Dynamic shared memory of k_sweep_smem for n spins and a slab of W walkers.
 size_t smem_sweep_bytes(int32_t n, int walkers_per_cta);
 // Dynamic shared memory of k_sweep_bits (slab of bits plus the nibble table).

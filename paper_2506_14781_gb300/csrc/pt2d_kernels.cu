@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_bits(Layout L, Walkers wk, in
 // table expands a byte to both quads' int8 spin words with one 8-byte shared
 // load, so no nibble shift and no pair shuffle; the byte is written whole.
 template <int DC, int DL>
-__global__ void __launch_bounds__(640, 1) k_sweep_bits8(Layout L, Walkers wk, int sw_shift,
+__global__ void __launch_bounds__(kBits8Threads, 1) k_sweep_bits8(Layout L, Walkers wk, int sw_shift,
                                                         int32_t quads_per_run, RoundKeys rk,
                                                         uint32_t sweep0, int32_t nsweeps) {
     extern __shared__ __align__(16) uint8_t smb[];

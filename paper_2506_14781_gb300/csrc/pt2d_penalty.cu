@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_penalty_bits(Layout L, Walker
 // 256-entry table expands a byte to both quads' int8 spin words with one 8-byte
 // shared load; the byte is written whole (no shuffle).
 template <int DC, int DL>
-__global__ void __launch_bounds__(512, 1) k_sweep_penalty_bits8(Layout L, Walkers wk, int sw_shift,
+__global__ void __launch_bounds__(kPenaltyBits8Threads, 1) k_sweep_penalty_bits8(Layout L, Walkers wk, int sw_shift,
                                                                 int32_t quads_per_run, RoundKeys rk,
                                                                 uint32_t sweep0, int32_t nsweeps) {
     extern __shared__ __align__(16) uint8_t spb[];

@@ -33,6 +33,18 @@ struct KeysShared {
         return x;
     }
 };
+// Two Philox calls with one run's staged round keys, one 16-byte shared load
+// per two rounds serving both.
+__device__ __forceinline__ void philox_pair_shared(const uint4 *rk, uint4 &x, uint4 &y) {
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const uint4 kk = rk[r];
+        x = philox_round(x, kk.x, kk.y);
+        y = philox_round(y, kk.x, kk.y);
+        x = philox_round(x, kk.z, kk.w);
+        y = philox_round(y, kk.z, kk.w);
+    }
+}
 template <typename Keys>
 __device__ __forceinline__ Keys make_keys(const RoundKeys &rk, const uint4 *staged) {
     if constexpr (std::is_same_v<Keys, KeysShared>) {

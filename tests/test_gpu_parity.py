@@ -189,6 +189,7 @@ def test_tiny_config_bit_exact_full_length(pt, tiny_config):
     ("smem", 32, 768, 0), ("bits", 8, 32, 0),
     ("bits", 16, 64, 0), ("bits", 64, 1024, 0), ("bits", 128, 96, 0), ("bits", 8, 64, 4),
     ("bits", 16, 64, 4), ("bits", 64, 512, 8), ("bits", 128, 512, 8), ("bits", 8, 640, 8),
+    ("bits", 8, 896, 8), ("bits", 16, 832, 0),
     ("auto", 0, 0, 0)])
 def test_ragged_tiles_and_resume(pt, kernel, wpc, threads, wpt):
     inst = synth.wishart_planted(30, 0.5, 21)
