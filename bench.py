@@ -66,16 +66,16 @@ BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
 # DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only while the kernel sources hash to `src`; the summaries are under profiles/.
 PROFILED_TRAFFIC = {
-    ("n200", "k_sweep_smem"): dict(src="49db11e6661d236b", dram_bytes_per_launch=389_465_856,
+    ("n200", "k_sweep_smem"): dict(src="d485597d441c7b13", dram_bytes_per_launch=388_925_696,
                                    profile="profiles/k_sweep_smem_n200.md"),
     # captured at 4 of the 16 runs and scaled by the walkers
-    ("n800", "k_sweep_bits8"): dict(src="49db11e6661d236b", dram_bytes_per_launch=18_695_494_656,
+    ("n800", "k_sweep_bits8"): dict(src="d485597d441c7b13", dram_bytes_per_launch=13_982_807_040,
                                     profile="profiles/k_sweep_bits8_n800.md (4 runs x 4)"),
-    ("constrained", "k_sweep_penalty_smem"): dict(src="704df347ebd1e10c", dram_bytes_per_launch=341_058_304,
+    ("constrained", "k_sweep_penalty_smem"): dict(src="023b52c7df089d79", dram_bytes_per_launch=342_603_264,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
     # V = 40000 colouring: captured at 16 of the 64 runs and scaled by the walkers
-    ("constrained", "k_sweep_penalty_bits"): dict(src="704df347ebd1e10c", dram_bytes_per_launch=3_800_154_112,
-                                                  profile="profiles/k_sweep_penalty_bits_colouring40k.md (16 runs x 4)"),
+    ("constrained", "k_sweep_penalty_bits8"): dict(src="023b52c7df089d79", dram_bytes_per_launch=5_572_865_024,
+                                                   profile="profiles/k_sweep_penalty_bits8_colouring40k.md (16 runs x 4)"),
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h", "pt2d_wide.cuh")
 # kernels defined outside pt2d_kernels.cu hash their own file as well
