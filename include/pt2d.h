@@ -300,9 +300,10 @@ int pt2d_batch_remove(pt2d_batch *b, int64_t id);
 int pt2d_batch_run(pt2d_batch *b, int32_t events, int32_t swap_interval);
 
 /* Launch shape of a batch.  Every shape computes the same trajectories.
- *   threads_per_cta  128..1024, multiple of 32 (int8 slabs; bit-packed slabs
- *                    of specialised records run at most 512, and every slab of
- *                    the runtime-degree kernel at most 768)
+ *   threads_per_cta  128..1024, multiple of 32; the kernels run at most 768
+ *                    (int8 slabs of specialised records, 8 walkers a thread),
+ *                    896 (bit-packed slabs of specialised records) or 768
+ *                    (every slab of the runtime-degree kernel) of them
  *   storage          where a run's slab of spins lives during an event: 0 =
  *                    int8 in shared memory where it fits, else bit-packed in
  *                    shared memory where that fits, else int8 in global

@@ -15,7 +15,6 @@
 // seed and run index.  Events are chained by replaying launches from a CUDA
 // graph.
 #include <cstdint>
-#include <type_traits>
 
 #include "pt2d_batch.h"
 #include "pt2d_device.cuh"
@@ -123,72 +122,88 @@ __device__ void run_swap(const BatchArgs &a, const BatchRun &d, int run_index, u
     }
 }
 
-// The sweep block of one event for one slab (colour classes separated by
-// __syncthreads).  fetch(row) / fetch_link(row) give the quad's spin word of a
-// neighbour / copy-link row, store(pos, word) writes the new word.
-//
-// Where the run's ten Philox round keys live: the int8 slabs of specialised
-// records hold them in per-thread registers for the whole block (1 % faster than
-// reading them from shared memory at every use, which costs 3 %); the
-// runtime-degree kernel, whose wide records already need more registers than
-// its 1024 threads allow (it spilled), reads them from shared memory, two
-// rounds per 16-byte load (22 % faster than holding them); so does
-// slab_event_bits8, whose two Philox calls per position share each load.
+// The sweep block of one event for one slab of a runtime-degree run (wide
+// records, optional penalty terms; colour classes separated by __syncthreads).
+// fetch(row) / fetch_link(row) give the quad's spin word of a neighbour /
+// copy-link row, store(pos, word) writes the new word.  The run's ten Philox
+// round keys are read from shared memory, two rounds per 16-byte load: the
+// wide records already need more registers than the CTA allows, and holding
+// the keys too made the kernel spill (22 % slower).
 template <int DC, int DL, typename Fetch, typename FetchLink, typename Store>
 __device__ __forceinline__ void slab_sweeps(const BatchArgs &a, const BatchRun &d, const int4 *rec,
                                             const int32_t *cofs, const Quad &q, Fetch fetch,
                                             FetchLink fetch_link, Store store, int grp, int G,
                                             uint32_t lq, int64_t sweeps_done, const uint4 *round_keys) {
-    RoundKeys rk;
-    if constexpr (DC != 0) {
-#pragma unroll
-        for (int r = 0; r < 5; ++r) {
-            const uint4 kk = round_keys[r];
-            rk.k0[2 * r] = kk.x;
-            rk.k1[2 * r] = kk.y;
-            rk.k0[2 * r + 1] = kk.z;
-            rk.k1[2 * r + 1] = kk.w;
-        }
-    }
-    using Keys = std::conditional_t<DC == 0, KeysShared, KeysConst>;
-    const Keys keys = make_keys<Keys>(rk, round_keys);
+    static_assert(DC == 0, "specialised records take slab_sweeps8 or slab_event_bits8");
+    const KeysShared keys{round_keys};
     const uint32_t c3 = (static_cast<uint32_t>(d.run) << 4) | kTagSweep;
     for (int t = 0; t < a.interval; ++t) {
         const uint32_t sweep = static_cast<uint32_t>(sweeps_done + t);
         for (int c = 0; c < d.C; ++c) {
             const int beg = __ldg(cofs + c), end = __ldg(cofs + c + 1);
             for (int pos = beg + grp; pos < end; pos += G) {
-                if constexpr (DC == 0) {  // runtime degrees on wide records, optional penalty terms
-                    const int dc = d.dc, dl = d.dl;
-                    const int jo = wide_jpack_offset(dc, dl), ko = jo + dc / 2;
-                    const int *rc = reinterpret_cast<const int *>(rec) + static_cast<int64_t>(pos) * d.rec_vec * 4;
-                    int j0, j1, j2, j3;  // sum_k J_k s_k per walker
-                    wide_coupling_sums<true>(rc, dc, jo, fetch, j0, j1, j2, j3);
-                    const int h2 = __ldg(rc + dc + dl + 1);
-                    const int kk = d.penalty ? __ldg(rc + ko + dl) : 0;
-                    int l0 = kk, l1 = kk, l2 = kk, l3 = kk;
-                    for (int k = 0; k < dl; ++k) {
-                        const uint32_t y = fetch_link(__ldg(rc + dc + k));
-                        const int w = d.penalty ? __ldg(rc + ko + k) : 1;
-                        l0 += w * sbyte<0>(y);
-                        l1 += w * sbyte<1>(y);
-                        l2 += w * sbyte<2>(y);
-                        l3 += w * sbyte<3>(y);
-                    }
-                    const uint4 r = keys(make_uint4(static_cast<uint32_t>(__ldg(rc + dc + dl)), sweep, lq, c3));
-                    store(pos, decide_fields(q, h2 + 2 * j0 + q.p0 * l0, h2 + 2 * j1 + q.p1 * l1,
-                                             h2 + 2 * j2 + q.p2 * l2, h2 + 2 * j3 + q.p3 * l3, r));
-                } else {
-                    Rec<DC, DL> rc;
-                    rc.load(rec, pos);
-                    uint32_t x[DC], y[DL];
-#pragma unroll
-                    for (int k = 0; k < DC; ++k) x[k] = fetch(rc.nb(k));
-#pragma unroll
-                    for (int l = 0; l < DL; ++l) y[l] = fetch_link(rc.lk(l));
-                    const uint4 r = keys(make_uint4(static_cast<uint32_t>(rc.pid()), sweep, lq, c3));
-                    store(pos, decide4<DC, DL>(rc, q, x, y, r));
+                const int dc = d.dc, dl = d.dl;
+                const int jo = wide_jpack_offset(dc, dl), ko = jo + dc / 2;
+                const int *rc = reinterpret_cast<const int *>(rec) + static_cast<int64_t>(pos) * d.rec_vec * 4;
+                int j0, j1, j2, j3;  // sum_k J_k s_k per walker
+                wide_coupling_sums<true>(rc, dc, jo, fetch, j0, j1, j2, j3);
+                const int h2 = __ldg(rc + dc + dl + 1);
+                const int kk = d.penalty ? __ldg(rc + ko + dl) : 0;
+                int l0 = kk, l1 = kk, l2 = kk, l3 = kk;
+                for (int k = 0; k < dl; ++k) {
+                    const uint32_t y = fetch_link(__ldg(rc + dc + k));
+                    const int w = d.penalty ? __ldg(rc + ko + k) : 1;
+                    l0 += w * sbyte<0>(y);
+                    l1 += w * sbyte<1>(y);
+                    l2 += w * sbyte<2>(y);
+                    l3 += w * sbyte<3>(y);
                 }
+                const uint4 r = keys(make_uint4(static_cast<uint32_t>(__ldg(rc + dc + dl)), sweep, lq, c3));
+                store(pos, decide_fields(q, h2 + 2 * j0 + q.p0 * l0, h2 + 2 * j1 + q.p1 * l1,
+                                         h2 + 2 * j2 + q.p2 * l2, h2 + 2 * j3 + q.p3 * l3, r));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The sweep block of one event for one int8 slab of a run with specialised
+// records, 8 walkers (two quads) per thread: one 8-byte fetch per neighbour and
+// two Philox calls per position that share each shared-memory load of the
+// run's round keys (the scheme of k_sweep_smem with 8 walkers a thread; 5 %
+// faster than 4 walkers a thread with the keys held in registers, which took
+// 20 of the 64 registers 1024 threads allow and spilled).  A missing link
+// points at the slab's zero row.
+template <int DC, int DL, typename Fetch8, typename Store8>
+__device__ __forceinline__ void slab_sweeps8(const BatchArgs &a, const BatchRun &d, const int4 *rec,
+                                             const int32_t *cofs, const Quad &qa, const Quad &qb,
+                                             Fetch8 fetch8, Store8 store8, int grp, int G, uint32_t lq,
+                                             int64_t sweeps_done, const uint4 *round_keys) {
+    const uint32_t c3 = (static_cast<uint32_t>(d.run) << 4) | kTagSweep;
+    for (int t = 0; t < a.interval; ++t) {
+        const uint32_t sweep = static_cast<uint32_t>(sweeps_done + t);
+        for (int c = 0; c < d.C; ++c) {
+            const int beg = __ldg(cofs + c), end = __ldg(cofs + c + 1);
+            for (int pos = beg + grp; pos < end; pos += G) {
+                Rec<DC, DL> rc;
+                rc.load(rec, pos);
+                uint32_t xa[DC], xb[DC], ya[DL], yb[DL];
+#pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const uint2 w = fetch8(rc.nb(k));
+                    xa[k] = w.x;
+                    xb[k] = w.y;
+                }
+#pragma unroll
+                for (int l = 0; l < DL; ++l) {
+                    const uint2 w = fetch8(rc.lk(l));
+                    ya[l] = w.x;
+                    yb[l] = w.y;
+                }
+                const uint32_t id = static_cast<uint32_t>(rc.pid());
+                uint4 ra = make_uint4(id, sweep, lq, c3), rb = make_uint4(id, sweep, lq + 1, c3);
+                philox_pair_shared(round_keys, ra, rb);
+                store8(pos, make_uint2(decide4<DC, DL>(rc, qa, xa, ya, ra), decide4<DC, DL>(rc, qb, xb, yb, rb)));
             }
             __syncthreads();
         }
@@ -357,6 +372,79 @@ __device__ __forceinline__ void int8_slab(const BatchArgs &a, const BatchRun &d,
     slab_energies<DC, DL>(d, rec, fetch, grp, G, lane_off, s_F, s_G);
 }
 
+// int8_slab with 8 walkers (two quads) per thread, for runs with specialised
+// records: the same slab storage, loads, stores and initial state, the sweep
+// block of slab_sweeps8, and f and g per quad.
+template <int DC, int DL, bool SMEM>
+__device__ __forceinline__ void int8_slab8(const BatchArgs &a, const BatchRun &d, const int4 *rec,
+                                           const int32_t *cofs, const Quad &qa, const Quad &qb, int8_t *S_g,
+                                           int col0, int lane_off, int grp, int G, uint32_t lq, bool inited,
+                                           int64_t sweeps_done, const uint4 *keys, long long *s_F, int *s_G) {
+    extern __shared__ __align__(16) uint8_t batch_smem[];
+    const int n = d.n, SW = d.sw, QL = SW >> 2;
+    const int64_t Rp = d.Rp;
+    int8_t *const Sg = S_g + col0;
+    int8_t *const Ss = reinterpret_cast<int8_t *>(batch_smem);
+    // byte `byte` of the slab's row `row` (8-byte aligned for byte = lane_off:
+    // rows are SW >= 8 or Rp >= 16 bytes apart, the run's state 256-byte aligned)
+    auto at = [&](int row, int byte) -> int8_t * {
+        if constexpr (SMEM)
+            return Ss + row * SW + byte;
+        else
+            return Sg + row * Rp + byte;
+    };
+    if (!inited) {
+        const int64_t total = static_cast<int64_t>(n) * QL;
+        for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+            const int pos = static_cast<int>(e / QL);
+            const int qq = static_cast<int>(e - static_cast<int64_t>(pos) * QL);
+            *reinterpret_cast<uint32_t *>(at(pos, 4 * qq)) =
+                init_word<DC, DL>(d, rec, pos, static_cast<uint32_t>((col0 >> 2) + qq));
+        }
+        for (int i = threadIdx.x; i < SW / 4; i += blockDim.x) *reinterpret_cast<uint32_t *>(at(n, 4 * i)) = 0u;
+    } else if (SMEM) {
+        if (SW >= 16) {
+            const int vec = SW >> 4;
+            const int nvec = (n + 1) * vec;
+            for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+                const int row = i / vec;
+                const int part = i - row * vec;
+                reinterpret_cast<uint4 *>(Ss)[i] = *reinterpret_cast<const uint4 *>(Sg + row * Rp + 16 * part);
+            }
+        } else {  // 8-walker slabs: one 8-byte word per row
+            for (int row = threadIdx.x; row <= n; row += blockDim.x)
+                reinterpret_cast<uint2 *>(Ss)[row] = *reinterpret_cast<const uint2 *>(Sg + row * Rp);
+        }
+    }
+    __syncthreads();
+    auto fetch8 = [&](int row) -> uint2 { return *reinterpret_cast<const uint2 *>(at(row, lane_off)); };
+    auto store8 = [&](int pos, uint2 w) { *reinterpret_cast<uint2 *>(at(pos, lane_off)) = w; };
+    slab_sweeps8<DC, DL>(a, d, rec, cofs, qa, qb, fetch8, store8, grp, G, lq, sweeps_done, keys);
+    if (SMEM) {  // write the slab back (rows 0..n, the zero row included)
+        if (SW >= 16) {
+            const int vec = SW >> 4;
+            const int nvec = (n + 1) * vec;
+            for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+                const int row = i / vec;
+                const int part = i - row * vec;
+                *reinterpret_cast<uint4 *>(Sg + row * Rp + 16 * part) = reinterpret_cast<const uint4 *>(Ss)[i];
+            }
+        } else {
+            for (int row = threadIdx.x; row <= n; row += blockDim.x)
+                *reinterpret_cast<uint2 *>(Sg + row * Rp) = reinterpret_cast<const uint2 *>(Ss)[row];
+        }
+    }
+    for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+        s_F[i] = 0;
+        s_G[i] = 0;
+    }
+    __syncthreads();
+    auto fetch_a = [&](int row) -> uint32_t { return *reinterpret_cast<const uint32_t *>(at(row, lane_off)); };
+    auto fetch_b = [&](int row) -> uint32_t { return *reinterpret_cast<const uint32_t *>(at(row, lane_off + 4)); };
+    slab_energies<DC, DL>(d, rec, fetch_a, grp, G, lane_off, s_F, s_G);
+    slab_energies<DC, DL>(d, rec, fetch_b, grp, G, lane_off + 4, s_F, s_G);
+}
+
 // Beta and P of the current slots of walkers w0 .. w0 + 3 of a run (a quad).
 __device__ __forceinline__ Quad batch_quad(const uint8_t *pool, const BatchRun &d, int w0, bool inited) {
     const float kNegL2E = -1.4426950408889634f;
@@ -408,13 +496,54 @@ __device__ __forceinline__ void slab_finish(const BatchArgs &a, const BatchRun &
     }
 }
 
-// One event of one slab: sweeps, f and g, and the run's swap when this slab is
-// the last of its run to finish.  The slab's spins are int8 in global memory
-// (mode 0), int8 in shared memory (mode 1) or bit-packed in shared memory
-// (mode 2: one bit per walker, a thread owns a nibble, a 16-entry table
-// expands it to int8 spins, the two nibbles of a byte are merged by a shuffle).
+// One event of one int8 slab (shared or global memory) of a run with
+// specialised records, 8 walkers per thread: lanes = SW / 8 threads per spin
+// row, the thread's quads lq and lq + 1 of the run.
+template <int DC, int DL>
+__device__ __forceinline__ void slab_event_int8w8(const BatchArgs &a, const BatchItem it, uint8_t *dsm) {
+    const BatchRun d = a.runs[it.run];
+    uint8_t *pool = a.pool;
+    const int SW = d.sw;
+    const int lanes = SW >> 3;
+    const int lane = threadIdx.x & (lanes - 1);
+    const int grp = threadIdx.x / lanes;
+    const int G = blockDim.x / lanes;
+    const int col0 = it.slab * SW;   // first walker of the slab
+    const int lane_off = 8 * lane;   // within the slab
+    int8_t *S_g = reinterpret_cast<int8_t *>(pool + d.state);
+    const int4 *rec = reinterpret_cast<const int4 *>(pool + d.rec);
+    const int32_t *cofs = reinterpret_cast<const int32_t *>(pool + d.cofs);
+    const int64_t *sc = reinterpret_cast<const int64_t *>(pool + d.scalars);
+    const bool inited = sc[kScInited] != 0;
+    const int64_t sweeps_done = sc[kScSweeps];
+    const uint32_t lq = static_cast<uint32_t>((col0 >> 2) + 2 * lane);
+    const Quad qa = batch_quad(pool, d, col0 + lane_off, inited);
+    const Quad qb = batch_quad(pool, d, col0 + lane_off + 4, inited);
+    uint8_t *small = dsm + a.smem_state;
+    long long *s_F = reinterpret_cast<long long *>(small);
+    int *s_G = reinterpret_cast<int *>(s_F + kMaxR);
+    __shared__ uint4 s_keys8[5];  // the run's Philox round keys, visible after the next barrier
+    stage_round_keys(s_keys8, d.k0, d.k1);
+    if (d.mode == 1) {
+        int8_slab8<DC, DL, true>(a, d, rec, cofs, qa, qb, S_g, col0, lane_off, grp, G, lq, inited, sweeps_done,
+                                 s_keys8, s_F, s_G);
+    } else {
+        int8_slab8<DC, DL, false>(a, d, rec, cofs, qa, qb, S_g, col0, lane_off, grp, G, lq, inited, sweeps_done,
+                                  s_keys8, s_F, s_G);
+    }
+    slab_finish<DC, DL>(a, d, it, small, s_F, s_G);
+}
+
+// One event of one slab of a runtime-degree run: sweeps, f and g, and the run's
+// swap when this slab is the last of its run to finish.  The slab's spins are
+// int8 in global memory (mode 0), int8 in shared memory (mode 1) or bit-packed
+// in shared memory (mode 2: one bit per walker, a thread owns a nibble, a
+// 16-entry table expands it to int8 spins, the two nibbles of a byte are merged
+// by a shuffle).  Runs with specialised records take slab_event_int8w8 and
+// slab_event_bits8.
 template <int DC, int DL>
 __device__ __forceinline__ void slab_event(const BatchArgs &a, const BatchItem it, uint8_t *dsm) {
+    static_assert(DC == 0, "specialised records take slab_event_int8w8 or slab_event_bits8");
     const BatchRun d = a.runs[it.run];
     uint8_t *pool = a.pool;
     const int n = d.n, Rp = d.Rp;
@@ -440,7 +569,7 @@ __device__ __forceinline__ void slab_event(const BatchArgs &a, const BatchItem i
     __shared__ uint4 s_keys[5];  // the run's Philox round keys, visible after the next barrier
     stage_round_keys(s_keys, d.k0, d.k1);
 
-    if (DC == 0 && d.mode == 2) {  // specialised records: bit-packed slabs go to k_batch_bits8
+    if (d.mode == 2) {
         const int B = SW >> 3;
         const int byte_lane = lane_q >> 1;
         const int nib_shift = (lane_q & 1) * 4;
@@ -676,10 +805,10 @@ __global__ void __launch_bounds__(kBatchBits8Threads, 1) k_batch_bits8(BatchArgs
 }
 
 // The runtime-degree instantiation (DC = 0) runs at most 768 threads: at 80
-// registers it needs no spills and is 5 % faster than at 1024 threads (64);
-// the specialised ones are faster at 1024 threads.
+// registers it needs no spills and is 5 % faster than at 1024 threads (64).
+// The specialised ones take 8 walkers a thread at up to kBatchInt8Threads.
 template <int DC, int DL>
-__global__ void __launch_bounds__(DC == 0 ? kBatchGenericThreads : 1024, 1) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(DC == 0 ? kBatchGenericThreads : kBatchInt8Threads, 1) k_batch(BatchArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ int s_item;
     for (;;) {
@@ -688,7 +817,11 @@ __global__ void __launch_bounds__(DC == 0 ? kBatchGenericThreads : 1024, 1) k_ba
         __syncthreads();
         const int item = s_item;
         if (item >= a.n_items) break;
-        slab_event<DC, DL>(a, a.items[item], dsm);
+        if constexpr (DC == 0) {
+            slab_event<DC, DL>(a, a.items[item], dsm);
+        } else {
+            slab_event_int8w8<DC, DL>(a, a.items[item], dsm);
+        }
     }
 }
 

@@ -86,5 +86,7 @@ cudaError_t launch_batch_bits8(const BatchArgs &a, int DC, int DL, int grid, int
 constexpr int kBatchBits8Threads = 896;
 // Most threads per CTA of the runtime-degree batch kernel.
 constexpr int kBatchGenericThreads = 768;
+// Most threads per CTA of the specialised int8 batch kernel (8 walkers a thread).
+constexpr int kBatchInt8Threads = 768;
 
 }  // namespace pt2d

@@ -333,7 +333,7 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
     const int grid = std::min(b->grid, b->n_items);
     const int grid8 = std::min(b->grid, b->n_items_bits8);
     const int threads8 = std::min(b->threads, pt2d::kBatchBits8Threads);
-    const int threads = b->generic ? std::min(b->threads, pt2d::kBatchGenericThreads) : b->threads;
+    const int threads = std::min(b->threads, b->generic ? pt2d::kBatchGenericThreads : pt2d::kBatchInt8Threads);
     const int kdc = b->generic ? 0 : b->DC;
     if (grid > 0) BK(b, pt2d::batch_kernel_attributes(kdc, 2, b->smem_state));
     // per event: the counters are cleared, then every slab of every run

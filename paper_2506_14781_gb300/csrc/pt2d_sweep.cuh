@@ -4,7 +4,6 @@
 #pragma once
 
 #include <cstdint>
-#include <type_traits>
 
 #include "pt2d_device.cuh"
 #include "pt2d_internal.h"
@@ -12,15 +11,14 @@
 
 namespace pt2d {
 
-// Philox key source of the sweep loops: the ten round keys, held as kernel
-// parameters (one seed per launch) or in per-thread registers (the batch, a
-// seed per run).
+// Philox key source of the plain sweep loops: the ten round keys as kernel
+// parameters (one seed per launch, read from constant memory).
 struct KeysConst {
     RoundKeys rk;
     __device__ __forceinline__ uint4 operator()(uint4 x) const { return philox4x32_10(x, rk); }
 };
 // Round keys read from shared memory at every use, two rounds per 16-byte load
-// (a run's keys staged by stage_round_keys).
+// (a run's keys staged by stage_round_keys; the batched kernels, a seed per run).
 struct KeysShared {
     const uint4 *rk;
     __device__ __forceinline__ uint4 operator()(uint4 x) const {
@@ -43,14 +41,6 @@ __device__ __forceinline__ void philox_pair_shared(const uint4 *rk, uint4 &x, ui
         y = philox_round(y, kk.x, kk.y);
         x = philox_round(x, kk.z, kk.w);
         y = philox_round(y, kk.z, kk.w);
-    }
-}
-template <typename Keys>
-__device__ __forceinline__ Keys make_keys(const RoundKeys &rk, const uint4 *staged) {
-    if constexpr (std::is_same_v<Keys, KeysShared>) {
-        return KeysShared{staged};
-    } else {
-        return KeysConst{rk};
     }
 }
 // A run's round keys staged in shared memory, two rounds per 16-byte word:
