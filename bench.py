@@ -673,7 +673,7 @@ def leg_ground_state(pt, args, stream, dev):
     probs = ground_state_problems(args.gs_ns, args.gs_instances)
     degree = max(64, max(int(np.diff(p[1].cp_ptr).max()) for p in probs))
     out = batched_vs_plain(pt, probs, 50, batched_events=args.gs_timed_events,
-                           plain_events=args.plain_events, tts_events=args.gs_events, autotune=False,
+                           plain_events=args.plain_events, tts_events=args.gs_events, autotune=True,
                            max_degree=degree, stream=stream, dev=dev, chunk=100)
     per = out["per_problem_sweeps"]["planted"]
     out = _strip(out)

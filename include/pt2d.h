@@ -327,11 +327,11 @@ typedef struct pt2d_batch_shape {
 int pt2d_batch_get_shape(const pt2d_batch *b, pt2d_batch_shape *shape);
 int pt2d_batch_set_shape(pt2d_batch *b, const pt2d_batch_shape *shape);
 
-/* Time candidate launch shapes (storage 0, 1 or 2 x balance 0, 2, 4 or 8 at 1024
- * threads, then the best of those at 512 threads) on two launches of `events`
- * events each and keep the fastest, returned in *chosen (may be NULL).  The
- * trial launches advance the chains like pt2d_batch_run.  Errors as
- * pt2d_batch_run. */
+/* Time candidate launch shapes (storage 0, 1 or 2 x balance 0, 2, 4 or 8 at
+ * 1024 threads, then the best of those at 512, 256 and 128 threads) on two
+ * launches of `events` events each and keep the fastest, returned in *chosen
+ * (may be NULL).  The trial launches advance the chains like pt2d_batch_run.
+ * Errors as pt2d_batch_run. */
 int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval,
                         pt2d_batch_shape *chosen);
 

@@ -839,7 +839,34 @@ cudaError_t launch_bits8_variant(const BatchArgs &a, int grid, int threads, size
     return cudaGetLastError();
 }
 
+template <auto kernel>
+int blocks_per_sm(int threads, size_t smem) {
+    if (allow_max_dynamic_smem<kernel>() != cudaSuccess) return 1;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
 }  // namespace
+
+int batch_blocks_per_sm(int DC, int DL, bool bits8, int threads, int smem_state) {
+    const size_t smem = static_cast<size_t>(smem_state) + batch_small_smem_bytes();
+    if (DL != 2) return 1;
+    if (bits8) {
+        if (DC == 3) return blocks_per_sm<k_batch_bits8<3, 2>>(threads, smem);
+        if (DC == 4) return blocks_per_sm<k_batch_bits8<4, 2>>(threads, smem);
+        if (DC == 6) return blocks_per_sm<k_batch_bits8<6, 2>>(threads, smem);
+        return 1;
+    }
+    if (DC == 0) return blocks_per_sm<k_batch<0, 0>>(threads, smem);
+    if (DC == 3) return blocks_per_sm<k_batch<3, 2>>(threads, smem);
+    if (DC == 4) return blocks_per_sm<k_batch<4, 2>>(threads, smem);
+    if (DC == 6) return blocks_per_sm<k_batch<6, 2>>(threads, smem);
+    return 1;
+}
 
 size_t batch_small_smem_bytes() {
     return static_cast<size_t>(kMaxR) * (4 + 8 + 4 + 4 + 4);

@@ -80,6 +80,9 @@ inline int64_t batch_bits_bytes(int32_t n, int32_t sw) {
 // from each run's descriptor).
 cudaError_t batch_kernel_attributes(int DC, int DL, int smem_state);
 cudaError_t launch_batch(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);
+// CTAs of k_batch (bits8 false) or k_batch_bits8 that fit on one SM at `threads`
+// threads with `smem_state` bytes of slab shared memory (at least 1).
+int batch_blocks_per_sm(int DC, int DL, bool bits8, int threads, int smem_state);
 // Bit-packed slabs of runs with specialised records (DC = 3, 4 or 6): k_batch_bits8,
 // at most kBatchBits8Threads threads per CTA.
 cudaError_t launch_batch_bits8(const BatchArgs &a, int DC, int DL, int grid, int threads, cudaStream_t st);

@@ -160,6 +160,7 @@ struct pt2d_batch {
     std::vector<std::pair<int64_t, int32_t>> order;  // run array order: (id, run)
     int32_t n_items = 0;                              // slabs for k_batch (d_items[0 .. n_items))
     int32_t n_items_bits8 = 0;                        // bit-packed slabs for k_batch_bits8, after them
+    int state_int8 = 0, state_bits8 = 0;              // slab shared memory the two lists need
     int glob_sw = 32;                                 // slab width when spins stay in global memory
     int swap_mode = 0;                                // PT2D_SWAP_2D or PT2D_SWAP_JCOLUMN, all problems
     bool generic = false;                             // runtime-degree kernel
@@ -303,6 +304,20 @@ int upload_descriptors(pt2d_batch *b) {
         n_bits8 += bits8(perm[k]) ? 1 : 0;
     }
     items.swap(sorted);
+    // shared memory of the largest slab of each list: a batch of small problems
+    // launches with less than the maximum, so several CTAs share an SM
+    int64_t need_int8 = 0, need_bits8 = 0;
+    for (size_t k = 0; k < items.size(); ++k) {
+        const pt2d::BatchRun &r = all[items[k].run];
+        if (k >= items.size() - n_bits8)
+            need_bits8 = std::max(need_bits8, pt2d::batch_bits_bytes(r.n, r.sw));
+        else if (r.mode == 1)
+            need_int8 = std::max(need_int8, static_cast<int64_t>(r.n + 1) * r.sw);
+        else if (r.mode == 2)
+            need_int8 = std::max(need_int8, pt2d::batch_bits_bytes(r.n, r.sw));
+    }
+    b->state_int8 = static_cast<int>((need_int8 + 15) & ~int64_t{15});
+    b->state_bits8 = static_cast<int>((need_bits8 + 15) & ~int64_t{15});
     if (!all.empty()) {
         BK(b, cudaMemcpyAsync(b->d_runs, all.data(), sizeof(pt2d::BatchRun) * all.size(),
                               cudaMemcpyHostToDevice, b->stream));
@@ -327,15 +342,20 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
     // k_batch_bits8 the bit-packed slabs of specialised records; each has its
     // own work counter
     pt2d::BatchArgs a{b->pool, b->d_runs, b->d_items, b->n_runs, b->n_items, b->d_queue, interval,
-                      b->smem_state, b->d_status};
+                      b->state_int8, b->d_status};
     pt2d::BatchArgs a8{b->pool, b->d_runs, b->d_items + b->n_items, b->n_runs, b->n_items_bits8,
-                       b->d_queue + 1, interval, b->smem_state, b->d_status};
-    const int grid = std::min(b->grid, b->n_items);
-    const int grid8 = std::min(b->grid, b->n_items_bits8);
+                       b->d_queue + 1, interval, b->state_bits8, b->d_status};
     const int threads8 = std::min(b->threads, pt2d::kBatchBits8Threads);
     const int threads = std::min(b->threads, b->generic ? pt2d::kBatchGenericThreads : pt2d::kBatchInt8Threads);
     const int kdc = b->generic ? 0 : b->DC;
-    if (grid > 0) BK(b, pt2d::batch_kernel_attributes(kdc, 2, b->smem_state));
+    // persistent CTAs: as many as fit on the SMs at once, no more than the slabs
+    const int per_sm = b->n_items > 0 ? pt2d::batch_blocks_per_sm(kdc, 2, false, threads, b->state_int8) : 1;
+    const int per_sm8 =
+        b->n_items_bits8 > 0 ? pt2d::batch_blocks_per_sm(kdc, 2, true, threads8, b->state_bits8) : 1;
+    const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(b->grid) * per_sm, b->n_items));
+    const int grid8 =
+        static_cast<int>(std::min<int64_t>(static_cast<int64_t>(b->grid) * per_sm8, b->n_items_bits8));
+    if (grid > 0) BK(b, pt2d::batch_kernel_attributes(kdc, 2, b->state_int8));
     // per event: the counters are cleared, then every slab of every run
     auto enqueue = [&]() -> cudaError_t {
         for (int32_t e = 0; e < events; ++e) {
@@ -673,9 +693,12 @@ int pt2d_batch_autotune(pt2d_batch *b, int32_t events, int32_t swap_interval, pt
             sh.balance = balance;
             if (int st = trial(sh)) return st;
         }
-    {
-        pt2d_batch_shape sh = best;
-        sh.threads_per_cta = 512;
+    // fewer threads per CTA: batches of small problems then fit several CTAs
+    // (several slabs at once) on an SM
+    const pt2d_batch_shape wide = best;
+    for (int threads : {512, 256, 128}) {
+        pt2d_batch_shape sh = wide;
+        sh.threads_per_cta = threads;
         if (int st = trial(sh)) return st;
     }
     apply_shape(b, best);

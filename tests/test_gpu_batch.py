@@ -178,7 +178,7 @@ def test_batch_pool_full_and_autotune(pt):
     with pytest.raises(pt.PoolFull):
         batch.add(a["phys"], a["beta"], a["P"], 1, a["seed"] + 2, a["target"])
     shape = batch.autotune(2, 3)  # every trial launch advances the chains
-    assert shape["threads_per_cta"] in (512, 1024) and shape == batch.shape
+    assert shape["threads_per_cta"] in (128, 256, 512, 1024) and shape == batch.shape
     batch.run(2, 3)
     sweeps = int(batch.read(i1, pt.COUNTERS)[0])
     assert sweeps % 6 == 0 and sweeps >= 5 * 2 * 3
