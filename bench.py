@@ -66,15 +66,15 @@ BYTES_PER_UPDATE = 2.0 + 40.0 / 128.0
 # DRAM bytes per sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only while the kernel sources hash to `src`; the summaries are under profiles/.
 PROFILED_TRAFFIC = {
-    ("n200", "k_sweep_smem"): dict(src="d485597d441c7b13", dram_bytes_per_launch=388_925_696,
+    ("n200", "k_sweep_smem"): dict(src="d9fe13f0f233316c", dram_bytes_per_launch=389_639_680,
                                    profile="profiles/k_sweep_smem_n200.md"),
     # captured at 4 of the 16 runs and scaled by the walkers
-    ("n800", "k_sweep_bits8"): dict(src="d485597d441c7b13", dram_bytes_per_launch=13_982_807_040,
+    ("n800", "k_sweep_bits8"): dict(src="d9fe13f0f233316c", dram_bytes_per_launch=14_168_667_136,
                                     profile="profiles/k_sweep_bits8_n800.md (4 runs x 4)"),
-    ("constrained", "k_sweep_penalty_smem"): dict(src="023b52c7df089d79", dram_bytes_per_launch=342_603_264,
+    ("constrained", "k_sweep_penalty_smem"): dict(src="abe90108dc60f7eb", dram_bytes_per_launch=342_726_144,
                                                   profile="profiles/k_sweep_penalty_smem_colouring.md"),
     # V = 40000 colouring: captured at 16 of the 64 runs and scaled by the walkers
-    ("constrained", "k_sweep_penalty_bits8"): dict(src="023b52c7df089d79", dram_bytes_per_launch=5_572_865_024,
+    ("constrained", "k_sweep_penalty_bits8"): dict(src="abe90108dc60f7eb", dram_bytes_per_launch=5_691_546_624,
                                                    profile="profiles/k_sweep_penalty_bits8_colouring40k.md (16 runs x 4)"),
 }
 KERNEL_SOURCES = ("pt2d_kernels.cu", "pt2d_sweep.cuh", "pt2d_device.cuh", "pt2d_internal.h", "pt2d_wide.cuh")
@@ -734,7 +734,7 @@ def run_batched(args):
     line["roofline"] = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tops/s (lane-ops)",
                         "frac": alu / alu_peak, "traffic": None, "kernel": "k_batch",
                         "ops_per_update": OPS_PER_UPDATE,
-                        "traffic_source": "profiles/k_batch_uneven128.md (128-instance capture, not scaled)",
+                        "traffic_source": "profiles/k_batch_uneven137.md (137-instance capture, not scaled)",
                         "peak_source": f"{sm_count} SMs x 128 lanes x max clock ({peak_src})"}
     print(json.dumps(line))
 
