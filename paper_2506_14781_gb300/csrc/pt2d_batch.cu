@@ -4,7 +4,8 @@
 // One launch advances every run by one swap event of Algorithm 1.  A run's
 // replicas are split into slabs (a power-of-two number of walkers, the whole
 // run when it fits in shared memory); a slab of one run is the unit of work.
-// CTAs take slabs from an atomic counter over a list sorted by decreasing run
+// Persistent CTAs (as many as fit on the SMs at the launch's shared memory)
+// take slabs from an atomic counter over a list sorted by decreasing run
 // size and, for their slab, perform the sweep block of the event (colour
 // classes separated by __syncthreads, the slab's spins in shared memory when
 // they fit) and f and g of the final sweep.  The CTA that completes the last
