@@ -1307,9 +1307,12 @@ def _serve_load(pt, synth, pool, stop, rate, max_sweeps, interval, args):
             time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
     wall = time.perf_counter() - t0
     lat, wait, service, rho, solved_lat, solved, done, updates = [], [], [], [], [], 0, 0, 0
+    executed = 0  # sweeps of every admitted request, finished or still resident at the end
     for rid, k in ids:
         st = srv.status(rid)
         inst, phys = pool[k][0], pool[k][1]
+        if st["state"] in ("done", "running"):
+            executed += phys.n * 128 * st["sweeps_done"]
         if st["state"] == "done":
             done += 1
             lat.append(st["t_done"] - st["t_submit"])
@@ -1335,6 +1338,7 @@ def _serve_load(pt, synth, pool, stop, rate, max_sweeps, interval, args):
         "solves_per_s": solved / wall, "completed_per_s": done / wall,
         "completed_per_min": 60.0 * done / wall,
         "spin_updates_per_s_completed": updates / wall,
+        "spin_updates_per_s_executed": executed / wall,
         "median_best_residual_per_spin": pct(rho, 50),
         "resident_peak": int(peak_active), "memory_admitted_peak_bytes": int(peak_used),
         "pool_bytes": int(pool_bytes),

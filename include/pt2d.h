@@ -389,10 +389,13 @@ int pt2d_server_create(pt2d_server **out, size_t pool_bytes, int32_t max_couplin
                        int32_t max_requests, int32_t swap_interval, int32_t events_per_step,
                        const pt2d_options *opt);
 
-/* Queue a request (the problem is copied).  Errors: INVALID_ARG (invalid
- * problem, or one a batch cannot hold: general penalty terms, I * J > 128, a
- * coupling degree above the server's), OOM (larger than the whole pool, so it
- * could never be admitted). */
+/* Queue a request (the problem is copied).  Errors: INVALID_ARG (bad
+ * arguments, or a problem a batch cannot hold: general penalty terms,
+ * I * J > 128, a coupling degree above the server's), OOM (larger than the
+ * whole pool, so it could never be admitted).  The rest of the problem's
+ * validation (a symmetric CSR without self loops or duplicates, the local-field
+ * bound) happens at admission: a problem that fails it ends FAILED with
+ * INVALID_ARG in its status.  Submission costs O(n) plus a copy of the arrays. */
 int pt2d_server_submit(pt2d_server *s, const pt2d_instance *inst, int32_t I, const float *beta,
                        int32_t J, const int32_t *P, uint64_t seed, int64_t target,
                        int64_t max_sweeps, int64_t *request_id);

@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/pt2d.h"
+
 namespace pt2d {
 
 constexpr int kBatchMaxReplicas = 128;  // I * J of one run, padded to a power of two
@@ -91,5 +93,13 @@ constexpr int kBatchBits8Threads = 896;
 constexpr int kBatchGenericThreads = 768;
 // Most threads per CTA of the specialised int8 batch kernel (8 walkers a thread).
 constexpr int kBatchInt8Threads = 768;
+
+// Bounds on pt2d_batch_instance_bytes from the degrees alone (no colouring and
+// no check of the CSR, so O(n) plus a scan of the penalty terms): the sizes
+// with 1 and with max degree + 1 colours, equal unless the colour offsets
+// outgrow their 256-byte block.  Errors: INVALID_ARG (arguments, or a problem
+// the batch cannot hold: degrees, penalty terms).
+int batch_instance_bytes_bounds(const pt2d_batch *b, const pt2d_instance *inst, int32_t I, int32_t J,
+                                int32_t runs, size_t *lo, size_t *hi);
 
 }  // namespace pt2d

@@ -16,6 +16,7 @@
 #include "pt2d_batch.h"
 #include "pt2d_prep.h"
 #include "pt2d_trace.h"
+#include "pt2d_wide.cuh"
 
 namespace {
 
@@ -398,6 +399,49 @@ int launch(pt2d_batch *b, int32_t events, int32_t interval) {
 }
 
 }  // namespace
+
+namespace pt2d {
+
+int batch_instance_bytes_bounds(const pt2d_batch *b, const pt2d_instance *inst, int32_t I, int32_t J,
+                                int32_t runs, size_t *lo, size_t *hi) {
+    if (!b || !inst || !lo || !hi || inst->n < 1 || I < 1 || J < 1 || runs < 1 ||
+        I * J > pt2d::kBatchMaxReplicas || !inst->cp_ptr || !inst->lk_ptr)
+        return PT2D_ERR_INVALID_ARG;
+    const int32_t n = inst->n;
+    if (inst->cp_ptr[0] != 0 || inst->lk_ptr[0] != 0) return PT2D_ERR_INVALID_ARG;
+    int32_t dcmax = 0, dlmax = 0, degmax = 0;
+    for (int32_t a = 0; a < n; ++a) {
+        const int32_t dc = inst->cp_ptr[a + 1] - inst->cp_ptr[a], dl = inst->lk_ptr[a + 1] - inst->lk_ptr[a];
+        if (dc < 0 || dl < 0) return PT2D_ERR_INVALID_ARG;
+        dcmax = std::max(dcmax, dc);
+        dlmax = std::max(dlmax, dl);
+        degmax = std::max(degmax, dc + dl);
+    }
+    if ((inst->cp_ptr[n] > 0 && (!inst->cp_col || !inst->cp_J)) || (inst->lk_ptr[n] > 0 && !inst->lk_col))
+        return PT2D_ERR_INVALID_ARG;
+    bool penalty = false;
+    if (inst->lk_w)
+        for (int32_t k = 0; k < inst->lk_ptr[n] && !penalty; ++k) penalty = inst->lk_w[k] != 1;
+    if (inst->hk)
+        for (int32_t a = 0; a < n && !penalty; ++a) penalty = inst->hk[a] != 0;
+    int32_t rec_ints;
+    if (b->generic) {  // the wide layout (prepare with force_dc < 0), within the declared degree
+        if (dcmax > std::max(b->DC, 6)) return PT2D_ERR_INVALID_ARG;
+        const int32_t DC = std::max<int32_t>(4, (dcmax + 3) / 4 * 4);
+        rec_ints = pt2d::wide_record_ints(DC, dlmax, penalty);
+    } else {  // the batch's specialised layout (prepare with force_dc = b->DC)
+        if (penalty || inst->g0 != 0 || dlmax > 2 || dcmax > b->DC) return PT2D_ERR_INVALID_ARG;
+        rec_ints = 2 * b->DC + 2 + 2;
+    }
+    const int32_t rec_vec = (rec_ints + 3) / 4;
+    const int32_t R = I * J, Rp = pow2_at_least(R);
+    // greedy colouring uses between 1 and degmax + 1 colours
+    *lo = align_up(block_layout(n, 1, rec_vec, I, J, R, Rp, runs, b->trace_cap).total);
+    *hi = align_up(block_layout(n, degmax + 1, rec_vec, I, J, R, Rp, runs, b->trace_cap).total);
+    return PT2D_OK;
+}
+
+}  // namespace pt2d
 
 extern "C" {
 

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/pt2d.h"
+#include "pt2d_batch.h"
 #include "pt2d_trace.h"
 
 namespace {
@@ -142,9 +143,18 @@ int pt2d_server_submit(pt2d_server *s, const pt2d_instance *inst, int32_t I, con
     if (!s || !inst || !beta || !P || !request_id || inst->n < 1 || I < 1 || J < 1 || max_sweeps < 1 ||
         !inst->cp_ptr || !inst->lk_ptr)
         return PT2D_ERR_INVALID_ARG;
-    const size_t need = pt2d_batch_instance_bytes(s->b, inst, I, J, 1);
-    if (need == 0) return PT2D_ERR_INVALID_ARG;
-    if (need > s->capacity) return PT2D_ERR_OOM;  // would block the FIFO head for ever
+    // Size from the degrees alone (no colouring, no CSR check: a submission
+    // costs O(n) here, so a stream of submissions does not starve the step
+    // loop); the exact size only when the bounds straddle the pool.  A problem
+    // larger than the pool would block the FIFO head for ever.
+    size_t lo = 0, hi = 0;
+    if (int st = pt2d::batch_instance_bytes_bounds(s->b, inst, I, J, 1, &lo, &hi)) return st;
+    if (lo > s->capacity) return PT2D_ERR_OOM;
+    if (hi > s->capacity) {
+        const size_t need = pt2d_batch_instance_bytes(s->b, inst, I, J, 1);
+        if (need == 0) return PT2D_ERR_INVALID_ARG;
+        if (need > s->capacity) return PT2D_ERR_OOM;
+    }
     Request r;
     const int32_t n = inst->n;
     r.n = n;

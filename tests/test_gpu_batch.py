@@ -254,12 +254,12 @@ def _penalty_problem(pt, n, groups, seed, I, J):
     return dict(phys=phys, beta=beta, P=P, runs=1, seed=seed, target=-10 ** 6)
 
 
-@pytest.mark.parametrize("kernel", ["auto", "global", "bits"])
-def test_runtime_degree_batch_matches_plain(pt, kernel):
+@pytest.mark.parametrize("kernel,threads", [("auto", 0), ("global", 0), ("bits", 0), ("auto", 128)])
+def test_runtime_degree_batch_matches_plain(pt, kernel, threads):
     """A batch declared with a coupling degree above 6 runs every problem on the
     runtime-degree kernel: three copies per node (~N/3 couplings per copy),
     one-hot penalty terms and ordinary <= 3-edge chains together, each equal to
-    its plain context."""
+    its plain context (at 128 threads per CTA several CTAs share an SM)."""
     probs = [
         _problem(pt, 30, 0.75, 41, ("fixed", 3), 8, 4, 2),
         _problem(pt, 45, 0.5, 42, ("fixed", 3), 16, 8, 1),
@@ -267,7 +267,8 @@ def test_runtime_degree_batch_matches_plain(pt, kernel):
         _penalty_problem(pt, 40, [list(range(k, k + 5)) for k in range(0, 40, 5)], 44, 8, 4),
         _penalty_problem(pt, 24, [[0, 1, 2], [3, 4, 5], [2, 6, 9, 12]], 45, 4, 4),
     ]
-    batch = pt.Batch(1 << 28, max_coupling_degree=64, max_runs=16, trace_capacity=16, sweep_kernel=kernel)
+    batch = pt.Batch(1 << 28, max_coupling_degree=64, max_runs=16, trace_capacity=16, sweep_kernel=kernel,
+                     threads_per_cta=threads)
     ids = [batch.add(p["phys"], p["beta"], p["P"], p["runs"], p["seed"], p["target"]) for p in probs]
     batch.run(3, 5)
     batch.run(4, 5)

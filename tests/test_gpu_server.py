@@ -137,6 +137,24 @@ def test_submit_rejects_what_can_never_run(pt):
     srv.close()
 
 
+def test_malformed_problem_fails_at_admission(pt):
+    """Submission checks only the degrees and the size; a CSR that is not
+    symmetric is caught when the request is admitted: it ends FAILED with
+    INVALID_ARG, and the requests around it run to completion."""
+    reqs = _requests(pt)
+    srv = pt.Server(1 << 28, 3, 8, INTERVAL, EVENTS_PER_STEP)
+    bad = pt.PhysicalInstance(4, np.array([0, 1, 1, 1, 1], np.int32), np.array([1], np.int32),
+                              np.array([5], np.int16), np.zeros(5, np.int32), np.zeros(0, np.int32))
+    before = srv.submit(reqs[0]["phys"], reqs[0]["beta"], reqs[0]["P"], 1, reqs[0]["target"], 40)
+    rid = srv.submit(bad, reqs[0]["beta"], reqs[0]["P"], 2, 0, 40)
+    after = srv.submit(reqs[1]["phys"], reqs[1]["beta"], reqs[1]["P"], 3, reqs[1]["target"], 40)
+    assert srv.status(rid)["state"] == "queued"
+    _drain(srv, [before, after])
+    st = srv.status(rid)
+    assert st["state"] == "failed" and st["error"] == -1  # PT2D_ERR_INVALID_ARG
+    srv.close()
+
+
 def test_requests_in_a_mix_match_the_oracle(pt):
     """Requests served in a mix (arrivals while others run, a pool that holds
     only some of them) give the oracle's result for the same instance, ladders
