@@ -360,8 +360,15 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         int32_t widest = 0;
         for (int32_t c = 0; c < C; ++c) widest = std::max(widest, pp.cofs[c + 1] - pp.cofs[c]);
         const int64_t want = (static_cast<int64_t>(widest) * lanes + 31) / 32 * 32;
+        // the runtime-degree kernel (wide records) runs small CTAs: its colour
+        // classes are short (three copies per node, N = 50 / 100 / 200: 4 or 5
+        // classes of <= 200 spins), so a 1024-thread CTA waits at the class
+        // barriers; at 256 threads several CTAs share an SM (N = 100: 1.99 ms per
+        // launch against 2.29 ms; N = 50: 0.79 against 0.95; N = 200: 6.56 / 7.32)
+        const bool wide_kernel = !spec_layout && !pen_ok;
+        const int tauto = wide_kernel ? std::min(tmax, 256) : tmax;
         threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta
-                                                    : static_cast<int>(std::min<int64_t>(tmax, want));
+                                                    : static_cast<int>(std::min<int64_t>(tauto, want));
         if (threads < 32 || threads > tmax || threads % 32 || threads < lanes) return PT2D_ERR_INVALID_ARG;
     } else {
         if (opt && opt->walkers_per_thread != 0 && opt->walkers_per_thread != 4)
