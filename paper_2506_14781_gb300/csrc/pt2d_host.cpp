@@ -360,13 +360,20 @@ int prepare(const pt2d_instance *inst, int32_t I, const float *beta, int32_t J, 
         int32_t widest = 0;
         for (int32_t c = 0; c < C; ++c) widest = std::max(widest, pp.cofs[c + 1] - pp.cofs[c]);
         const int64_t want = (static_cast<int64_t>(widest) * lanes + 31) / 32 * 32;
-        // the runtime-degree kernel (wide records) runs small CTAs: its colour
-        // classes are short (three copies per node, N = 50 / 100 / 200: 4 or 5
-        // classes of <= 200 spins), so a 1024-thread CTA waits at the class
-        // barriers; at 256 threads several CTAs share an SM (N = 100: 1.99 ms per
-        // launch against 2.29 ms; N = 50: 0.79 against 0.95; N = 200: 6.56 / 7.32)
+        // the runtime-degree kernel (wide records) runs smaller CTAs when there
+        // are CTAs enough to put several on each SM: its colour classes are short
+        // (three copies per node, N = 50 / 100 / 200: 4 or 5 classes of <= 200
+        // spins), so a 1024-thread CTA waits at the class barriers, while CTAs
+        // sharing an SM overlap one another's barriers (400 CTAs, N = 100: 1.99 ms
+        // per launch at 256 threads against 2.06 at 320 and 2.29 at 1024; N = 50:
+        // 0.79 against 0.95; N = 200: 6.54 / 7.32).  With no more CTAs than SMs
+        // (one run of 400 replicas: 7) each keeps the full width.
         const bool wide_kernel = !spec_layout && !pen_ok;
-        const int tauto = wide_kernel ? std::min(tmax, 256) : tmax;
+        const int64_t ctas = (walkers + sw - 1) / sw;
+        const int64_t per_sm = (ctas + sms - 1) / sms;
+        const int tauto = wide_kernel && per_sm > 1
+                              ? static_cast<int>(std::max<int64_t>(256, (1024 / (per_sm + 1)) / 32 * 32))
+                              : tmax;
         threads = (opt && opt->threads_per_cta > 0) ? opt->threads_per_cta
                                                     : static_cast<int>(std::min<int64_t>(tauto, want));
         if (threads < 32 || threads > tmax || threads % 32 || threads < lanes) return PT2D_ERR_INVALID_ARG;
