@@ -405,7 +405,7 @@ namespace pt2d {
 int batch_instance_bytes_bounds(const pt2d_batch *b, const pt2d_instance *inst, int32_t I, int32_t J,
                                 int32_t runs, size_t *lo, size_t *hi) {
     if (!b || !inst || !lo || !hi || inst->n < 1 || I < 1 || J < 1 || runs < 1 ||
-        I * J > pt2d::kBatchMaxReplicas || !inst->cp_ptr || !inst->lk_ptr)
+        static_cast<int64_t>(I) * J > pt2d::kBatchMaxReplicas || !inst->cp_ptr || !inst->lk_ptr)
         return PT2D_ERR_INVALID_ARG;
     const int32_t n = inst->n;
     if (inst->cp_ptr[0] != 0 || inst->lk_ptr[0] != 0) return PT2D_ERR_INVALID_ARG;
@@ -447,7 +447,8 @@ extern "C" {
 
 size_t pt2d_batch_instance_bytes(const pt2d_batch *b, const pt2d_instance *inst, int32_t I,
                                  int32_t J, int32_t runs) {
-    if (!b || !inst || inst->n < 1 || I < 1 || J < 1 || runs < 1 || I * J > pt2d::kBatchMaxReplicas)
+    if (!b || !inst || inst->n < 1 || I < 1 || J < 1 || runs < 1 ||
+        static_cast<int64_t>(I) * J > pt2d::kBatchMaxReplicas)
         return 0;
     pt2d::Prep pp;
     pt2d_options o;
@@ -566,7 +567,7 @@ int pt2d_batch_add(pt2d_batch *b, const pt2d_instance *inst, int32_t I, const fl
                    const int32_t *P, int32_t runs, uint64_t seed, const int64_t *target,
                    int64_t *id_out) {
     if (!b || !inst || !beta || !P || !id_out || runs < 1 || I < 1 || J < 1) return PT2D_ERR_INVALID_ARG;
-    if (I * J > pt2d::kBatchMaxReplicas) return PT2D_ERR_INVALID_ARG;
+    if (static_cast<int64_t>(I) * J > pt2d::kBatchMaxReplicas) return PT2D_ERR_INVALID_ARG;
     if (runs >= (1 << 27)) return PT2D_ERR_INVALID_ARG;
     pt2d_options o;
     pt2d_default_options(&o);
