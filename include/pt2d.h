@@ -227,6 +227,13 @@ int64_t pt2d_launch_count(const pt2d_ctx *ctx);
  * out[3] = walkers per thread.  Host only.  Errors: INVALID_ARG (NULL). */
 int pt2d_tiling(const pt2d_ctx *ctx, int32_t out[4]);
 
+/* The sweep tiling pt2d_create would choose for this problem (out as for
+ * pt2d_tiling), without creating a context or touching the GPU; with no GPU
+ * visible it plans for 152 SMs and 227 KB of shared memory per CTA.  Host
+ * only.  Errors: INVALID_ARG (as pt2d_workspace_size). */
+int pt2d_plan_tiling(const pt2d_instance *inst, int32_t I, int32_t J, int32_t runs,
+                     const pt2d_options *opt, int32_t out[4]);
+
 /* Kernel timing of a context created with opt.profile != 0: total device
  * milliseconds and launch count of the sweep kernel (kind 0) or the swap-event
  * kernel (kind 1) since creation, from CUDA events recorded on the context

@@ -18,7 +18,7 @@ from ._lib import (ACC_B, ACC_P, BEST_EVENT, BEST_F, BEST_STATE, COLORS, COUNTER
                    WALKER_AT, Pt2dError)
 
 __all__ = [
-    "PhysicalInstance", "sparsify", "greedy_color", "PT2D", "Batch", "PoolFull", "Server",
+    "PhysicalInstance", "sparsify", "greedy_color", "plan_tiling", "PT2D", "Batch", "PoolFull", "Server",
     "Pt2dError", "onehot_penalty", "equality_penalty", "adaptive_schedule",
     "diag_philox",
     "diag_pt_exp", "diag_heatbath", "diag_swap_accept", "diag_read_bandwidth", "STATES", "WALKER_AT", "F", "G",
@@ -285,10 +285,7 @@ class PT2D:
         walkers per thread."""
         out = (C.c_int32 * 4)()
         _lib.check(_lib.lib().pt2d_tiling(self._ctx, out), "pt2d_tiling", self._ctx)
-        kernel = {1: "global", 2: "smem", 3: "bits", 4: "generic", 5: "generic_smem", 6: "penalty_smem",
-                  7: "penalty_bits"}[out[0]]
-        return dict(kernel=kernel, walkers_per_cta=out[1], threads_per_cta=out[2],
-                    walkers_per_thread=out[3])
+        return _tiling_dict(out)
 
     def close(self) -> None:
         if getattr(self, "_ctx", None) and self._ctx.value:
@@ -307,6 +304,30 @@ class PT2D:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _tiling_dict(out) -> dict:
+    kernel = {1: "global", 2: "smem", 3: "bits", 4: "generic", 5: "generic_smem", 6: "penalty_smem",
+              7: "penalty_bits"}[out[0]]
+    return dict(kernel=kernel, walkers_per_cta=out[1], threads_per_cta=out[2], walkers_per_thread=out[3])
+
+
+def plan_tiling(inst: PhysicalInstance, I: int, J: int, runs: int, *, walkers_per_cta: int = 0,
+                threads_per_cta: int = 0, walkers_per_thread: int = 0, sweep_kernel: str = "auto") -> dict:
+    """The sweep tiling a context would choose (pt2d_plan_tiling), computed on
+    the host without a GPU: kernel, walkers and threads per CTA, walkers per
+    thread."""
+    opt = _lib.Options()
+    _lib.lib().pt2d_default_options(C.byref(opt))
+    opt.walkers_per_cta = int(walkers_per_cta)
+    opt.threads_per_cta = int(threads_per_cta)
+    opt.walkers_per_thread = int(walkers_per_thread)
+    opt.sweep_kernel = {"auto": 0, "global": 1, "smem": 2, "bits": 3}[sweep_kernel]
+    cs = inst.c_struct()
+    out = (C.c_int32 * 4)()
+    _lib.check(_lib.lib().pt2d_plan_tiling(C.byref(cs), int(I), int(J), int(runs), C.byref(opt), out),
+               "pt2d_plan_tiling")
+    return _tiling_dict(out)
 
 
 def _array_spec(what, runs, R, n, T):

@@ -28,7 +28,7 @@ SPARSIFY_FIXED, SPARSIFY_MAX_EDGES, SPARSIFY_MAX_DEGREE = 0, 1, 2
 EXPORTS = [
     "pt2d_default_options", "pt2d_workspace_size", "pt2d_create", "pt2d_run", "pt2d_read",
     "pt2d_read_walker",
-    "pt2d_write", "pt2d_array_bytes", "pt2d_sync", "pt2d_num_colors", "pt2d_tiling", "pt2d_launch_count",
+    "pt2d_write", "pt2d_array_bytes", "pt2d_sync", "pt2d_num_colors", "pt2d_tiling", "pt2d_plan_tiling", "pt2d_launch_count",
     "pt2d_destroy", "pt2d_strerror", "pt2d_cuda_error", "pt2d_sparsify", "pt2d_greedy_color",
     "pt2d_diag_philox", "pt2d_diag_pt_exp", "pt2d_diag_heatbath", "pt2d_diag_swap_accept",
     "pt2d_kernel_time", "pt2d_run_noalloc", "pt2d_batch_create", "pt2d_batch_instance_bytes",
@@ -150,6 +150,7 @@ def lib():
         L.pt2d_sync.argtypes = [vp]
         L.pt2d_num_colors.argtypes = [vp]
         L.pt2d_tiling.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.pt2d_plan_tiling.argtypes = [vp, i32, i32, i32, vp, C.POINTER(C.c_int32)]
         L.pt2d_launch_count.argtypes = [vp]
         L.pt2d_launch_count.restype = i64
         L.pt2d_destroy.argtypes = [vp]

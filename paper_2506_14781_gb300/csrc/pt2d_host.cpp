@@ -579,6 +579,17 @@ int cuda_fail(pt2d_ctx *c, cudaError_t e) {
 
 }  // namespace
 
+// The code of a sweep tiling reported by pt2d_tiling and pt2d_plan_tiling.
+namespace {
+void tiling_code(const pt2d::Prep &pp, int32_t out[4]) {
+    const pt2d::SweepTiling &t = pp.tiling;
+    out[0] = t.bits ? (pp.pen_kernel ? 7 : 3) : t.smem ? (pp.pen_kernel ? 6 : (pp.wide ? 5 : 2)) : (pp.wide ? 4 : 1);
+    out[1] = 4 * t.lanes_per_spin;
+    out[2] = t.threads;
+    out[3] = t.walkers_per_thread;
+}
+}  // namespace
+
 extern "C" {
 
 void pt2d_default_options(pt2d_options *opt) {
@@ -736,12 +747,17 @@ int pt2d_num_colors(const pt2d_ctx *c) { return c ? c->pp.C : 0; }
 
 int pt2d_tiling(const pt2d_ctx *c, int32_t out[4]) {
     if (!c || !out) return PT2D_ERR_INVALID_ARG;
-    const pt2d::SweepTiling &t = c->pp.tiling;
-    out[0] = t.bits ? (c->pp.pen_kernel ? 7 : 3)
-                    : t.smem ? (c->pp.pen_kernel ? 6 : (c->pp.wide ? 5 : 2)) : (c->pp.wide ? 4 : 1);
-    out[1] = 4 * t.lanes_per_spin;
-    out[2] = t.threads;
-    out[3] = t.walkers_per_thread;
+    tiling_code(c->pp, out);
+    return PT2D_OK;
+}
+
+int pt2d_plan_tiling(const pt2d_instance *inst, int32_t I, int32_t J, int32_t runs, const pt2d_options *opt,
+                     int32_t out[4]) {
+    if (!out) return PT2D_ERR_INVALID_ARG;
+    pt2d::Prep pp;
+    const int st = pt2d::prepare(inst, I, nullptr, J, nullptr, runs, opt, pp, 0, false);
+    if (st) return st;
+    tiling_code(pp, out);
     return PT2D_OK;
 }
 int64_t pt2d_launch_count(const pt2d_ctx *c) { return c ? c->launches : 0; }
